@@ -1,0 +1,732 @@
+/*
+ * Plain FP64 CPU oracle of the interpolative butterfly factorization (IBF)
+ * of Li & Yang, "Interpolative Butterfly Factorization" (arXiv 1605.03616).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this file; only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark do.  It shares no code with the CUDA library.
+ *
+ * Everything is complex128, written for readability, not speed:
+ *   - orc_direct_1d / orc_direct_2d : the defining sum u(x) = sum_xi K(x,xi) g(xi)
+ *     (Sec. 1, eq. DFIO).
+ *   - orc_ibf_apply_1d / orc_ibf_adjoint_1d : the butterfly algorithm in the
+ *     matrix-free form of Algorithm 2.1 (Sec. 2.2, eqs. (1), (2), switch,
+ *     (3), bf3) -- the same numbers as the preliminary IBF (Sec. 3).
+ *   - orc_ibf_build_1d + orc_ibf_explicit_* : the preliminary IBF of Sec. 3
+ *     with its factors V^0, H^l, M^h, G^l, U^L stored as explicit blocks
+ *     (eqs. PIBF1, PIBF2, switchlocM, PIBF3, PIBFbf3) and applied block by block.
+ *
+ * Conventions (readings of the paper where it is silent):
+ *   - r is the number of Chebyshev points per dimension; grid on [-1/2,1/2]
+ *     is z_t = cos(t*pi/(r-1))/2, t = 0..r-1 (Sec. 2.1).
+ *   - X boxes are half-open dyadic intervals of [0,1); Omega boxes are
+ *     half-open dyadic intervals of [-N/2, N/2); centres are midpoints, so the
+ *     Omega root has centre 0.  A point on a box boundary belongs to the box
+ *     on its right.
+ *   - The initialization uses A = root of T_X (centre 1/2), as Algorithm 2.1
+ *     states; h is the switch level, floor(L/2) unless the caller asks
+ *     otherwise.
+ *   - e(t) = exp(2*pi*i*t) is evaluated after removing the nearest integer
+ *     from t (an exact operation), so that sin/cos see |arg| <= pi.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+#define ORC_PHASE_NUFFT 0      /* Phi = x.xi                                   */
+#define ORC_PHASE_FIO1D 1      /* Phi = x xi + c(x)|xi|, c = (2+sin 2 pi x)/8  */
+#define ORC_PHASE_FIO2D 2      /* Phi = x.xi + sqrt(c1^2 xi1^2 + c2^2 xi2^2)   */
+#define ORC_PHASE_SEPARABLE 100 /* test phase f(x) + h(xi): remainder R^{AB}=0 */
+
+/* ------------------------------------------------------------------ */
+/* kernel pieces                                                       */
+/* ------------------------------------------------------------------ */
+
+/* exp(2 pi i t), argument reduced mod 1 first */
+static cplx e2pi(double t)
+{
+    double th = t - nearbyint(t);
+    double a = 2.0 * M_PI * th;
+    return cos(a) + I * sin(a);
+}
+
+/* 1D phase functions: eq. 1D-FT (with the sign of the K = e(+x xi) reading),
+ * eq. 1D-FIO-kernal, and the separable test phase. */
+double orc_phi_1d(int phase_id, double x, double xi)
+{
+    switch (phase_id) {
+    case ORC_PHASE_NUFFT:
+        return x * xi;
+    case ORC_PHASE_FIO1D: {
+        double c = (2.0 + sin(2.0 * M_PI * x)) / 8.0;
+        return x * xi + c * fabs(xi);
+    }
+    case ORC_PHASE_SEPARABLE:
+        return 0.75 * sin(2.0 * M_PI * x) + (0.125 * fabs(xi) + 0.3 * sin(0.1 * xi));
+    default:
+        return 0.0;
+    }
+}
+
+/* 2D phase of Sec. 6.3 with constants c1 = (2 + sin(2 pi x1) sin(2 pi x2))/16,
+ * c2 = (2 + cos(2 pi x1) cos(2 pi x2))/16; the separable test phase in 2D. */
+double orc_phi_2d(int phase_id, double x1, double x2, double k1, double k2)
+{
+    switch (phase_id) {
+    case ORC_PHASE_FIO2D: {
+        double c1 = (2.0 + sin(2.0 * M_PI * x1) * sin(2.0 * M_PI * x2)) / 16.0;
+        double c2 = (2.0 + cos(2.0 * M_PI * x1) * cos(2.0 * M_PI * x2)) / 16.0;
+        double a = c1 * k1;
+        double b = c2 * k2;
+        return (x1 * k1 + x2 * k2) + sqrt(a * a + b * b);
+    }
+    case ORC_PHASE_NUFFT:
+        return x1 * k1 + x2 * k2;
+    case ORC_PHASE_SEPARABLE:
+        return 0.75 * sin(2.0 * M_PI * x1) * cos(2.0 * M_PI * x2) +
+               (0.125 * sqrt(k1 * k1 + k2 * k2) + 0.3 * sin(0.1 * k1 - 0.07 * k2));
+    default:
+        return 0.0;
+    }
+}
+
+/* Chebyshev grid of order r on [-1/2, 1/2] (Sec. 2.1) */
+void orc_cheb_grid(int r, double* z)
+{
+    for (int t = 0; t < r; ++t)
+        z[t] = 0.5 * cos(t * M_PI / (r - 1));
+}
+
+/* Lagrange polynomial M_t on the grid z, evaluated at u (Sec. 2.1, product form) */
+double orc_lagrange(int r, const double* z, int t, double u)
+{
+    double p = 1.0;
+    for (int m = 0; m < r; ++m)
+        if (m != t)
+            p *= (u - z[m]) / (z[t] - z[m]);
+    return p;
+}
+
+/* ------------------------------------------------------------------ */
+/* 1D dyadic boxes: X box (l,i) = [i 2^-l, (i+1) 2^-l);                 */
+/* Omega box (l,j) = [-N/2 + j N 2^-l, -N/2 + (j+1) N 2^-l)             */
+/* ------------------------------------------------------------------ */
+static double xbox_c(int l, int64_t i) { return ((double)i + 0.5) / ldexp(1.0, l); }
+static double xbox_w(int l) { return 1.0 / ldexp(1.0, l); }
+static double wbox_w(int64_t N, int l) { return (double)N / ldexp(1.0, l); }
+static double wbox_c(int64_t N, int l, int64_t j) { return -0.5 * (double)N + ((double)j + 0.5) * wbox_w(N, l); }
+
+/* grid point t of a box of centre c and width w: c + w z_t */
+static double gridpt(double c, double w, const double* z, int t) { return c + w * z[t]; }
+
+/* leaf of T_X holding x (level L); leaf of T_Omega holding xi */
+static int64_t xleaf(int L, double x)
+{
+    int64_t n = (int64_t)1 << L;
+    int64_t i = (int64_t)floor(x * (double)n);
+    if (i < 0) i = 0;
+    if (i >= n) i = n - 1;
+    return i;
+}
+static int64_t wleaf(int64_t N, int L, double xi)
+{
+    int64_t n = (int64_t)1 << L;
+    int64_t j = (int64_t)floor((xi + 0.5 * (double)N) / wbox_w(N, L));
+    if (j < 0) j = 0;
+    if (j >= n) j = n - 1;
+    return j;
+}
+
+static int ilog2(int64_t N)
+{
+    int L = 0;
+    while (((int64_t)1 << L) < N) ++L;
+    return L;
+}
+
+/* ------------------------------------------------------------------ */
+/* Direct summation (eq. DFIO): u[n + nx c] = sum_k e(Phi(x_n, xi_k)) g[k + nxi c] */
+/* ------------------------------------------------------------------ */
+int orc_direct_1d(int phase_id, int64_t nx, const double* x, int64_t nxi, const double* xi,
+                  const cplx* g, int nrhs, cplx* u)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t n = 0; n < nx; ++n) {
+        for (int c = 0; c < nrhs; ++c) {
+            cplx s = 0;
+            for (int64_t k = 0; k < nxi; ++k)
+                s += e2pi(orc_phi_1d(phase_id, x[n], xi[k])) * g[k + nxi * c];
+            u[n + nx * c] = s;
+        }
+    }
+    return 0;
+}
+
+int orc_direct_2d(int phase_id, int64_t nx, const double* x, int64_t nxi, const double* xi,
+                  const cplx* g, int nrhs, cplx* u)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t n = 0; n < nx; ++n) {
+        for (int c = 0; c < nrhs; ++c) {
+            cplx s = 0;
+            for (int64_t k = 0; k < nxi; ++k)
+                s += e2pi(orc_phi_2d(phase_id, x[2 * n], x[2 * n + 1], xi[2 * k], xi[2 * k + 1])) *
+                     g[k + nxi * c];
+            u[n + nx * c] = s;
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* 1D butterfly, matrix-free (Algorithm 2.1 = the preliminary IBF, Sec. 3) */
+/* Lambda^l_{i,j} is stored at lam[(i * 2^(L-l) + j) * r + t].            */
+/* Omega is the integer grid xi_k = k - N/2 (eq. Omega).                  */
+/* ------------------------------------------------------------------ */
+
+/* Initialization, eq. (1) / eq. PIBF1, with A = root of T_X */
+static void mf_init(int ph, int64_t N, int L, int r, const double* z, const cplx* g, cplx* lam)
+{
+    double cA = xbox_c(0, 0);
+    int64_t nb = (int64_t)1 << L;
+    memset(lam, 0, sizeof(cplx) * nb * r);
+    double wB = wbox_w(N, L);
+    for (int64_t k = 0; k < N; ++k) {
+        double xi = (double)k - 0.5 * (double)N;
+        int64_t j = wleaf(N, L, xi);
+        double cB = wbox_c(N, L, j);
+        for (int t = 0; t < r; ++t) {
+            double gBt = gridpt(cB, wB, z, t);
+            lam[j * r + t] += e2pi(-orc_phi_1d(ph, cA, gBt)) *
+                              orc_lagrange(r, z, t, (xi - cB) / wB) * e2pi(orc_phi_1d(ph, cA, xi)) * g[k];
+        }
+    }
+}
+
+/* Recursion in xi, eq. (2) / eq. PIBF2: level l from level l-1 */
+static void mf_rec_xi(int ph, int64_t N, int L, int r, const double* z, int l, const cplx* prev, cplx* next)
+{
+    int64_t ni = (int64_t)1 << l, nj = (int64_t)1 << (L - l);
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int64_t i = 0; i < ni; ++i) {
+        for (int64_t j = 0; j < nj; ++j) {
+            double cA = xbox_c(l, i);
+            double cB = wbox_c(N, L - l, j), wB = wbox_w(N, L - l);
+            double wC = wbox_w(N, L - l + 1);
+            int64_t ip = i / 2;
+            for (int t = 0; t < r; ++t) {
+                double gBt = gridpt(cB, wB, z, t);
+                cplx acc = 0;
+                for (int c = 0; c < 2; ++c) {
+                    int64_t C = 2 * j + c;
+                    double cC = wbox_c(N, L - l + 1, C);
+                    const cplx* lp = prev + (ip * ((int64_t)1 << (L - l + 1)) + C) * r;
+                    for (int s = 0; s < r; ++s) {
+                        double gCs = gridpt(cC, wC, z, s);
+                        acc += orc_lagrange(r, z, t, (gCs - cB) / wB) * e2pi(orc_phi_1d(ph, cA, gCs)) * lp[s];
+                    }
+                }
+                next[(i * nj + j) * r + t] = e2pi(-orc_phi_1d(ph, cA, gBt)) * acc;
+            }
+        }
+    }
+}
+
+/* Switch, eq. switchlocM: at level h, in place */
+static void mf_switch(int ph, int64_t N, int L, int r, const double* z, int h, cplx* lam)
+{
+    int64_t ni = (int64_t)1 << h, nj = (int64_t)1 << (L - h);
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int64_t i = 0; i < ni; ++i) {
+        for (int64_t j = 0; j < nj; ++j) {
+            double cA = xbox_c(h, i), wA = xbox_w(h);
+            double cB = wbox_c(N, L - h, j), wB = wbox_w(N, L - h);
+            cplx old[64];
+            cplx* v = lam + (i * nj + j) * r;
+            for (int s = 0; s < r; ++s) old[s] = v[s];
+            for (int t = 0; t < r; ++t) {
+                cplx acc = 0;
+                for (int s = 0; s < r; ++s)
+                    acc += e2pi(orc_phi_1d(ph, gridpt(cA, wA, z, t), gridpt(cB, wB, z, s))) * old[s];
+                v[t] = acc;
+            }
+        }
+    }
+}
+
+/* Recursion in x, eq. (3) / eq. PIBF3: level l from level l-1 */
+static void mf_rec_x(int ph, int64_t N, int L, int r, const double* z, int l, const cplx* prev, cplx* next)
+{
+    int64_t ni = (int64_t)1 << l, nj = (int64_t)1 << (L - l);
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int64_t i = 0; i < ni; ++i) {
+        for (int64_t j = 0; j < nj; ++j) {
+            double cA = xbox_c(l, i), wA = xbox_w(l);
+            int64_t ip = i / 2;
+            double cP = xbox_c(l - 1, ip), wP = xbox_w(l - 1);
+            for (int t = 0; t < r; ++t) {
+                double gAt = gridpt(cA, wA, z, t);
+                cplx acc = 0;
+                for (int c = 0; c < 2; ++c) {
+                    int64_t C = 2 * j + c;
+                    double cC = wbox_c(N, L - l + 1, C);
+                    const cplx* lp = prev + (ip * ((int64_t)1 << (L - l + 1)) + C) * r;
+                    cplx inner = 0;
+                    for (int s = 0; s < r; ++s) {
+                        double gPs = gridpt(cP, wP, z, s);
+                        inner += orc_lagrange(r, z, s, (gAt - cP) / wP) * e2pi(-orc_phi_1d(ph, gPs, cC)) * lp[s];
+                    }
+                    acc += e2pi(orc_phi_1d(ph, gAt, cC)) * inner;
+                }
+                next[(i * nj + j) * r + t] = acc;
+            }
+        }
+    }
+}
+
+/* Termination, eq. bf3 / eq. PIBFbf3, B = root of T_Omega (centre 0) */
+static void mf_term(int ph, int64_t N, int L, int r, const double* z, int64_t nx, const double* x,
+                    const cplx* lam, cplx* u)
+{
+    double cB = wbox_c(N, 0, 0);
+    double wA = xbox_w(L);
+    for (int64_t n = 0; n < nx; ++n) {
+        int64_t i = xleaf(L, x[n]);
+        double cA = xbox_c(L, i);
+        cplx acc = 0;
+        for (int t = 0; t < r; ++t)
+            acc += orc_lagrange(r, z, t, (x[n] - cA) / wA) * e2pi(-orc_phi_1d(ph, gridpt(cA, wA, z, t), cB)) *
+                   lam[i * r + t];
+        u[n] = e2pi(orc_phi_1d(ph, x[n], cB)) * acc;
+    }
+}
+
+int orc_ibf_apply_1d(int phase_id, int64_t N, int r, int h, int64_t nx, const double* x, const cplx* g,
+                     int nrhs, cplx* u)
+{
+    int L = ilog2(N);
+    if (((int64_t)1 << L) != N || r < 2 || r > 64 || h < 0 || h > L) return 1;
+    double z[64];
+    orc_cheb_grid(r, z);
+    cplx* a = (cplx*)malloc(sizeof(cplx) * N * r);
+    cplx* b = (cplx*)malloc(sizeof(cplx) * N * r);
+    if (!a || !b) { free(a); free(b); return 2; }
+    for (int col = 0; col < nrhs; ++col) {
+        mf_init(phase_id, N, L, r, z, g + N * col, a);
+        for (int l = 1; l <= h; ++l) {
+            mf_rec_xi(phase_id, N, L, r, z, l, a, b);
+            cplx* tmp = a; a = b; b = tmp;
+        }
+        mf_switch(phase_id, N, L, r, z, h, a);
+        for (int l = h + 1; l <= L; ++l) {
+            mf_rec_x(phase_id, N, L, r, z, l, a, b);
+            cplx* tmp = a; a = b; b = tmp;
+        }
+        mf_term(phase_id, N, L, r, z, nx, x, a, u + nx * col);
+    }
+    free(a);
+    free(b);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Adjoint, matrix-free: the conjugate transpose of each step above,    */
+/* taken in reverse order (K^* = V^0 H^1 ... (M^h)^* ... (U^L)^*).       */
+/* ------------------------------------------------------------------ */
+static void mfa_term(int ph, int64_t N, int L, int r, const double* z, int64_t nx, const double* x,
+                     const cplx* y, cplx* lam)
+{
+    double cB = wbox_c(N, 0, 0);
+    double wA = xbox_w(L);
+    memset(lam, 0, sizeof(cplx) * ((int64_t)1 << L) * r);
+    for (int64_t n = 0; n < nx; ++n) {
+        int64_t i = xleaf(L, x[n]);
+        double cA = xbox_c(L, i);
+        for (int t = 0; t < r; ++t) {
+            cplx w = e2pi(orc_phi_1d(ph, x[n], cB)) * orc_lagrange(r, z, t, (x[n] - cA) / wA) *
+                     e2pi(-orc_phi_1d(ph, gridpt(cA, wA, z, t), cB));
+            lam[i * r + t] += conj(w) * y[n];
+        }
+    }
+}
+
+/* adjoint of eq. (3): level l (next) back to level l-1 (prev) */
+static void mfa_rec_x(int ph, int64_t N, int L, int r, const double* z, int l, const cplx* next, cplx* prev)
+{
+    int64_t npi = (int64_t)1 << (l - 1), nC = (int64_t)1 << (L - l + 1), nj = (int64_t)1 << (L - l);
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int64_t ip = 0; ip < npi; ++ip) {
+        for (int64_t C = 0; C < nC; ++C) {
+            double cP = xbox_c(l - 1, ip), wP = xbox_w(l - 1);
+            double cC = wbox_c(N, L - l + 1, C);
+            int64_t j = C / 2;
+            for (int s = 0; s < r; ++s) {
+                double gPs = gridpt(cP, wP, z, s);
+                cplx acc = 0;
+                for (int a = 0; a < 2; ++a) {
+                    int64_t i = 2 * ip + a;
+                    double cA = xbox_c(l, i), wA = xbox_w(l);
+                    const cplx* ln = next + (i * nj + j) * r;
+                    for (int t = 0; t < r; ++t) {
+                        double gAt = gridpt(cA, wA, z, t);
+                        cplx w = e2pi(orc_phi_1d(ph, gAt, cC)) * orc_lagrange(r, z, s, (gAt - cP) / wP) *
+                                 e2pi(-orc_phi_1d(ph, gPs, cC));
+                        acc += conj(w) * ln[t];
+                    }
+                }
+                prev[(ip * nC + C) * r + s] = acc;
+            }
+        }
+    }
+}
+
+static void mfa_switch(int ph, int64_t N, int L, int r, const double* z, int h, cplx* lam)
+{
+    int64_t ni = (int64_t)1 << h, nj = (int64_t)1 << (L - h);
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int64_t i = 0; i < ni; ++i) {
+        for (int64_t j = 0; j < nj; ++j) {
+            double cA = xbox_c(h, i), wA = xbox_w(h);
+            double cB = wbox_c(N, L - h, j), wB = wbox_w(N, L - h);
+            cplx old[64];
+            cplx* v = lam + (i * nj + j) * r;
+            for (int t = 0; t < r; ++t) old[t] = v[t];
+            for (int s = 0; s < r; ++s) {
+                cplx acc = 0;
+                for (int t = 0; t < r; ++t)
+                    acc += conj(e2pi(orc_phi_1d(ph, gridpt(cA, wA, z, t), gridpt(cB, wB, z, s)))) * old[t];
+                v[s] = acc;
+            }
+        }
+    }
+}
+
+/* adjoint of eq. (2): level l (next) back to level l-1 (prev) */
+static void mfa_rec_xi(int ph, int64_t N, int L, int r, const double* z, int l, const cplx* next, cplx* prev)
+{
+    int64_t npi = (int64_t)1 << (l - 1), nC = (int64_t)1 << (L - l + 1), nj = (int64_t)1 << (L - l);
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int64_t ip = 0; ip < npi; ++ip) {
+        for (int64_t C = 0; C < nC; ++C) {
+            int64_t j = C / 2;
+            double cB = wbox_c(N, L - l, j), wB = wbox_w(N, L - l);
+            double cC = wbox_c(N, L - l + 1, C), wC = wbox_w(N, L - l + 1);
+            for (int s = 0; s < r; ++s) {
+                double gCs = gridpt(cC, wC, z, s);
+                cplx acc = 0;
+                for (int a = 0; a < 2; ++a) {
+                    int64_t i = 2 * ip + a;
+                    double cA = xbox_c(l, i);
+                    const cplx* ln = next + (i * nj + j) * r;
+                    for (int t = 0; t < r; ++t) {
+                        double gBt = gridpt(cB, wB, z, t);
+                        cplx w = e2pi(-orc_phi_1d(ph, cA, gBt)) * orc_lagrange(r, z, t, (gCs - cB) / wB) *
+                                 e2pi(orc_phi_1d(ph, cA, gCs));
+                        acc += conj(w) * ln[t];
+                    }
+                }
+                prev[(ip * nC + C) * r + s] = acc;
+            }
+        }
+    }
+}
+
+static void mfa_init(int ph, int64_t N, int L, int r, const double* z, const cplx* lam, cplx* g)
+{
+    double cA = xbox_c(0, 0);
+    double wB = wbox_w(N, L);
+    for (int64_t k = 0; k < N; ++k) {
+        double xi = (double)k - 0.5 * (double)N;
+        int64_t j = wleaf(N, L, xi);
+        double cB = wbox_c(N, L, j);
+        cplx acc = 0;
+        for (int t = 0; t < r; ++t) {
+            double gBt = gridpt(cB, wB, z, t);
+            cplx w = e2pi(-orc_phi_1d(ph, cA, gBt)) * orc_lagrange(r, z, t, (xi - cB) / wB) *
+                     e2pi(orc_phi_1d(ph, cA, xi));
+            acc += conj(w) * lam[j * r + t];
+        }
+        g[k] = acc;
+    }
+}
+
+int orc_ibf_adjoint_1d(int phase_id, int64_t N, int r, int h, int64_t nx, const double* x, const cplx* y,
+                       int nrhs, cplx* g)
+{
+    int L = ilog2(N);
+    if (((int64_t)1 << L) != N || r < 2 || r > 64 || h < 0 || h > L) return 1;
+    double z[64];
+    orc_cheb_grid(r, z);
+    cplx* a = (cplx*)malloc(sizeof(cplx) * N * r);
+    cplx* b = (cplx*)malloc(sizeof(cplx) * N * r);
+    if (!a || !b) { free(a); free(b); return 2; }
+    for (int col = 0; col < nrhs; ++col) {
+        mfa_term(phase_id, N, L, r, z, nx, x, y + nx * col, a);
+        for (int l = L; l >= h + 1; --l) {
+            mfa_rec_x(phase_id, N, L, r, z, l, a, b);
+            cplx* tmp = a; a = b; b = tmp;
+        }
+        mfa_switch(phase_id, N, L, r, z, h, a);
+        for (int l = h; l >= 1; --l) {
+            mfa_rec_xi(phase_id, N, L, r, z, l, a, b);
+            cplx* tmp = a; a = b; b = tmp;
+        }
+        mfa_init(phase_id, N, L, r, z, a, g + N * col);
+    }
+    free(a);
+    free(b);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Preliminary IBF with explicit factors (Sec. 3).                      */
+/* Blocks are indexed by the output pair p = i * 2^(L-l) + j of level l: */
+/*   H[l][p][c][t][s] maps Lambda^{l-1}_{i/2, 2j+c}[s] -> Lambda^l_{i,j}[t]  */
+/*   (l = 1..h, eq. PIBF2),  G[l][p][c][t][s] the same for l = h+1..L      */
+/*   (eq. PIBF3), Msw[p][t][s] the switch blocks (eq. switchlocM),         */
+/*   V[k][t] the column of (V^0)^* for xi_k (eq. PIBF1), U[n][t] the row of  */
+/*   U^L for x_n (eq. PIBFbf3).                                            */
+/* ------------------------------------------------------------------ */
+typedef struct orc_ibf {
+    int phase_id, L, h, r;
+    int64_t N, nx;
+    double* x;
+    cplx* V;      /* N * r               */
+    cplx** blk;   /* blk[l], l = 1..L: N * 2 * r * r */
+    cplx* Msw;    /* N * r * r           */
+    cplx* U;      /* nx * r              */
+} orc_ibf;
+
+void orc_ibf_free(orc_ibf* f)
+{
+    if (!f) return;
+    free(f->x);
+    free(f->V);
+    if (f->blk)
+        for (int l = 1; l <= f->L; ++l) free(f->blk[l]);
+    free(f->blk);
+    free(f->Msw);
+    free(f->U);
+    free(f);
+}
+
+orc_ibf* orc_ibf_build_1d(int phase_id, int64_t N, int r, int h, int64_t nx, const double* x)
+{
+    int L = ilog2(N);
+    if (((int64_t)1 << L) != N || r < 2 || r > 64 || h < 0 || h > L) return NULL;
+    orc_ibf* f = (orc_ibf*)calloc(1, sizeof(orc_ibf));
+    f->phase_id = phase_id; f->L = L; f->h = h; f->r = r; f->N = N; f->nx = nx;
+    f->x = (double*)malloc(sizeof(double) * nx);
+    memcpy(f->x, x, sizeof(double) * nx);
+    double z[64];
+    orc_cheb_grid(r, z);
+    int ph = phase_id;
+
+    /* V^0 (eq. PIBF1) */
+    f->V = (cplx*)malloc(sizeof(cplx) * N * r);
+    {
+        double cA = xbox_c(0, 0), wB = wbox_w(N, L);
+        for (int64_t k = 0; k < N; ++k) {
+            double xi = (double)k - 0.5 * (double)N;
+            double cB = wbox_c(N, L, wleaf(N, L, xi));
+            for (int t = 0; t < r; ++t)
+                f->V[k * r + t] = e2pi(-orc_phi_1d(ph, cA, gridpt(cB, wB, z, t))) *
+                                  orc_lagrange(r, z, t, (xi - cB) / wB) * e2pi(orc_phi_1d(ph, cA, xi));
+        }
+    }
+    f->blk = (cplx**)calloc(L + 1, sizeof(cplx*));
+    for (int l = 1; l <= L; ++l) {
+        cplx* B = (cplx*)malloc(sizeof(cplx) * N * 2 * r * r);
+        f->blk[l] = B;
+        int64_t ni = (int64_t)1 << l, nj = (int64_t)1 << (L - l);
+        for (int64_t i = 0; i < ni; ++i)
+            for (int64_t j = 0; j < nj; ++j)
+                for (int c = 0; c < 2; ++c)
+                    for (int t = 0; t < r; ++t)
+                        for (int s = 0; s < r; ++s) {
+                            cplx v;
+                            double cC = wbox_c(N, L - l + 1, 2 * j + c), wC = wbox_w(N, L - l + 1);
+                            if (l <= h) { /* eq. PIBF2 */
+                                double cA = xbox_c(l, i);
+                                double cB = wbox_c(N, L - l, j), wB = wbox_w(N, L - l);
+                                double gCs = gridpt(cC, wC, z, s);
+                                v = e2pi(-orc_phi_1d(ph, cA, gridpt(cB, wB, z, t))) *
+                                    orc_lagrange(r, z, t, (gCs - cB) / wB) * e2pi(orc_phi_1d(ph, cA, gCs));
+                            } else { /* eq. PIBF3 */
+                                double cA = xbox_c(l, i), wA = xbox_w(l);
+                                double cP = xbox_c(l - 1, i / 2), wP = xbox_w(l - 1);
+                                double gAt = gridpt(cA, wA, z, t);
+                                v = e2pi(orc_phi_1d(ph, gAt, cC)) * orc_lagrange(r, z, s, (gAt - cP) / wP) *
+                                    e2pi(-orc_phi_1d(ph, gridpt(cP, wP, z, s), cC));
+                            }
+                            B[((((i * nj + j) * 2 + c) * r) + t) * r + s] = v;
+                        }
+    }
+    /* M^h (eq. switchlocM) */
+    f->Msw = (cplx*)malloc(sizeof(cplx) * N * r * r);
+    {
+        int64_t ni = (int64_t)1 << h, nj = (int64_t)1 << (L - h);
+        for (int64_t i = 0; i < ni; ++i)
+            for (int64_t j = 0; j < nj; ++j) {
+                double cA = xbox_c(h, i), wA = xbox_w(h);
+                double cB = wbox_c(N, L - h, j), wB = wbox_w(N, L - h);
+                for (int t = 0; t < r; ++t)
+                    for (int s = 0; s < r; ++s)
+                        f->Msw[((i * nj + j) * r + t) * r + s] =
+                            e2pi(orc_phi_1d(ph, gridpt(cA, wA, z, t), gridpt(cB, wB, z, s)));
+            }
+    }
+    /* U^L (eq. PIBFbf3) */
+    f->U = (cplx*)malloc(sizeof(cplx) * nx * r);
+    {
+        double cB = wbox_c(N, 0, 0), wA = xbox_w(L);
+        for (int64_t n = 0; n < nx; ++n) {
+            double cA = xbox_c(L, xleaf(L, x[n]));
+            for (int t = 0; t < r; ++t)
+                f->U[n * r + t] = e2pi(orc_phi_1d(ph, x[n], cB)) * orc_lagrange(r, z, t, (x[n] - cA) / wA) *
+                                  e2pi(-orc_phi_1d(ph, gridpt(cA, wA, z, t), cB));
+        }
+    }
+    return f;
+}
+
+/* the switch at level h with the stored blocks: out_p = M~_p in_p for every pair p */
+static void orc_switch_explicit(const orc_ibf* f, const cplx* in, cplx* out)
+{
+    int r = f->r;
+    for (int64_t p = 0; p < f->N; ++p)
+        for (int t = 0; t < r; ++t) {
+            cplx acc = 0;
+            for (int s = 0; s < r; ++s) acc += f->Msw[(p * r + t) * r + s] * in[p * r + s];
+            out[p * r + t] = acc;
+        }
+}
+
+int orc_ibf_explicit_apply(const orc_ibf* f, const cplx* g, int nrhs, cplx* u)
+{
+    int64_t N = f->N;
+    int L = f->L, h = f->h, r = f->r;
+    cplx* a = (cplx*)malloc(sizeof(cplx) * N * r);
+    cplx* b = (cplx*)malloc(sizeof(cplx) * N * r);
+    for (int col = 0; col < nrhs; ++col) {
+        const cplx* gc = g + N * col;
+        /* Lambda^0 = (V^0)^* g */
+        memset(a, 0, sizeof(cplx) * N * r);
+        for (int64_t k = 0; k < N; ++k) {
+            int64_t j = wleaf(N, L, (double)k - 0.5 * (double)N);
+            for (int t = 0; t < r; ++t) a[j * r + t] += f->V[k * r + t] * gc[k];
+        }
+        if (h == 0) {
+            orc_switch_explicit(f, a, b);
+            cplx* tmp = a; a = b; b = tmp;
+        }
+        for (int l = 1; l <= L; ++l) {
+            int64_t ni = (int64_t)1 << l, nj = (int64_t)1 << (L - l);
+            const cplx* B = f->blk[l];
+            for (int64_t i = 0; i < ni; ++i)
+                for (int64_t j = 0; j < nj; ++j)
+                    for (int t = 0; t < r; ++t) {
+                        cplx acc = 0;
+                        for (int c = 0; c < 2; ++c) {
+                            const cplx* in = a + ((i / 2) * (2 * nj) + 2 * j + c) * r;
+                            const cplx* row = B + ((((i * nj + j) * 2 + c) * r) + t) * r;
+                            for (int s = 0; s < r; ++s) acc += row[s] * in[s];
+                        }
+                        b[(i * nj + j) * r + t] = acc;
+                    }
+            cplx* tmp = a; a = b; b = tmp;
+            if (l == h) {
+                /* the switch at level h: Lambda~ = M~ Lambda for every pair */
+                orc_switch_explicit(f, a, b);
+                tmp = a; a = b; b = tmp;
+            }
+        }
+        for (int64_t n = 0; n < f->nx; ++n) {
+            int64_t i = xleaf(L, f->x[n]);
+            cplx acc = 0;
+            for (int t = 0; t < r; ++t) acc += f->U[n * r + t] * a[i * r + t];
+            u[n + f->nx * col] = acc;
+        }
+    }
+    free(a);
+    free(b);
+    return 0;
+}
+
+int orc_ibf_explicit_adjoint(const orc_ibf* f, const cplx* y, int nrhs, cplx* g)
+{
+    int64_t N = f->N;
+    int L = f->L, h = f->h, r = f->r;
+    cplx* a = (cplx*)malloc(sizeof(cplx) * N * r);
+    cplx* b = (cplx*)malloc(sizeof(cplx) * N * r);
+    for (int col = 0; col < nrhs; ++col) {
+        const cplx* yc = y + f->nx * col;
+        memset(a, 0, sizeof(cplx) * N * r);
+        for (int64_t n = 0; n < f->nx; ++n) {
+            int64_t i = xleaf(L, f->x[n]);
+            for (int t = 0; t < r; ++t) a[i * r + t] += conj(f->U[n * r + t]) * yc[n];
+        }
+        for (int l = L; l >= 1; --l) {
+            if (l == h) {
+                for (int64_t p = 0; p < N; ++p)
+                    for (int s = 0; s < r; ++s) {
+                        cplx acc = 0;
+                        for (int t = 0; t < r; ++t) acc += conj(f->Msw[(p * r + t) * r + s]) * a[p * r + t];
+                        b[p * r + s] = acc;
+                    }
+                cplx* tmp = a; a = b; b = tmp;
+            }
+            int64_t nj = (int64_t)1 << (L - l), npi = (int64_t)1 << (l - 1), nC = 2 * nj;
+            const cplx* B = f->blk[l];
+            memset(b, 0, sizeof(cplx) * N * r);
+            for (int64_t ip = 0; ip < npi; ++ip)
+                for (int64_t C = 0; C < nC; ++C)
+                    for (int s = 0; s < r; ++s) {
+                        cplx acc = 0;
+                        int64_t j = C / 2;
+                        int c = (int)(C % 2);
+                        for (int aa = 0; aa < 2; ++aa) {
+                            int64_t i = 2 * ip + aa;
+                            const cplx* on = a + (i * nj + j) * r;
+                            for (int t = 0; t < r; ++t)
+                                acc += conj(B[((((i * nj + j) * 2 + c) * r) + t) * r + s]) * on[t];
+                        }
+                        b[(ip * nC + C) * r + s] = acc;
+                    }
+            cplx* tmp = a; a = b; b = tmp;
+        }
+        if (h == 0) {
+            for (int64_t p = 0; p < N; ++p)
+                for (int s = 0; s < r; ++s) {
+                    cplx acc = 0;
+                    for (int t = 0; t < r; ++t) acc += conj(f->Msw[(p * r + t) * r + s]) * a[p * r + t];
+                    b[p * r + s] = acc;
+                }
+            cplx* tmp = a; a = b; b = tmp;
+        }
+        for (int64_t k = 0; k < N; ++k) {
+            int64_t j = wleaf(N, L, (double)k - 0.5 * (double)N);
+            cplx acc = 0;
+            for (int t = 0; t < r; ++t) acc += conj(f->V[k * r + t]) * a[j * r + t];
+            g[k + N * col] = acc;
+        }
+    }
+    free(a);
+    free(b);
+    return 0;
+}
+
+/* block accessors for the dense-assembly tests (copies out, complex128) */
+int orc_ibf_get_V(const orc_ibf* f, cplx* out) { memcpy(out, f->V, sizeof(cplx) * f->N * f->r); return 0; }
+int orc_ibf_get_U(const orc_ibf* f, cplx* out) { memcpy(out, f->U, sizeof(cplx) * f->nx * f->r); return 0; }
+int orc_ibf_get_M(const orc_ibf* f, cplx* out) { memcpy(out, f->Msw, sizeof(cplx) * f->N * f->r * f->r); return 0; }
+int orc_ibf_get_blk(const orc_ibf* f, int l, cplx* out)
+{
+    if (l < 1 || l > f->L) return 1;
+    memcpy(out, f->blk[l], sizeof(cplx) * f->N * 2 * f->r * f->r);
+    return 0;
+}
