@@ -1,0 +1,373 @@
+"""Benchmark of the IBF apply on GB300 (one JSON line on rank 0).
+
+Workload (default): 1D FIO, Phi(x,xi) = x xi + c(x)|xi|, c = (2 + sin 2 pi x)/8
+(Sec. 6.2), x_j = j/N, xi_k = k - N/2, N = 2^20, r = 9 Chebyshev points,
+nrhs = 64 complex64 right-hand sides with iid N(0,1) real and imaginary
+parts, FP32 structured fused apply.  A step is one u = K g over the 64
+vectors.  Inputs (512 MB) and the two Lambda buffers (4.8 GB each) exceed
+the 129 MB L2, so no flush is needed between steps.
+
+Reported next to it: the plain FP64 explicit single-vector form on the same
+GPU (the form the fast path is measured against) with the relative L2
+difference of the FP32 result from it, per-kernel CUDA-event timing of the
+dominant kernel against its roofline, and the FP64 CPU oracle timed on the
+host cores.
+
+--impl reference times the FP64 CPU oracle (the method as the paper states
+it, matrix-free, all host cores) on one vector of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+FP32_LANES_PER_SM = 128
+METRIC = "IBF apply vectors/s (rel.err <= 1e-5 vs plain FP64 GPU form)"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def workload_name(a):
+    return "1D FIO Phi=x*xi+c(x)|xi| N=2^%d r=%d nrhs=%d complex64 (FP32 structured)" % (
+        int(np.log2(a.N)), a.r, a.nrhs)
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_index: int):
+        self.dev = dev_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [v.strip() for v in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, p[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU oracle arm
+def oracle_vectors_per_s(a, threads: int):
+    """Time the FP64 oracle (matrix-free butterfly) on one vector of the
+    workload; returns (vectors/s, seconds)."""
+    import oracle as O
+    O.set_threads(threads)
+    g = W.complex_normal((a.N, 1), W.rng(workload=2))
+    x = W.uniform_x(a.N)
+    t0 = time.perf_counter()
+    O.ibf_apply_1d(O.PHASE_FIO1D, a.N, a.r, x, g)
+    dt = time.perf_counter() - t0
+    return 1.0 / dt, dt
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cores = os.cpu_count() or 1
+    # warm-up steps run the same code on a 2^12 problem: the CPU oracle has no
+    # state to warm beyond its first touch of the code and the thread pool
+    small = argparse.Namespace(**{**vars(a), "N": 1 << 12})
+    for _ in range(a.warmup):
+        oracle_vectors_per_s(small, cores)
+    times = []
+    for _ in range(a.steps):
+        times.append(oracle_vectors_per_s(a, cores)[1])
+    tot = sum(times)
+    v = a.steps / tot
+    sample = "one of the %d vectors per step (N=2^%d, matrix-free FP64 oracle, %d threads)" % (
+        a.nrhs, int(np.log2(a.N)), cores)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "vectors/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "N": a.N, "r": a.r, "nrhs": a.nrhs, "phase": "FIO1D"},
+            "cpu_baseline": {"value": v, "unit": "vectors/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "vectors/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def structured_flops(kind_levels, r, N, nc, pro, epi):
+    """Algorithmic FP32 flops of one fused launch: per butterfly unit and
+    right-hand side, 4 diagonal complex multiplies (6 r flops each) and 4 real
+    r x r times complex r products (4 r^2 flops each)."""
+    unit = 16 * r * r + 24 * r
+    f = unit * (N // 2) * kind_levels * nc
+    if pro == "V":
+        f += 6 * r * N * nc
+    if epi == "switch":
+        f += 8 * r * r * N * nc
+    if epi == "U":
+        f += 8 * r * N * nc
+    return f
+
+
+def run_gpu(a):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1605_03616_gb300 as ibf
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    N, r, nrhs = a.N, a.r, a.nrhs
+    plan = ibf.Plan(ibf.PHASE_FIO1D, N, r, ibf.C64_FP32, max_nrhs=nrhs)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    g_host = W.complex_normal((nrhs, N), W.rng(workload=2 + 1000 * rank), dtype=np.complex64)  # row = column
+    g = torch.from_numpy(g_host).to(dev)            # column-major N x nrhs
+    u = torch.empty_like(g)
+    launches = plan.query(ibf.Q_LAUNCHES)
+
+    def step():
+        plan.apply_raw(g.data_ptr(), u.data_ptr(), nrhs, stream.cuda_stream)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    plan.profile_begin(a.steps * launches + 8)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    prof = plan.profile_end()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * nrhs * a.steps / (ms / 1e3)
+
+    # ---- dominant kernel and its roofline (per-launch CUDA events, timed region)
+    sched = []
+    L, h = plan.L, plan.h
+    kfuse = plan.query(ibf.Q_LEVELS_PER_LAUNCH)
+
+    def split(lo, hi, kind):
+        n = hi - lo
+        nch = (n + kfuse - 1) // kfuse
+        for c in range(nch):
+            ln = n // nch + (1 if c < n % nch else 0)
+            sched.append((lo, lo + ln, kind))
+            lo += ln
+    split(0, h, ibf.K_FUSED_H)
+    split(h, L, ibf.K_FUSED_G)
+    per_launch = {}
+    for idx, (kind, t_ms) in enumerate(prof):
+        lo, hi, kd = sched[idx % len(sched)]
+        per_launch.setdefault((lo, hi, kd), []).append(t_ms)
+    tot = {k: sum(v) for k, v in per_launch.items()}
+    dom = max(tot, key=tot.get)
+    lo, hi, kd = dom
+    pro = "V" if lo == 0 else None
+    epi = "U" if hi == L else ("switch" if hi == h else None)
+    avg_ms = statistics.mean(per_launch[dom])
+    flops = structured_flops(hi - lo, r, N, nrhs, pro, epi)
+    esz = 8
+    bytes_alg = 0
+    bytes_alg += (N * nrhs * esz) if pro == "V" else (N * r * nrhs * esz)          # input
+    bytes_alg += (N * nrhs * esz) if epi == "U" else (N * r * nrhs * esz)          # output
+    bytes_alg += (hi - lo) * 2 * N * r * esz                                       # phase tables
+    if epi == "switch":
+        bytes_alg += N * r * r * esz
+    pk, pk_kind = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = nsm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12      # TFLOP/s at max clock
+    ach_tf = flops / (avg_ms / 1e3) / 1e12
+    ach_gb = bytes_alg / (avg_ms / 1e3) / 1e9
+    frac_alu = ach_tf / fp32_peak
+    frac_hbm = ach_gb / float(pk["hbm_gbs"])
+    kname = "k_fused<float,%d,fwd,%s> levels %d..%d" % (r, "H" if kd == ibf.K_FUSED_H else "G", lo + 1, hi)
+    if frac_alu >= frac_hbm:
+        roof = {"bound": "alu", "achieved": ach_tf, "peak": fp32_peak, "unit": "TFLOP/s", "frac": frac_alu,
+                "traffic": None}
+    else:
+        roof = {"bound": "hbm", "achieved": ach_gb, "peak": float(pk["hbm_gbs"]), "unit": "GB/s",
+                "frac": frac_hbm, "traffic": None}
+    roof.update({"kernel": kname, "avg_launch_ms": avg_ms, "launches_timed": len(per_launch[dom]),
+                 "peak_source": ("FP32 lanes x SMs x 2 x max SM clock (%s clock)" % pk_kind) if roof["bound"] == "alu"
+                 else "%s hbm_gbs" % pk_kind,
+                 "alu_frac": frac_alu, "hbm_frac": frac_hbm, "alg_flops": flops, "alg_bytes": bytes_alg})
+
+    # ---- end to end through the public API with host buffers
+    gh = torch.from_numpy(g_host).pin_memory()
+    uh = torch.empty_like(gh).pin_memory()
+
+    def e2e_step():
+        g.copy_(gh, non_blocking=True)
+        plan.apply_raw(g.data_ptr(), u.data_ptr(), nrhs, stream.cuda_stream)
+        uh.copy_(u, non_blocking=True)
+
+    for _ in range(max(1, a.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(stream)
+    for _ in range(a.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": world * nrhs * a.steps / (e2e_ms / 1e3), "unit": "vectors/s",
+           "h2d_bytes_per_step": int(g.numel() * 8), "d2h_bytes_per_step": int(u.numel() * 8)}
+
+    # ---- plain FP64 explicit single-vector form on the same GPU, and accuracy
+    fp64 = None
+    if not a.skip_fp64 and rank == 0:
+        p64 = ibf.Plan(ibf.PHASE_FIO1D, N, r, ibf.C128, max_nrhs=1)
+        g64 = g[0:1].to(torch.complex128).contiguous()
+        u64 = torch.empty_like(g64)
+        for _ in range(2):
+            p64.apply_raw(g64.data_ptr(), u64.data_ptr(), 1, stream.cuda_stream)
+        torch.cuda.synchronize()
+        reps = 3
+        e0.record(stream)
+        for _ in range(reps):
+            p64.apply_raw(g64.data_ptr(), u64.data_ptr(), 1, stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) / reps
+        ucmp = u[0:4].to(torch.complex128)
+        g4 = g[0:4].to(torch.complex128).contiguous()
+        u4 = torch.empty_like(g4)
+        for c in range(4):
+            p64.apply_raw(g4[c].data_ptr(), u4[c].data_ptr(), 1, stream.cuda_stream)
+        plan.apply_raw(g.data_ptr(), u.data_ptr(), nrhs, stream.cuda_stream)
+        torch.cuda.synchronize()
+        ucmp = u[0:4].to(torch.complex128)
+        err = float(torch.linalg.vector_norm(ucmp - u4) / torch.linalg.vector_norm(u4))
+        fp64 = {"value": 1e3 / t64, "unit": "vectors/s", "ms_per_vector": t64, "form": "explicit FP64, nrhs=1",
+                "rel_err_fp32_vs_fp64": err, "speedup": value / world / (1e3 / t64)}
+        p64.close()
+        del g64, u64, g4, u4
+
+    # ---- CPU oracle on the host cores (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not a.skip_cpu:
+        cores = os.cpu_count() or 1
+        v, dt = oracle_vectors_per_s(a, cores)
+        cpu = {"value": v, "unit": "vectors/s", "cores": cores, "kind": "oracle",
+               "sample": "1 of the %d vectors (full N=2^%d, matrix-free FP64 oracle, %.1f s)" % (
+                   nrhs, int(np.log2(N)), dt)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "vectors/s", "n_gpus": world, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": workload_name(a), "N": N, "r": r, "nrhs_per_gpu": nrhs, "phase": "FIO1D",
+                           "form": "structured, %d fused launches/apply" % launches,
+                           "l2": "inputs and workspace larger than L2 (no flush)",
+                           "parallelism": "independent rhs batches per GPU (dp%d)" % world},
+                "clocks": clk, "e2e": e2e, "gpu_launches": a.steps * launches, "roofline": roof,
+                "fp64_plain": fp64, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ibf", choices=["ibf", "reference"])
+    ap.add_argument("--N", type=int, default=1 << 20)
+    ap.add_argument("--r", type=int, default=9)
+    ap.add_argument("--nrhs", type=int, default=64)
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    a = ap.parse_args()
+    if a.warmup < 3 and a.impl == "ibf":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_gpu(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,197 @@
+/*
+ * ibf.h -- C ABI of the GB300 (sm_103a) interpolative butterfly factorization.
+ *
+ * The library builds and applies the preliminary interpolative butterfly
+ * factorization (IBF) of Li & Yang, arXiv 1605.03616, Sec. 3, of the
+ * complementary low-rank kernel K(x, xi) = exp(2 pi i Phi(x, xi)) on
+ *   X     = N points in [0,1)        (eq. X: x_j = j/N, or caller-given points),
+ *   Omega = {xi_k = k - N/2 : k = 0..N-1}  (eq. Omega),
+ * so that  u = K g  (eq. DFIO: u(x) = sum_{xi in Omega} K(x, xi) g(xi))  costs
+ * O(r^2 N log N) instead of O(N^2).  The factorization is
+ *   K ~ U^L G^{L-1} ... G^h M^h (H^h)^* ... (H^1)^* (V^0)^*       (Sec. 3)
+ * with L = log2 N levels, switch level h = floor(L/2), and r Chebyshev points
+ * per box (Sec. 2.1).  All computation happens in CUDA kernels on the current
+ * device; there is no CPU fallback.
+ *
+ * Conventions shared by every call:
+ *   - Return value: IBF_OK (0) or one of the IBF_ERR_* codes below.  No call
+ *     aborts the process.  ibf_get_last_error() returns a message for the last
+ *     failure of the calling thread.
+ *   - Complex vectors are interleaved (re, im).  Their element type follows the
+ *     plan's dtype: complex128 (two doubles) for IBF_C128, complex64 (two
+ *     floats) for IBF_C64_FP32 and IBF_C64_BF16X3.
+ *   - Multi-vector arguments are column-major: column c of an n x nrhs array
+ *     starts at element n*c.
+ *   - Streams are CUDA streams (cudaStream_t); NULL is the legacy default
+ *     stream.  Apply calls are asynchronous on that stream, allocate nothing
+ *     and do not synchronize the host.
+ */
+#ifndef IBF_GB300_H
+#define IBF_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream handle; identical to cudaStream_t. */
+typedef struct CUstream_st* ibf_stream_t;
+
+/* Opaque plan.  Owns all device memory of the factorization and the
+ * workspace used by the apply calls. */
+typedef struct ibf_plan ibf_plan;
+
+enum ibf_status {
+    IBF_OK = 0,
+    IBF_ERR_INVALID = 1,     /* bad argument (sizes, pointers, ids)             */
+    IBF_ERR_OOM = 2,         /* device allocation failed                         */
+    IBF_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed      */
+    IBF_ERR_UNSUPPORTED = 4, /* valid request this build does not implement      */
+    IBF_ERR_TIMEOUT = 5      /* a bounded device-side wait expired               */
+};
+
+/* Phase functions Phi(x, xi) (Assumption 1.1: homogeneous of degree 1 in xi). */
+enum ibf_phase {
+    IBF_PHASE_NUFFT = 0,        /* Phi = x . xi  (Sec. 6.1, eq. 1D-FT with K = e(+x xi))  */
+    IBF_PHASE_FIO1D = 1,        /* Phi = x xi + c(x)|xi|, c = (2 + sin 2 pi x)/8
+                                   (Sec. 6.2, eq. 1D-FIO-kernal)                       */
+    IBF_PHASE_FIO2D = 2,        /* Phi = x.xi + sqrt(c1^2 xi1^2 + c2^2 xi2^2), Sec. 6.3
+                                   (reserved: 2D plans return IBF_ERR_UNSUPPORTED)     */
+    IBF_PHASE_SEPARABLE = 100   /* test phase f(x) + h(xi), f = 0.75 sin 2 pi x,
+                                   h = 0.125|xi| + 0.3 sin(0.1 xi); the remainder
+                                   R^{AB} of eq. RAB vanishes, so the IBF is exact    */
+};
+
+/* Arithmetic of the apply. */
+enum ibf_dtype {
+    IBF_C128 = 0,       /* complex128 in and out, FP64 factors and FP64 arithmetic  */
+    IBF_C64_FP32 = 1,   /* complex64 in and out, FP32 factors, FP32 arithmetic      */
+    IBF_C64_BF16X3 = 2  /* complex64 in and out, three-term split-BF16 tensor-core
+                           products with FP32 accumulation                          */
+};
+
+/* Storage form of the factors. */
+enum ibf_form {
+    IBF_FORM_AUTO = 0,       /* EXPLICIT for IBF_C128, STRUCTURED otherwise             */
+    IBF_FORM_EXPLICIT = 1,   /* every r x r block of V^0, H^l, M^h, G^l, U^L stored
+                                as in Sec. 3; one kernel per level (the plain form)   */
+    IBF_FORM_STRUCTURED = 2  /* each butterfly block stored as diag * T_c * diag with
+                                the two universal real Lagrange transfer matrices T_c
+                                and the diagonal phases of adjacent levels merged;
+                                several levels fused per kernel                       */
+};
+
+/* Optional plan parameters; zero-initialise and set what you need. */
+typedef struct ibf_options {
+    int form;              /* enum ibf_form                                         */
+    int h;                 /* switch level in [1, L-1]; <= 0 means floor(L/2)        */
+    int max_nrhs;          /* columns of the apply workspace; larger nrhs is
+                              processed in slices of max_nrhs.  <= 0: 64 for the
+                              structured form, 8 for the explicit form.            */
+    int levels_per_launch; /* structured form: butterfly levels fused per kernel
+                              (1..10); <= 0 lets the autotuner choose              */
+    int rhs_tile;          /* structured form: right-hand sides per CTA (1..64,
+                              power of two); <= 0 lets the autotuner choose        */
+} ibf_options;
+
+/*
+ * ibf_plan_create -- build the preliminary IBF (Sec. 3) for the uniform grid
+ * X = {j/N} (eq. X) and Omega = {k - N/2} (eq. Omega).
+ *   phase_id : enum ibf_phase.
+ *   d        : dimension; only d = 1 is implemented (d = 2 returns
+ *              IBF_ERR_UNSUPPORTED).
+ *   N        : number of points, a power of two, 4 <= N <= 2^24.
+ *   r        : Chebyshev points per box (the paper's r_eps), 3 <= r <= 16;
+ *              the structured form supports r in {5, 7, 9, 11}.
+ *   dtype    : enum ibf_dtype.
+ *   out      : receives the plan; *out is NULL on failure.
+ * Construction evaluates every phase in FP64 on the current device and
+ * stream 0, and synchronizes before returning.  The caller owns the plan and
+ * frees it with ibf_plan_destroy.
+ */
+int ibf_plan_create(int phase_id, int d, int64_t N, int r, int dtype, ibf_plan** out);
+
+/*
+ * ibf_plan_create_ex -- as ibf_plan_create, with caller-given target points.
+ *   x   : host array of N doubles in [0,1) (the rows of K, in the caller's
+ *         order; they need not be sorted and a leaf box may hold any number of
+ *         them, Sec. 2.2), or NULL for the uniform grid.  Copied; the caller
+ *         keeps ownership.
+ *   opt : options, or NULL for the defaults.
+ */
+int ibf_plan_create_ex(int phase_id, int d, int64_t N, int r, int dtype, const double* x,
+                       const ibf_options* opt, ibf_plan** out);
+
+/*
+ * ibf_apply -- u = K g with the IBF factors (Sec. 3: V^0, H^1..H^h, M^h,
+ * G^h..G^{L-1}, U^L in that order).
+ *   g    : device array, N x nrhs column-major; column c holds g(xi_k) at
+ *          element k + N c, xi_k = k - N/2.
+ *   u    : device array, N x nrhs column-major, in the caller's x order.
+ *          Overwritten.  Must not overlap g.
+ *   nrhs : number of columns, >= 1.
+ * Both pointers must be aligned to their element size.  Asynchronous on
+ * `stream`; uses the plan's workspace, so calls on one plan must be ordered
+ * (same stream or explicit synchronisation).
+ */
+int ibf_apply(ibf_plan* plan, const void* g, void* u, int nrhs, ibf_stream_t stream);
+
+/*
+ * ibf_apply_adjoint -- g = K^* y, the conjugate-transposed factors in reverse
+ * order: V^0 H^1 ... H^h (M^h)^* (G^h)^* ... (G^{L-1})^* (U^L)^*.  The paper
+ * gives only the forward product (Sec. 3); this is its exact adjoint.
+ *   y : device array N x nrhs (rows in the caller's x order).
+ *   g : device array N x nrhs (rows xi_k).  Overwritten.
+ * Same layout, alignment and stream rules as ibf_apply.
+ */
+int ibf_apply_adjoint(ibf_plan* plan, const void* y, void* g, int nrhs, ibf_stream_t stream);
+
+/* Free the plan and all its device memory; NULL is accepted.  Synchronizes
+ * the device first. */
+int ibf_plan_destroy(ibf_plan* plan);
+
+/* Plan facts for measurement and bookkeeping. */
+enum ibf_query {
+    IBF_Q_N = 0,
+    IBF_Q_L = 1,
+    IBF_Q_H = 2,
+    IBF_Q_R = 3,
+    IBF_Q_DTYPE = 4,
+    IBF_Q_FORM = 5,
+    IBF_Q_FACTOR_BYTES = 6,    /* device bytes of all stored factors              */
+    IBF_Q_WORKSPACE_BYTES = 7, /* device bytes of the apply workspace             */
+    IBF_Q_MAX_NRHS = 8,
+    IBF_Q_NNZ = 9,             /* entries of the explicit factors (complex)       */
+    IBF_Q_LAUNCHES = 10,       /* kernels one apply of one slice launches         */
+    IBF_Q_LEVELS_PER_LAUNCH = 11,
+    IBF_Q_RHS_TILE = 12
+};
+int ibf_plan_query(const ibf_plan* plan, int what, int64_t* value);
+
+/*
+ * Per-launch timing for measurement tools.  ibf_plan_profile_begin(plan, cap)
+ * makes the following apply calls record a CUDA event on their stream before
+ * the first kernel and after every kernel, for up to `cap` kernels in total.
+ * ibf_plan_profile_end waits for those events, writes the duration of each
+ * recorded kernel in milliseconds to ms[] and its kind to kind[] (enum
+ * ibf_kernel_kind), at most `cap_out` entries, stores the number of recorded
+ * kernels in *count, and stops recording.  Recording adds two event records
+ * per kernel and no synchronisation to the apply calls.
+ */
+enum ibf_kernel_kind {
+    IBF_K_EXPLICIT_INIT = 0, IBF_K_EXPLICIT_LEVEL = 1, IBF_K_EXPLICIT_SWITCH = 2, IBF_K_EXPLICIT_TERM = 3,
+    IBF_K_FUSED_H = 4, IBF_K_FUSED_G = 5
+};
+int ibf_plan_profile_begin(ibf_plan* plan, int cap);
+int ibf_plan_profile_end(ibf_plan* plan, float* ms, int* kind, int cap_out, int* count);
+
+/* Copy the calling thread's last error message into buf (NUL-terminated,
+ * truncated to len).  Returns the last status code. */
+int ibf_get_last_error(char* buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IBF_GB300_H */

@@ -1,0 +1,212 @@
+"""GB300 (sm_103a) interpolative butterfly factorization -- Python binding.
+
+Thin ctypes binding of the C ABI in ``include/ibf.h`` (argument marshalling
+only: every step of construction and apply runs in the library's CUDA
+kernels).  PyTorch provides device memory and streams.
+
+    plan = Plan(PHASE_FIO1D, N=1 << 16, r=9, dtype=C64_FP32)
+    u = plan.apply(g)            # g: complex64 CUDA tensor (N,) or (N, nrhs)
+    gy = plan.adjoint(y)         # K^* y
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB as _LIB_PATH
+
+PHASE_NUFFT = 0
+PHASE_FIO1D = 1
+PHASE_FIO2D = 2
+PHASE_SEPARABLE = 100
+
+C128 = 0
+C64_FP32 = 1
+C64_BF16X3 = 2
+
+FORM_AUTO = 0
+FORM_EXPLICIT = 1
+FORM_STRUCTURED = 2
+
+Q_N, Q_L, Q_H, Q_R, Q_DTYPE, Q_FORM, Q_FACTOR_BYTES, Q_WORKSPACE_BYTES, Q_MAX_NRHS, Q_NNZ, Q_LAUNCHES, \
+    Q_LEVELS_PER_LAUNCH, Q_RHS_TILE = range(13)
+
+STATUS = {0: "IBF_OK", 1: "IBF_ERR_INVALID", 2: "IBF_ERR_OOM", 3: "IBF_ERR_CUDA", 4: "IBF_ERR_UNSUPPORTED",
+          5: "IBF_ERR_TIMEOUT"}
+
+# every symbol include/ibf.h declares
+EXPORTS = ("ibf_plan_create", "ibf_plan_create_ex", "ibf_apply", "ibf_apply_adjoint", "ibf_plan_destroy",
+           "ibf_plan_query", "ibf_get_last_error", "ibf_plan_profile_begin", "ibf_plan_profile_end")
+
+K_EXPLICIT_INIT, K_EXPLICIT_LEVEL, K_EXPLICIT_SWITCH, K_EXPLICIT_TERM, K_FUSED_H, K_FUSED_G = range(6)
+
+
+class IBFError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s: %s" % (STATUS.get(code, code), msg))
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("form", ctypes.c_int), ("h", ctypes.c_int), ("max_nrhs", ctypes.c_int),
+                ("levels_per_launch", ctypes.c_int), ("rhs_tile", ctypes.c_int)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load_library(path: str | None = None):
+    """Load the compiled library; raises if it has not been built."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or _LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError("IBF CUDA library not built (%s); run __graft_entry__.build()" % p)
+    L = ctypes.CDLL(p)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    I64 = ctypes.c_int64
+    L.ibf_plan_create.argtypes = [I, I, I64, I, I, ctypes.POINTER(P)]
+    L.ibf_plan_create_ex.argtypes = [I, I, I64, I, I, P, ctypes.POINTER(Options), ctypes.POINTER(P)]
+    L.ibf_apply.argtypes = [P, P, P, I, P]
+    L.ibf_apply_adjoint.argtypes = [P, P, P, I, P]
+    L.ibf_plan_destroy.argtypes = [P]
+    L.ibf_plan_query.argtypes = [P, I, ctypes.POINTER(I64)]
+    L.ibf_get_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
+    L.ibf_plan_profile_begin.argtypes = [P, I]
+    L.ibf_plan_profile_end.argtypes = [P, P, P, I, ctypes.POINTER(I)]
+    for nm in EXPORTS:
+        getattr(L, nm).restype = I
+    if path is None:
+        _lib = L
+    return L
+
+
+def last_error() -> str:
+    buf = ctypes.create_string_buffer(512)
+    load_library().ibf_get_last_error(buf, 512)
+    return buf.value.decode()
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise IBFError(rc, last_error())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Plan:
+    """An IBF plan (include/ibf.h: ibf_plan_create_ex / ibf_plan_destroy)."""
+
+    def __init__(self, phase: int, N: int, r: int = 9, dtype: int = C64_FP32, x=None, d: int = 1,
+                 form: int = FORM_AUTO, h: int = 0, max_nrhs: int = 0, levels_per_launch: int = 0,
+                 rhs_tile: int = 0):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("the IBF library runs on a CUDA GPU only; none is available")
+        torch.cuda.init()
+        self._lib = load_library()
+        self.N, self.r, self.dtype, self.phase = int(N), int(r), int(dtype), int(phase)
+        opt = Options(form, h, max_nrhs, levels_per_launch, rhs_tile)
+        xa = None
+        if x is not None:
+            xa = np.ascontiguousarray(x, dtype=np.float64)
+            if xa.size != N * d:
+                raise ValueError("x must hold N*d doubles")
+        out = ctypes.c_void_p()
+        with torch.cuda.device(torch.cuda.current_device()):
+            _check(self._lib.ibf_plan_create_ex(self.phase, d, self.N, self.r, self.dtype,
+                                                xa.ctypes.data_as(ctypes.c_void_p) if xa is not None else None,
+                                                ctypes.byref(opt), ctypes.byref(out)))
+        self._p = out
+        self.cdtype = torch.complex128 if self.dtype == C128 else torch.complex64
+
+    def close(self):
+        if getattr(self, "_p", None):
+            self._lib.ibf_plan_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def query(self, what: int) -> int:
+        v = ctypes.c_int64()
+        _check(self._lib.ibf_plan_query(self._p, what, ctypes.byref(v)))
+        return v.value
+
+    @property
+    def L(self) -> int:
+        return self.query(Q_L)
+
+    @property
+    def h(self) -> int:
+        return self.query(Q_H)
+
+    def _prep(self, v):
+        torch = _torch()
+        if not isinstance(v, torch.Tensor) or not v.is_cuda:
+            raise TypeError("expected a CUDA tensor")
+        if v.dtype != self.cdtype:
+            raise TypeError("expected %s, got %s" % (self.cdtype, v.dtype))
+        if v.shape[0] != self.N or v.dim() not in (1, 2):
+            raise ValueError("expected shape (N,) or (N, nrhs)")
+        nrhs = 1 if v.dim() == 1 else v.shape[1]
+        # column-major N x nrhs == row-major (nrhs, N)
+        colmajor = v.reshape(self.N, nrhs).t().contiguous()
+        return colmajor, nrhs
+
+    def _run(self, fn, v, out, stream):
+        torch = _torch()
+        src, nrhs = self._prep(v)
+        dst = torch.empty((nrhs, self.N), dtype=self.cdtype, device=v.device) if out is None else out
+        if dst.shape != (nrhs, self.N) or not dst.is_contiguous():
+            raise ValueError("out must be a contiguous (nrhs, N) tensor")
+        s = (stream or torch.cuda.current_stream(v.device)).cuda_stream
+        _check(fn(self._p, ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()), nrhs,
+                  ctypes.c_void_p(s)))
+        res = dst.t()
+        return res[:, 0] if v.dim() == 1 else res
+
+    def apply(self, g, out=None, stream=None):
+        """u = K g (ibf_apply)."""
+        return self._run(self._lib.ibf_apply, g, out, stream)
+
+    def adjoint(self, y, out=None, stream=None):
+        """g = K^* y (ibf_apply_adjoint)."""
+        return self._run(self._lib.ibf_apply_adjoint, y, out, stream)
+
+    def profile_begin(self, cap: int) -> None:
+        """Record per-kernel CUDA events for the next `cap` kernels."""
+        _check(self._lib.ibf_plan_profile_begin(self._p, cap))
+
+    def profile_end(self, cap: int = 1 << 16):
+        """-> list of (kernel kind, milliseconds) recorded since profile_begin."""
+        ms = np.zeros(cap, np.float32)
+        kind = np.zeros(cap, np.int32)
+        n = ctypes.c_int()
+        _check(self._lib.ibf_plan_profile_end(self._p, ms.ctypes.data_as(ctypes.c_void_p),
+                                              kind.ctypes.data_as(ctypes.c_void_p), cap, ctypes.byref(n)))
+        m = min(n.value, cap)
+        return list(zip(kind[:m].tolist(), ms[:m].tolist()))
+
+    def apply_raw(self, g_ptr: int, u_ptr: int, nrhs: int, stream_ptr: int = 0) -> None:
+        """Pointer-level ibf_apply for callers that manage their own buffers."""
+        _check(self._lib.ibf_apply(self._p, ctypes.c_void_p(g_ptr), ctypes.c_void_p(u_ptr), nrhs,
+                                   ctypes.c_void_p(stream_ptr)))
+
+    def adjoint_raw(self, y_ptr: int, g_ptr: int, nrhs: int, stream_ptr: int = 0) -> None:
+        _check(self._lib.ibf_apply_adjoint(self._p, ctypes.c_void_p(y_ptr), ctypes.c_void_p(g_ptr), nrhs,
+                                           ctypes.c_void_p(stream_ptr)))

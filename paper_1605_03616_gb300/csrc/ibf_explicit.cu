@@ -1,0 +1,202 @@
+// Explicit-form apply of the preliminary IBF (Sec. 3), FP64: the plain form.
+//
+// u = U^L G^{L-1} ... G^h M^h (H^h)^* ... (H^1)^* (V^0)^* g, one kernel per
+// factor.  Lambda^l_{i,j} (r complex per box pair and right-hand side) is kept
+// in i-major pair order p = i 2^(L-l) + j at every level, element
+// (p r + t) nc + col, so the switch's reordering (Sec. 3, step 4) is only a
+// change of index arithmetic.  Each butterfly block maps
+// Lambda^{l-1}_{i/2, 2j+c} to Lambda^l_{i,j} (eqs. PIBF2, PIBF3).
+#include <algorithm>
+
+#include "ibf_internal.h"
+
+namespace ibf {
+
+typedef double2 cd;
+
+__device__ __forceinline__ cd cmul(cd a, cd b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ cd cmulc(cd a, cd b)  // conj(a) * b
+{
+    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ void cadd(cd& a, cd b) { a.x += b.x; a.y += b.y; }
+
+// Lambda^0[k][t][col] = V[k][t] g[k + N col]       ((V^0)^* g, eq. step2mv1)
+__global__ void kx_init(const cd* V, const cd* g, cd* lam, int64_t N, int r, int nc)
+{
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= N * r * nc) return;
+    int col = (int)(e % nc);
+    int t = (int)((e / nc) % r);
+    int64_t k = e / ((int64_t)nc * r);
+    lam[e] = cmul(V[k * r + t], g[k + N * col]);
+}
+
+// g[k + N col] = sum_t conj(V[k][t]) Lambda^0[k][t][col]
+__global__ void kx_init_adj(const cd* V, const cd* lam, cd* g, int64_t N, int r, int nc)
+{
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= N * nc) return;
+    int64_t k = e % N;
+    int col = (int)(e / N);
+    cd acc = make_double2(0, 0);
+    for (int t = 0; t < r; ++t) cadd(acc, cmulc(V[k * r + t], lam[(k * r + t) * nc + col]));
+    g[k + N * col] = acc;
+}
+
+// one butterfly level l: out pair p = (i,j) from in pairs (i/2, 2j+c)
+__global__ void kx_level(const cd* blk, const cd* in, cd* out, int L, int l, int r, int nc, int64_t N)
+{
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= N * r * nc) return;
+    int col = (int)(e % nc);
+    int t = (int)((e / nc) % r);
+    int64_t p = e / ((int64_t)nc * r);
+    int64_t nj = 1LL << (L - l);
+    int64_t i = p >> (L - l), j = p & (nj - 1);
+    int64_t q0 = (i >> 1) * (2 * nj) + 2 * j;
+    cd acc = make_double2(0, 0);
+    for (int c = 0; c < 2; ++c) {
+        const cd* row = blk + ((p * 2 + c) * r + t) * r;
+        const cd* v = in + (q0 + c) * r * nc + col;
+        for (int s = 0; s < r; ++s) cadd(acc, cmul(row[s], v[(int64_t)s * nc]));
+    }
+    out[e] = acc;
+}
+
+// adjoint of level l: in pair q = (i', C) at level l-1 gathers from the two
+// out pairs (2i'+a, C/2) at level l with the conjugated blocks
+__global__ void kx_level_adj(const cd* blk, const cd* out, cd* in, int L, int l, int r, int nc, int64_t N)
+{
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= N * r * nc) return;
+    int col = (int)(e % nc);
+    int s = (int)((e / nc) % r);
+    int64_t q = e / ((int64_t)nc * r);
+    int64_t nC = 1LL << (L - l + 1), nj = nC >> 1;
+    int64_t ip = q >> (L - l + 1), C = q & (nC - 1);
+    int64_t j = C >> 1;
+    int c = (int)(C & 1);
+    cd acc = make_double2(0, 0);
+    for (int a = 0; a < 2; ++a) {
+        int64_t p = (2 * ip + a) * nj + j;
+        const cd* col_blk = blk + ((p * 2 + c) * r) * r + s;
+        const cd* v = out + p * r * nc + col;
+        for (int t = 0; t < r; ++t) cadd(acc, cmulc(col_blk[(int64_t)t * r], v[(int64_t)t * nc]));
+    }
+    in[e] = acc;
+}
+
+// switch at level h: out_p = M~_p in_p (eq. switchlocM), or its adjoint
+__global__ void kx_switch(const cd* M, const cd* in, cd* out, int r, int nc, int64_t N, int adj)
+{
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= N * r * nc) return;
+    int col = (int)(e % nc);
+    int t = (int)((e / nc) % r);
+    int64_t p = e / ((int64_t)nc * r);
+    const cd* Mp = M + p * r * r;
+    const cd* v = in + p * r * nc + col;
+    cd acc = make_double2(0, 0);
+    if (!adj)
+        for (int s = 0; s < r; ++s) cadd(acc, cmul(Mp[t * r + s], v[(int64_t)s * nc]));
+    else
+        for (int s = 0; s < r; ++s) cadd(acc, cmulc(Mp[s * r + t], v[(int64_t)s * nc]));
+    out[e] = acc;
+}
+
+// u[perm[n] + nx col] = sum_t U[n][t] Lambda^L[leaf(n)][t][col]   (eq. PIBFbf3)
+__global__ void kx_term(const cd* U, const int32_t* leaf, const int32_t* perm, const cd* lam, cd* u, int64_t nx,
+                        int r, int nc)
+{
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= nx * nc) return;
+    int64_t n = e % nx;
+    int col = (int)(e / nx);
+    const cd* v = lam + (int64_t)leaf[n] * r * nc + col;
+    cd acc = make_double2(0, 0);
+    for (int t = 0; t < r; ++t) cadd(acc, cmul(U[n * r + t], v[(int64_t)t * nc]));
+    u[perm[n] + nx * col] = acc;
+}
+
+// Lambda^L[i][t][col] = sum_{n in leaf i} conj(U[n][t]) y[perm[n] + nx col]
+__global__ void kx_term_adj(const cd* U, const int32_t* off, const int32_t* perm, const cd* y, cd* lam, int64_t N,
+                            int64_t nx, int r, int nc)
+{
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= N * r * nc) return;
+    int col = (int)(e % nc);
+    int t = (int)((e / nc) % r);
+    int64_t i = e / ((int64_t)nc * r);
+    cd acc = make_double2(0, 0);
+    for (int32_t n = off[i]; n < off[i + 1]; ++n) cadd(acc, cmulc(U[(int64_t)n * r + t], y[perm[n] + nx * col]));
+    lam[e] = acc;
+}
+
+static inline unsigned nb(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+int explicit_launches(const ibf_plan* p) { return p->L + 3; }
+
+int explicit_apply(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStream_t st)
+{
+    const int r = p->r, L = p->L;
+    const int64_t N = p->N;
+    for (int c0 = 0; c0 < nrhs; c0 += p->max_nrhs) {
+        int nc = std::min(p->max_nrhs, nrhs - c0);
+        const cd* g = (const cd*)gv + N * c0;
+        cd* u = (cd*)uv + p->nx * c0;
+        cd* a = (cd*)p->ws[0];
+        cd* b = (cd*)p->ws[1];
+        int64_t tot = N * r * nc;
+        prof_start(p, st);
+        kx_init<<<nb(tot), 256, 0, st>>>((const cd*)p->eV, g, a, N, r, nc);
+        prof_mark(p, st, IBF_K_EXPLICIT_INIT);
+        for (int l = 1; l <= L; ++l) {
+            kx_level<<<nb(tot), 256, 0, st>>>((const cd*)p->eblk[l], a, b, L, l, r, nc, N);
+            prof_mark(p, st, IBF_K_EXPLICIT_LEVEL);
+            std::swap(a, b);
+            if (l == p->h) {
+                kx_switch<<<nb(tot), 256, 0, st>>>((const cd*)p->eM, a, b, r, nc, N, 0);
+                prof_mark(p, st, IBF_K_EXPLICIT_SWITCH);
+                std::swap(a, b);
+            }
+        }
+        kx_term<<<nb(p->nx * nc), 256, 0, st>>>((const cd*)p->eU, p->d_leaf, p->d_perm, a, u, p->nx, r, nc);
+        prof_mark(p, st, IBF_K_EXPLICIT_TERM);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? IBF_OK : cuda_error(e, "explicit apply launch");
+}
+
+int explicit_adjoint(ibf_plan* p, const void* yv, void* gv, int nrhs, cudaStream_t st)
+{
+    const int r = p->r, L = p->L;
+    const int64_t N = p->N;
+    for (int c0 = 0; c0 < nrhs; c0 += p->max_nrhs) {
+        int nc = std::min(p->max_nrhs, nrhs - c0);
+        const cd* y = (const cd*)yv + p->nx * c0;
+        cd* g = (cd*)gv + N * c0;
+        cd* a = (cd*)p->ws[0];
+        cd* b = (cd*)p->ws[1];
+        int64_t tot = N * r * nc;
+        prof_start(p, st);
+        kx_term_adj<<<nb(tot), 256, 0, st>>>((const cd*)p->eU, p->d_off, p->d_perm, y, a, N, p->nx, r, nc);
+        prof_mark(p, st, IBF_K_EXPLICIT_TERM);
+        for (int l = L; l >= 1; --l) {
+            if (l == p->h) {
+                kx_switch<<<nb(tot), 256, 0, st>>>((const cd*)p->eM, a, b, r, nc, N, 1);
+                prof_mark(p, st, IBF_K_EXPLICIT_SWITCH);
+                std::swap(a, b);
+            }
+            kx_level_adj<<<nb(tot), 256, 0, st>>>((const cd*)p->eblk[l], a, b, L, l, r, nc, N);
+            prof_mark(p, st, IBF_K_EXPLICIT_LEVEL);
+            std::swap(a, b);
+        }
+        kx_init_adj<<<nb(N * nc), 256, 0, st>>>((const cd*)p->eV, a, g, N, r, nc);
+        prof_mark(p, st, IBF_K_EXPLICIT_INIT);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? IBF_OK : cuda_error(e, "explicit adjoint launch");
+}
+
+}  // namespace ibf

@@ -1,0 +1,11 @@
+// FP64 instantiation of the structured fused apply.
+#include "ibf_fused.cuh"
+
+namespace ibf {
+
+int fused_apply_f64(ibf_plan* p, const void* vin, void* vout, int nrhs, bool adj, cudaStream_t st)
+{
+    return fused_apply_t<double>(p, vin, vout, nrhs, adj, st);
+}
+
+}  // namespace ibf

@@ -1,0 +1,97 @@
+// Internal declarations shared by the translation units of the IBF library.
+// The public C ABI is include/ibf.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ibf.h"
+
+namespace ibf {
+
+constexpr int kMaxR = 16;       // Chebyshev points per box
+constexpr int kMaxFuse = 10;    // butterfly levels fused in one structured kernel
+
+// Host-side record of the last error of the calling thread.
+int set_error(int code, const std::string& msg);
+int cuda_error(cudaError_t e, const char* what);
+
+}  // namespace ibf
+
+struct ibf_plan {
+    int phase_id = 0, d = 1, r = 0, dtype = 0, form = 0;
+    int L = 0, h = 0;
+    int64_t N = 0, nx = 0;
+    int max_nrhs = 0;
+    int kfuse = 0, rtile = 0;   // structured form launch shape
+    bool user_kfuse = false, user_rtile = false;
+
+    // Chebyshev grid on [-1/2,1/2] and the two child-to-parent Lagrange
+    // transfer matrices T_c[t][s] = M_t((2c-1)/4 + z_s/2)   (Sec. 2.1)
+    double z[ibf::kMaxR];
+    double T[2][ibf::kMaxR][ibf::kMaxR];
+
+    // target points, sorted by leaf; perm[n] = caller index of sorted point n;
+    // off[i]..off[i+1] = sorted points in leaf i (N+1 entries)
+    double* d_x = nullptr;
+    int32_t* d_perm = nullptr;
+    int32_t* d_off = nullptr;
+    int32_t* d_leaf = nullptr;
+
+    // explicit form (complex128): V[k][t], blk[l][p][c][t][s], M[p][t][s], U[n][t]
+    void* eV = nullptr;
+    void* eM = nullptr;
+    void* eU = nullptr;
+    std::vector<void*> eblk;   // index 1..L
+
+    // structured form (complex of the apply precision):
+    //   sV[k][t]         = M_t((xi_k - c_B)/w_B) e(Phi(c_root, xi_k))
+    //   stab[l][i][C][s] = e(Phi(c_{A^l_i}, g_s) - Phi(c_{A^{l-1}_{i/2}}, g_s)),  l <= h
+    //   stab[l][i][C][t] = e(Phi(g^{A^l_i}_t, c_C) - Phi(g^{A^l_i}_t, c_{parent(C)})), l > h
+    //   sM[p][t][s]      = the switch block with both neighbouring diagonals merged
+    //   sU[n][t]         = e(Phi(x_n, 0)) M_t((x_n - c_A)/w_A)
+    void* sV = nullptr;
+    void* sM = nullptr;
+    void* sU = nullptr;
+    std::vector<void*> stab;   // index 1..L
+
+    // BF16x3 tensor-core form: split transfer matrices (device)
+    void* tc_T = nullptr;
+
+    void* ws[2] = {nullptr, nullptr};   // apply workspace (ping-pong Lambda buffers)
+    size_t factor_bytes = 0, ws_bytes = 0;
+    int64_t nnz = 0;
+    std::vector<void*> allocations;
+
+    // optional per-launch timing (ibf_plan_profile_begin/end): kernel n ran
+    // between events prof_a[n] and prof_b[n]
+    int prof_cap = 0, prof_n = 0, prof_nev = 0, prof_last = -1;
+    std::vector<cudaEvent_t> prof_ev;
+    std::vector<int> prof_a, prof_b, prof_kind;
+};
+
+namespace ibf {
+
+// per-launch timing helpers (no-ops unless profiling is on)
+void prof_start(ibf_plan* p, cudaStream_t s);
+void prof_mark(ibf_plan* p, cudaStream_t s, int kind);
+
+// construction (ibf_plan.cu)
+int build_explicit(ibf_plan* p);
+int build_structured(ibf_plan* p);
+
+// explicit-form apply (ibf_explicit.cu), FP64
+int explicit_apply(ibf_plan* p, const void* g, void* u, int nrhs, cudaStream_t s);
+int explicit_adjoint(ibf_plan* p, const void* y, void* g, int nrhs, cudaStream_t s);
+int explicit_launches(const ibf_plan* p);
+
+// structured-form apply (ibf_fused.cu), FP32 or FP64
+int fused_apply(ibf_plan* p, const void* g, void* u, int nrhs, bool adjoint, cudaStream_t s);
+int fused_launches(const ibf_plan* p);
+bool fused_supports_r(int r);
+void fused_choose_shape(ibf_plan* p);
+
+}  // namespace ibf

@@ -1,0 +1,66 @@
+"""CPU-side checks of the C ABI library: it builds, loads, exports every
+symbol include/ibf.h declares, and rejects bad arguments before touching the
+GPU.  No compute call is made here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1605_03616_gb300 import build as B
+    import paper_1605_03616_gb300 as ibf
+    B.build()
+    return ibf.load_library()
+
+
+def declared_symbols():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            names += re.findall(r"^\s*int\s+(ibf_\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert "ibf_apply" in names and "ibf_plan_create" in names
+    for nm in names:
+        assert hasattr(lib, nm), nm
+
+
+def test_python_binding_lists_every_symbol():
+    import paper_1605_03616_gb300 as ibf
+    assert set(declared_symbols()) <= set(ibf.EXPORTS) | set(getattr(ibf, "EXTRA_EXPORTS", ()))
+
+
+def _create(lib, phase=1, d=1, N=1024, r=9, dtype=1):
+    out = ctypes.c_void_p()
+    rc = lib.ibf_plan_create(phase, d, N, r, dtype, ctypes.byref(out))
+    return rc, out
+
+
+def test_argument_validation_without_gpu(lib):
+    import paper_1605_03616_gb300 as ibf
+    assert _create(lib, N=1000)[0] == 1           # not a power of two
+    assert _create(lib, N=2)[0] == 1              # too small
+    assert _create(lib, r=2)[0] == 1
+    assert _create(lib, r=17)[0] == 1
+    assert _create(lib, phase=7)[0] == 1
+    assert _create(lib, d=3)[0] == 1
+    assert _create(lib, dtype=9)[0] == 1
+    assert _create(lib, d=2)[0] == 4              # 2D not implemented: unsupported
+    assert _create(lib, r=6)[0] == 4              # structured form: r in {5,7,9,11}
+    assert "r" in ibf.last_error()
+    assert lib.ibf_plan_create(1, 1, 1024, 9, 1, None) == 1
+    # NULL plan and NULL pointers are rejected before any CUDA call
+    assert lib.ibf_apply(None, None, None, 1, None) == 1
+    assert lib.ibf_apply_adjoint(None, None, None, 1, None) == 1
+    assert lib.ibf_plan_destroy(None) == 0
+    v = ctypes.c_int64()
+    assert lib.ibf_plan_query(None, 0, ctypes.byref(v)) == 1
