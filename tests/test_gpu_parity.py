@@ -1,7 +1,13 @@
 """GPU parity of the CUDA IBF against the FP64 oracle (element by element).
 
 Tolerances (relative L2 over all outputs):
-* FP64 explicit form vs the oracle's IBF: 1e-12.
+* FP64 explicit form vs the oracle's IBF: 1e-12, or for the 1D FIO phase
+  the conditioning floor fp64_floor(N) if that is larger.  The FIO phase
+  contains c(x)|xi| with c = (2 + sin 2 pi x)/8; the CUDA and libm sines may
+  differ by up to 2 ulp, so c differs by up to 2^-52/8 and the phase by up
+  to |xi| 2^-55 <= N 2^-56.  A phase error d moves a unit-modulus factor by
+  2 pi d, so the relative result error is bounded by about 2 pi N 2^-56;
+  we allow 4x that (N = 2^14: 5.6e-12; N <= 2^12 stays at 1e-12).
 * FP64 structured form: 1e-11.  It uses the universal transfer matrices
   T_c (exact child offsets) where the paper's formula evaluates the Lagrange
   weight at the rounded grid point c_C + w_C z_s; for Omega boxes far from
@@ -34,6 +40,12 @@ def _dev(a, dt):
     return torch.from_numpy(np.ascontiguousarray(a).astype(dt)).cuda()
 
 
+def fp64_floor(phase, N):
+    if phase != O.PHASE_FIO1D:
+        return 1e-12
+    return max(1e-12, 4 * 2 * np.pi * N * 2.0 ** -56)
+
+
 def _x(phase, N, seed):
     return W.random_sorted_x(N, W.rng(seed)) if phase == O.PHASE_NUFFT else W.uniform_x(N)
 
@@ -60,8 +72,11 @@ def test_fp64_explicit_matches_oracle(ibf, phase, N, r, nrhs):
     ga = plan.adjoint(_dev(y, np.complex128)).cpu().numpy()
     ref = O.ibf_apply_1d(phase, N, r, x, g)
     refa = O.ibf_adjoint_1d(phase, N, r, x, y)
-    assert O.rel_l2(u, ref) < 1e-12
-    assert O.rel_l2(ga, refa) < 1e-12
+    tol = fp64_floor(phase, N)
+    print("\nparity fp64-explicit phase=%d N=%d r=%d nrhs=%d fwd %.3e adj %.3e tol %.1e" % (
+        phase, N, r, nrhs, O.rel_l2(u, ref), O.rel_l2(ga, refa), tol))
+    assert O.rel_l2(u, ref) < tol
+    assert O.rel_l2(ga, refa) < tol
 
 
 @pytest.mark.parametrize("phase,N,r,nrhs", CASES_64)
@@ -74,8 +89,12 @@ def test_fp64_structured_matches_oracle(ibf, phase, N, r, nrhs):
     plan = ibf.Plan(phase, N, r, ibf.C128, x=None if phase != O.PHASE_NUFFT else x, form=ibf.FORM_STRUCTURED)
     u = plan.apply(_dev(g, np.complex128)).cpu().numpy()
     ga = plan.adjoint(_dev(y, np.complex128)).cpu().numpy()
-    assert O.rel_l2(u, O.ibf_apply_1d(phase, N, r, x, g)) < 1e-11
-    assert O.rel_l2(ga, O.ibf_adjoint_1d(phase, N, r, x, y)) < 1e-11
+    tol = max(1e-11, fp64_floor(phase, N))
+    ef, ea = O.rel_l2(u, O.ibf_apply_1d(phase, N, r, x, g)), O.rel_l2(ga, O.ibf_adjoint_1d(phase, N, r, x, y))
+    print("\nparity fp64-structured phase=%d N=%d r=%d nrhs=%d fwd %.3e adj %.3e tol %.1e" % (
+        phase, N, r, nrhs, ef, ea, tol))
+    assert ef < tol
+    assert ea < tol
 
 
 @pytest.mark.parametrize("phase,N,r,nrhs,kw", [
@@ -94,8 +113,11 @@ def test_fp32_structured_matches_oracle(ibf, phase, N, r, nrhs, kw):
     plan = ibf.Plan(phase, N, r, ibf.C64_FP32, x=None if phase != O.PHASE_NUFFT else x, **kw)
     u = plan.apply(_dev(g, np.complex64)).cpu().numpy()
     ga = plan.adjoint(_dev(y, np.complex64)).cpu().numpy()
-    assert O.rel_l2(u, O.ibf_apply_1d(phase, N, r, x, g)) < 1e-5
-    assert O.rel_l2(ga, O.ibf_adjoint_1d(phase, N, r, x, y)) < 1e-5
+    ef, ea = O.rel_l2(u, O.ibf_apply_1d(phase, N, r, x, g)), O.rel_l2(ga, O.ibf_adjoint_1d(phase, N, r, x, y))
+    print("\nparity fp32-structured phase=%d N=%d r=%d nrhs=%d %s fwd %.3e adj %.3e" % (
+        phase, N, r, nrhs, kw, ef, ea))
+    assert ef < 1e-5
+    assert ea < 1e-5
 
 
 def test_unsorted_points_follow_caller_order(ibf):
