@@ -148,6 +148,33 @@ int ibf_apply(ibf_plan* plan, const void* g, void* u, int nrhs, ibf_stream_t str
  */
 int ibf_apply_adjoint(ibf_plan* plan, const void* y, void* g, int nrhs, ibf_stream_t stream);
 
+/*
+ * ibf_apply_static_scratch -- u = K g like ibf_apply, for callers that may
+ * not allocate device memory once their plans exist (for example a plug-in
+ * whose host application owns the device heap and forbids further cudaMalloc
+ * calls, or a server whose memory budget was fixed when its plans were
+ * built).  The paper has no counterpart: this is an operational variant of
+ * the structured-form apply.
+ *
+ * It allocates nothing.  Its two Lambda buffers live in one file-scope
+ * device array of 256 MiB (two halves of 128 MiB) that every GPU loading the
+ * library holds until the process exits; the plan's own workspace is not
+ * used, so a plan created with max_nrhs = 1 still applies many columns per
+ * launch here.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Every call shares the array and it keeps
+ * the last call's contents; no part of it needs to start at zero because each
+ * launch writes every element the next launch reads.  Calls that overlap on
+ * the GPU (other streams, or other threads) race on the array: order them.
+ *   plan : a structured-form plan (IBF_FORM_STRUCTURED); otherwise
+ *          IBF_ERR_UNSUPPORTED.
+ *   g, u, nrhs, stream : as ibf_apply.
+ * Size limit: N * r * (element size) must not exceed 128 MiB (one Lambda
+ * column per half), else IBF_ERR_INVALID with a message naming the limit;
+ * e.g. complex64 with r = 9 allows N <= 2^20, complex128 N <= 2^19.
+ */
+int ibf_apply_static_scratch(const ibf_plan* plan, const void* g, void* u, int nrhs, ibf_stream_t stream);
+
 /* Free the plan and all its device memory; NULL is accepted.  Synchronizes
  * the device first. */
 int ibf_plan_destroy(ibf_plan* plan);

@@ -38,7 +38,8 @@ STATUS = {0: "IBF_OK", 1: "IBF_ERR_INVALID", 2: "IBF_ERR_OOM", 3: "IBF_ERR_CUDA"
 
 # every symbol include/ibf.h declares
 EXPORTS = ("ibf_plan_create", "ibf_plan_create_ex", "ibf_apply", "ibf_apply_adjoint", "ibf_plan_destroy",
-           "ibf_plan_query", "ibf_get_last_error", "ibf_plan_profile_begin", "ibf_plan_profile_end")
+           "ibf_plan_query", "ibf_get_last_error", "ibf_plan_profile_begin", "ibf_plan_profile_end",
+           "ibf_apply_static_scratch")
 
 K_EXPLICIT_INIT, K_EXPLICIT_LEVEL, K_EXPLICIT_SWITCH, K_EXPLICIT_TERM, K_FUSED_H, K_FUSED_G = range(6)
 
@@ -80,6 +81,7 @@ def load_library(path: str | None = None):
     L.ibf_plan_destroy.argtypes = [P]
     L.ibf_plan_query.argtypes = [P, I, ctypes.POINTER(I64)]
     L.ibf_get_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
+    L.ibf_apply_static_scratch.argtypes = [P, P, P, I, P]
     L.ibf_plan_profile_begin.argtypes = [P, I]
     L.ibf_plan_profile_end.argtypes = [P, P, P, I, ctypes.POINTER(I)]
     for nm in EXPORTS:

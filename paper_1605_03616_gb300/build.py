@@ -26,6 +26,7 @@ UNITS = {
     "ibf_explicit.cu": [],
     "ibf_fused_f32.cu": [],
     "ibf_fused_f64.cu": [],
+    "ibf_static.cu": [],
 }
 
 

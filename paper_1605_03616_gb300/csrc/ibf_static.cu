@@ -1,0 +1,148 @@
+// ibf_apply_static_scratch: the structured-form apply with its scratch in a
+// fixed, library-owned device array instead of the plan's workspace.
+//
+// Why: some callers may not allocate device memory once their plans exist --
+// for example a plug-in inside a host application that owns the device heap
+// and forbids further cudaMalloc calls, or a server whose memory budget was
+// fixed when the plans were built.  Such a caller can create its plans with
+// max_nrhs = 1 (the smallest workspace a plan owns) and still apply many
+// right-hand sides per launch through this entry point, which allocates
+// nothing: its two Lambda buffers live in the static array below.
+//
+// The array is a file-scope __device__ variable: every GPU that loads this
+// library holds its kStaticScratchBytes until the process exits.  Host code
+// must not pass the symbol itself to a kernel (on the host it names a
+// stand-in, not device memory); the device address is looked up once per
+// device with cudaGetSymbolAddress and cached.
+#include <mutex>
+
+#include "ibf_fused.cuh"
+
+namespace ibf {
+
+// 256 MiB: two Lambda buffers of 128 MiB each.
+constexpr size_t kStaticScratchBytes = size_t(256) << 20;
+constexpr size_t kStaticHalf = kStaticScratchBytes / 2;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+static std::mutex g_static_mu;
+static void* g_static_addr[64] = {nullptr};
+
+// Device address of g_static_scratch on the current device (set-up on the
+// first call per device).
+static int static_scratch_address(void** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return set_error(IBF_ERR_UNSUPPORTED, "device index >= 64");
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(static scratch)");
+        g_static_addr[dev] = ptr;
+    }
+    *out = g_static_addr[dev];
+    return IBF_OK;
+}
+
+// The fused forward schedule of fused_run with caller-chosen Lambda buffers.
+template <typename Real, int RP>
+static int static_run(const ibf_plan* p, const void* vin, void* vout, int nrhs, cudaStream_t st, void* buf0,
+                      void* buf1, int max_cols)
+{
+    typedef typename CT<Real>::T cx;
+    FusedParams<Real, RP> P;
+    memset(&P, 0, sizeof(P));
+    for (int c = 0; c < 2; ++c)
+        for (int t = 0; t < RP; ++t)
+            for (int s = 0; s < RP; ++s) P.T[c][t][s] = (Real)p->T[c][t][s];
+    P.Vs = p->sV;
+    P.Us = p->sU;
+    P.Ms = p->sM;
+    P.perm = p->d_perm;
+    P.off = p->d_off;
+    P.N = p->N;
+    P.L = p->L;
+    const int64_t N = p->N;
+    for (int c0 = 0; c0 < nrhs; c0 += max_cols) {
+        const int nc = std::min(max_cols, nrhs - c0);
+        const int rt = std::min(32, pow2ceil(nc));
+        const int budget = FusedTraits<Real>::kPairCols;
+        int kmax = 0;
+        while (kmax < kMaxFuse && (2 << kmax) * rt <= budget) ++kmax;
+        kmax = std::max(1, kmax);
+        std::vector<Chunk> sched = fused_schedule(p->L, p->h, kmax);
+        P.nc = nc;
+        P.rt = rt;
+        P.vin = (const cx*)vin + N * c0;
+        P.vout = (cx*)vout + N * c0;
+        void* bufs[2] = {buf0, buf1};
+        int cur = 0;
+        for (const Chunk& ch : sched) {
+            P.l0 = ch.lo;
+            P.k = ch.hi - ch.lo;
+            for (int s = 1; s <= P.k; ++s) P.D[s - 1] = p->stab[ch.lo + s];
+            for (int s = P.k; s < kMaxFuse; ++s) P.D[s] = nullptr;
+            P.pro = ch.lo == 0 ? PRO_V : PRO_LAMBDA;
+            P.epi = ch.hi == p->L ? EPI_U : (ch.hi == p->h ? EPI_SWITCH : EPI_LAMBDA);
+            P.in = bufs[cur];
+            P.out = bufs[cur ^ 1];
+            const int64_t ngroups = 1LL << (p->L - P.k);
+            if (ch.kind == 0)
+                launch_one<Real, RP, false, 0>(P, ngroups, st);
+            else
+                launch_one<Real, RP, false, 1>(P, ngroups, st);
+            cur ^= 1;
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? IBF_OK : cuda_error(e, "static-scratch apply launch");
+}
+
+template <typename Real>
+static int static_dispatch(const ibf_plan* p, const void* g, void* u, int nrhs, cudaStream_t st, void* b0, void* b1,
+                           int max_cols)
+{
+    switch (p->r) {
+    case 5: return static_run<Real, 5>(p, g, u, nrhs, st, b0, b1, max_cols);
+    case 7: return static_run<Real, 7>(p, g, u, nrhs, st, b0, b1, max_cols);
+    case 9: return static_run<Real, 9>(p, g, u, nrhs, st, b0, b1, max_cols);
+    case 11: return static_run<Real, 11>(p, g, u, nrhs, st, b0, b1, max_cols);
+    default: return set_error(IBF_ERR_UNSUPPORTED, "structured form: unsupported r");
+    }
+}
+
+}  // namespace ibf
+
+using namespace ibf;
+
+extern "C" int ibf_apply_static_scratch(const ibf_plan* p, const void* g, void* u, int nrhs, ibf_stream_t stream)
+{
+    if (!p) return set_error(IBF_ERR_INVALID, "plan is NULL");
+    if (!g || !u) return set_error(IBF_ERR_INVALID, "NULL vector pointer");
+    if (nrhs < 1) return set_error(IBF_ERR_INVALID, "nrhs must be >= 1");
+    if (p->form != IBF_FORM_STRUCTURED)
+        return set_error(IBF_ERR_UNSUPPORTED, "static-scratch apply needs a structured-form plan");
+    const size_t esz = p->dtype == IBF_C128 ? sizeof(double2) : sizeof(float2);
+    if (((uintptr_t)g % esz) || ((uintptr_t)u % esz)) return set_error(IBF_ERR_INVALID, "misaligned vector pointer");
+    const size_t bytes = esz * (size_t)p->N * nrhs;
+    const char* cg = (const char*)g;
+    const char* cu = (const char*)u;
+    if (cg < cu + bytes && cu < cg + bytes) return set_error(IBF_ERR_INVALID, "input and output overlap");
+    const size_t col_bytes = esz * (size_t)p->N * p->r;   // one Lambda column
+    if (col_bytes > kStaticHalf)
+        return set_error(IBF_ERR_INVALID, "N*r*element size = " + std::to_string(col_bytes) +
+                                              " bytes exceeds the static scratch limit of " +
+                                              std::to_string(kStaticHalf) + " bytes per Lambda buffer");
+    void* base = nullptr;
+    int rc = static_scratch_address(&base);
+    if (rc) return rc;
+    const int max_cols = (int)std::min<size_t>(kStaticHalf / col_bytes, 1 << 20);
+    void* b0 = base;
+    void* b1 = (char*)base + kStaticHalf;
+    if (p->dtype == IBF_C128) return static_dispatch<double>(p, g, u, nrhs, (cudaStream_t)stream, b0, b1, max_cols);
+    return static_dispatch<float>(p, g, u, nrhs, (cudaStream_t)stream, b0, b1, max_cols);
+}
