@@ -38,8 +38,8 @@ template <typename Real>
 struct FusedTraits {
     // threads per CTA cap; FP64 keeps more registers per thread
     static constexpr int kThreads = sizeof(Real) == 4 ? 512 : 256;
-    // shared-memory budget in (pairs x rhs tile) units: 2^k * rt <= kPairCols
-    static constexpr int kPairCols = sizeof(Real) == 4 ? 1024 : 512;
+    // resident CTAs per SM the register budget is sized for
+    static constexpr int kMinBlocks = sizeof(Real) == 4 ? 2 : 1;
 };
 
 template <typename Real>
@@ -109,15 +109,17 @@ __device__ __forceinline__ void cacc(C& a, C b)
     a.y += b.y;
 }
 
-// KIND: 0 = H levels (1..h), 1 = G levels (h+1..L)
-template <typename Real, int RP, bool ADJ, int KIND>
-__global__ void __launch_bounds__(FusedTraits<Real>::kThreads, 1) k_fused(const __grid_constant__ FusedParams<Real, RP> P)
+// KIND: 0 = H levels (1..h), 1 = G levels (h+1..L).  RT: the rhs tile width
+// when it is known at compile time (32, the batched case), 0 otherwise.
+template <typename Real, int RP, bool ADJ, int KIND, int RT>
+__global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>::kMinBlocks) k_fused(const __grid_constant__ FusedParams<Real, RP> P)
 {
     typedef typename CT<Real>::T cx;
     extern __shared__ __align__(16) unsigned char smraw[];
     cx* sm = reinterpret_cast<cx*>(smraw);
 
-    const int k = P.k, rt = P.rt, L = P.L, l0 = P.l0;
+    const int k = P.k, L = P.L, l0 = P.l0;
+    const int rt = RT ? RT : P.rt;
     const int G = 1 << k;
     const int ntile = (P.nc + rt - 1) / rt;
     const int64_t grp = blockIdx.x / ntile;
@@ -177,99 +179,126 @@ __global__ void __launch_bounds__(FusedTraits<Real>::kThreads, 1) k_fused(const 
     }
     __syncthreads();
 
-    // --------------------------------------------------------------- levels
-    for (int st = 0; st < k; ++st) {
-        const int s = ADJ ? (k - st) : (st + 1);
-        const int l = l0 + s;
-        const int bit = s - 1;
-        const cx* D = (const cx*)P.D[s - 1];
-        const int64_t ldC = 1LL << (L - l + 1);
+    // ------------------------------------------------- stage phase tables
+    // D entries of every unit of every fused level, [s-1][u][a][c][RP]; the
+    // CTA reads each once from global memory.
+    constexpr int DS = 4 * RP + 1;   // per-unit stride, padded against bank conflicts
+    cx* dsm = sm + (size_t)G * RP * rt;
+    {
         const int nunit = G >> 1;
-        for (int w = threadIdx.x; w < nunit * rt; w += blockDim.x) {
-            const int c = w % rt, u = w / rt;
-            if (c < ncol) {
+        const int per_level = nunit * 4 * RP;
+        for (int st1 = 0; st1 < k; ++st1) {      // level s = st1 + 1 of the launch
+            const int s = st1 + 1, bit = st1;
+            const int64_t ldC = 1LL << (L - l0 - s + 1);
+            const cx* Dg = (const cx*)P.D[st1];
+            for (int e = threadIdx.x; e < per_level; e += blockDim.x) {
+                const int u = e / (4 * RP);
+                const int rem = e - u * (4 * RP);
+                const int ac = rem / RP;                 // a * 2 + c
+                const int t = rem - ac * RP;
                 const int p0 = ((u >> bit) << (bit + 1)) | (u & ((1 << bit) - 1));
-                const int p1 = p0 | (1 << bit);
                 const int low = p0 & ((1 << bit) - 1);
-                const int64_t ia = (i0 << s) + ((int64_t)brevk(low, bit) << 1);
-                const int64_t C0 = ((jb << (k - s)) + (p0 >> s)) << 1;
-                const cx* d00 = D + (ia * ldC + C0) * RP;        // (a=0, c=0)
-                const cx* d01 = d00 + RP;                         // (a=0, c=1)
-                const cx* d10 = D + ((ia + 1) * ldC + C0) * RP;  // (a=1, c=0)
-                const cx* d11 = d10 + RP;                         // (a=1, c=1)
-                cx x0[RP], x1[RP];
+                const int64_t ia = (i0 << s) + ((int64_t)brevk(low, bit) << 1) + (ac >> 1);
+                const int64_t C = (((jb << (k - s)) + (p0 >> s)) << 1) + (ac & 1);
+                dsm[((size_t)st1 * nunit + u) * DS + rem] = __ldg(Dg + (ia * ldC + C) * RP + t);
+            }
+        }
+    }
+    __syncthreads();
+
+    // --------------------------------------------------------------- levels
+    // A warp owns UW units x CW columns; lanes 0-15 compute output 0 and
+    // lanes 16-31 output 1 of the same (unit, column), so both inputs are read
+    // before either output overwrites them (in place, __syncwarp between).
+    {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+        const int o = lane >> 4, l16 = lane & 15;
+        const int CW = rt < 16 ? rt : 16;
+        const int UW = 16 / CW;
+        const int nunit = G >> 1;
+        const int nug = (nunit + UW - 1) / UW, nch = rt / CW;
+        // TD forms use T_o^T; for o = 1 they run T_0^T on reversed vectors
+        // (T_1 = J T_0 J for the symmetric Chebyshev grid), so the matrix
+        // operand stays uniform across the warp.
+        constexpr bool TD = (!ADJ && KIND == 1) || (ADJ && KIND == 0);
+        for (int st = 0; st < k; ++st) {
+            const int s = ADJ ? (k - st) : (st + 1);
+            const int bit = s - 1;
+            const cx* dl = dsm + (size_t)(s - 1) * nunit * DS;
+            for (int task = warp; task < nug * nch; task += nwarp) {
+                const int ug = task / nch, chn = task - ug * nch;
+                const int u = ug * UW + l16 / CW;
+                const int col = chn * CW + l16 % CW;
+                const bool valid = u < nunit && col < ncol;
+                const int uu = valid ? u : 0;
+                const int p0 = ((uu >> bit) << (bit + 1)) | (uu & ((1 << bit) - 1));
+                const int p1 = p0 | (1 << bit);
+                const int cc = valid ? col : 0;
+                const cx* x0p = sm + (size_t)p0 * RP * rt + cc;
+                const cx* x1p = sm + (size_t)p1 * RP * rt + cc;
+                const cx* du = dl + (size_t)uu * DS;
+                cx acc[RP];
 #pragma unroll
-                for (int t = 0; t < RP; ++t) {
-                    x0[t] = sm[(p0 * RP + t) * rt + c];
-                    x1[t] = sm[(p1 * RP + t) * rt + c];
-                }
-#pragma unroll
-                for (int o = 0; o < 2; ++o) {
-                    cx acc[RP];
-#pragma unroll
-                    for (int t = 0; t < RP; ++t) acc[t] = cz<cx>();
+                for (int t = 0; t < RP; ++t) acc[t] = cz<cx>();
+                if (!TD) {
+                    // acc[t] = sum_q sum_s T_q[t][s] y_q[s],  y_q = D * x_q
 #pragma unroll
                     for (int q = 0; q < 2; ++q) {
-                        const cx* xq = q ? x1 : x0;
-                        if (!ADJ && KIND == 0) {
-                            // out a=o, in c=q: acc[t] += sum_s T_q[t][s] D_{o,q}[s] x_q[s]
-                            const cx* dd = o ? (q ? d11 : d10) : (q ? d01 : d00);
+                        const cx* xp = q ? x1p : x0p;
+                        const cx* dd = du + (ADJ ? (q * 2 + o) : (o * 2 + q)) * RP;
 #pragma unroll
-                            for (int s2 = 0; s2 < RP; ++s2) {
-                                const cx y = cmul(__ldg(dd + s2), xq[s2]);
-#pragma unroll
-                                for (int t = 0; t < RP; ++t) {
-                                    acc[t].x += P.T[q][t][s2] * y.x;
-                                    acc[t].y += P.T[q][t][s2] * y.y;
-                                }
-                            }
-                        } else if (!ADJ && KIND == 1) {
-                            // out a=o, in c=q: acc[t] += D_{o,q}[t] sum_s T_o[s][t] x_q[s]
-                            const cx* dd = o ? (q ? d11 : d10) : (q ? d01 : d00);
+                        for (int s2 = 0; s2 < RP; ++s2) {
+                            const cx xv = xp[s2 * rt];
+                            const cx y = ADJ ? cmulc(dd[s2], xv) : cmul(dd[s2], xv);
 #pragma unroll
                             for (int t = 0; t < RP; ++t) {
-                                cx y = cz<cx>();
-#pragma unroll
-                                for (int s2 = 0; s2 < RP; ++s2) {
-                                    y.x += P.T[o][s2][t] * xq[s2].x;
-                                    y.y += P.T[o][s2][t] * xq[s2].y;
-                                }
-                                cacc(acc[t], cmul(__ldg(dd + t), y));
-                            }
-                        } else if (ADJ && KIND == 0) {
-                            // out c=o, in a=q: acc[s] += conj(D_{q,o}[s]) sum_t T_o[t][s] x_q[t]
-                            const cx* dd = q ? (o ? d11 : d10) : (o ? d01 : d00);
-#pragma unroll
-                            for (int s2 = 0; s2 < RP; ++s2) {
-                                cx y = cz<cx>();
-#pragma unroll
-                                for (int t = 0; t < RP; ++t) {
-                                    y.x += P.T[o][t][s2] * xq[t].x;
-                                    y.y += P.T[o][t][s2] * xq[t].y;
-                                }
-                                cacc(acc[s2], cmulc(__ldg(dd + s2), y));
-                            }
-                        } else {
-                            // out c=o, in a=q: acc[s] += sum_t T_q[s][t] conj(D_{q,o}[t]) x_q[t]
-                            const cx* dd = q ? (o ? d11 : d10) : (o ? d01 : d00);
-#pragma unroll
-                            for (int t = 0; t < RP; ++t) {
-                                const cx y = cmulc(__ldg(dd + t), xq[t]);
-#pragma unroll
-                                for (int s2 = 0; s2 < RP; ++s2) {
-                                    acc[s2].x += P.T[q][s2][t] * y.x;
-                                    acc[s2].y += P.T[q][s2][t] * y.y;
-                                }
+                                acc[t].x += P.T[q][t][s2] * y.x;
+                                acc[t].y += P.T[q][t][s2] * y.y;
                             }
                         }
                     }
-                    const int po = o ? p1 : p0;
+                } else {
+                    // acc[t] = sum_q D[t] (T_o^T x_q)[t]; lanes with o = 1 walk
+                    // x and D backwards (index RP-1-t) and use T_0
+                    const int xstep = o ? -rt : rt;
+                    const int dstep = o ? -1 : 1;
 #pragma unroll
-                    for (int t = 0; t < RP; ++t) sm[(po * RP + t) * rt + c] = acc[t];
+                    for (int q = 0; q < 2; ++q) {
+                        const cx* xp = (q ? x1p : x0p) + (o ? (RP - 1) * rt : 0);
+                        const cx* dd = du + (ADJ ? (q * 2 + o) : (o * 2 + q)) * RP + (o ? RP - 1 : 0);
+                        cx xr[RP];
+#pragma unroll
+                        for (int s2 = 0; s2 < RP; ++s2) xr[s2] = xp[s2 * xstep];
+#pragma unroll
+                        for (int t = 0; t < RP; ++t) {
+                            cx y = cz<cx>();
+#pragma unroll
+                            for (int s2 = 0; s2 < RP; ++s2) {
+                                y.x += P.T[0][s2][t] * xr[s2].x;
+                                y.y += P.T[0][s2][t] * xr[s2].y;
+                            }
+                            const cx dv = dd[t * dstep];
+                            cacc(acc[t], ADJ ? cmulc(dv, y) : cmul(dv, y));
+                        }
+                    }
                 }
+                __syncwarp();
+                if (valid) {
+                    if (TD) {
+                        cx* dst = sm + (size_t)(o ? p1 : p0) * RP * rt + col + (o ? (RP - 1) * rt : 0);
+                        const int step = o ? -rt : rt;
+#pragma unroll
+                        for (int t = 0; t < RP; ++t) dst[t * step] = acc[t];
+                    } else {
+                        cx* dst = sm + (size_t)(o ? p1 : p0) * RP * rt + col;
+#pragma unroll
+                        for (int t = 0; t < RP; ++t) dst[t * rt] = acc[t];
+                    }
+                }
+                __syncwarp();
             }
+            __syncthreads();
         }
-        __syncthreads();
     }
 
     // ---------------------------------------------------------------- store
@@ -384,25 +413,54 @@ inline int pow2ceil(int v)
     return p;
 }
 
+// dynamic shared memory of one fused CTA: the Lambda tile plus the staged
+// phase tables of its k levels (padded per-unit stride 4r+1)
+inline size_t fused_smem_bytes(int k, int rt, int RP, size_t esz)
+{
+    const size_t G = (size_t)1 << k;
+    return (G * RP * rt + (size_t)k * (G / 2) * (4 * RP + 1)) * esz;
+}
+
+// largest fusion depth whose CTA fits the shared-memory budget that keeps
+// two CTAs per SM
+inline int fused_kmax(int rt, int RP, size_t esz)
+{
+    const size_t budget = 100 * 1024;
+    int k = 1;
+    while (k < kMaxFuse && fused_smem_bytes(k + 1, rt, RP, esz) <= budget) ++k;
+    return k;
+}
+
+template <typename Real, int RP, bool ADJ, int KIND, int RT>
+static void set_smem_attr()
+{
+    static bool done = false;
+    if (!done) {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaFuncSetAttribute(k_fused<Real, RP, ADJ, KIND, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        done = true;
+    }
+}
+
 template <typename Real, int RP, bool ADJ, int KIND>
 static int launch_one(const FusedParams<Real, RP>& P, int64_t ngroups, cudaStream_t st)
 {
     typedef typename CT<Real>::T cx;
-    static bool attr_set = false;
-    if (!attr_set) {
-        int dev = 0, optin = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        cudaFuncSetAttribute(k_fused<Real, RP, ADJ, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-        attr_set = true;
-    }
     const int G = 1 << P.k;
-    size_t smem = (size_t)G * RP * P.rt * sizeof(cx);
+    size_t smem = fused_smem_bytes(P.k, P.rt, RP, sizeof(cx));
     int ntile = (P.nc + P.rt - 1) / P.rt;
-    int threads = std::min(FusedTraits<Real>::kThreads, std::max(32, (G / 2) * P.rt));
+    int threads = std::min(FusedTraits<Real>::kThreads, std::max(32, G * P.rt));
     threads = (threads + 31) / 32 * 32;
     int64_t blocks = ngroups * ntile;
-    k_fused<Real, RP, ADJ, KIND><<<(unsigned)blocks, threads, smem, st>>>(P);
+    if (P.rt == 32) {
+        set_smem_attr<Real, RP, ADJ, KIND, 32>();
+        k_fused<Real, RP, ADJ, KIND, 32><<<(unsigned)blocks, threads, smem, st>>>(P);
+    } else {
+        set_smem_attr<Real, RP, ADJ, KIND, 0>();
+        k_fused<Real, RP, ADJ, KIND, 0><<<(unsigned)blocks, threads, smem, st>>>(P);
+    }
     return IBF_OK;
 }
 
@@ -426,8 +484,7 @@ static int fused_run(ibf_plan* p, const void* vin, void* vout, int nrhs, bool ad
     for (int c0 = 0; c0 < nrhs; c0 += p->max_nrhs) {
         const int nc = std::min(p->max_nrhs, nrhs - c0);
         const int rt = std::min(p->rtile, pow2ceil(nc));
-        const int budget = FusedTraits<Real>::kPairCols;
-        int kmax = p->user_kfuse ? p->kfuse : std::max(1, std::min(kMaxFuse, budget / rt > 0 ? 31 - __builtin_clz(budget / rt) : 1));
+        int kmax = p->user_kfuse ? p->kfuse : fused_kmax(rt, RP, sizeof(cx));
         kmax = std::max(1, std::min(kmax, kMaxFuse));
         std::vector<Chunk> sched = fused_schedule(p->L, p->h, kmax);
         P.nc = nc;

@@ -16,13 +16,9 @@ bool fused_supports_r(int r) { return r == 5 || r == 7 || r == 9 || r == 11; }
 
 void fused_choose_shape(ibf_plan* p)
 {
-    const int budget = p->dtype == IBF_C128 ? FusedTraits<double>::kPairCols : FusedTraits<float>::kPairCols;
+    const size_t esz = p->dtype == IBF_C128 ? sizeof(double2) : sizeof(float2);
     if (!p->user_rtile) p->rtile = std::min(32, pow2ceil(p->max_nrhs));
-    if (!p->user_kfuse) {
-        int k = 0;
-        while ((2 << k) * p->rtile <= budget && k < kMaxFuse) ++k;
-        p->kfuse = std::max(1, k);
-    }
+    if (!p->user_kfuse) p->kfuse = fused_kmax(p->rtile, p->r, esz);
 }
 
 int fused_launches(const ibf_plan* p) { return (int)fused_schedule(p->L, p->h, p->kfuse).size(); }

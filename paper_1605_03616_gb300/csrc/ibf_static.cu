@@ -70,10 +70,7 @@ static int static_run(const ibf_plan* p, const void* vin, void* vout, int nrhs, 
     for (int c0 = 0; c0 < nrhs; c0 += max_cols) {
         const int nc = std::min(max_cols, nrhs - c0);
         const int rt = std::min(32, pow2ceil(nc));
-        const int budget = FusedTraits<Real>::kPairCols;
-        int kmax = 0;
-        while (kmax < kMaxFuse && (2 << kmax) * rt <= budget) ++kmax;
-        kmax = std::max(1, kmax);
+        const int kmax = fused_kmax(rt, RP, sizeof(cx));
         std::vector<Chunk> sched = fused_schedule(p->L, p->h, kmax);
         P.nc = nc;
         P.rt = rt;
