@@ -146,11 +146,14 @@ def run_reference(a):
 
 
 # ------------------------------------------------------------------ GPU arm
-def structured_flops(kind_levels, r, N, nc, pro, epi):
-    """Algorithmic FP32 flops of one fused launch: per butterfly unit and
-    right-hand side, 4 diagonal complex multiplies (6 r flops each) and 4 real
-    r x r times complex r products (4 r^2 flops each)."""
-    unit = 16 * r * r + 24 * r
+def structured_flops(kind_levels, r, N, nc, pro, epi, kind_g):
+    """Algorithmic FP32 flops of one fused launch of the even/odd structured
+    form, per butterfly unit (two outputs) and right-hand side:
+    H form 8 r^2 + 36 r (two complex phase products, the even/odd sums and
+    r^2 real multiply-adds per output), G form 8 r^2 + 44 r (even/odd parts
+    of both inputs, r^2 multiply-adds per input shared by both outputs, four
+    complex phase products per output index)."""
+    unit = 8 * r * r + (44 if kind_g else 36) * r
     f = unit * (N // 2) * kind_levels * nc
     if pro == "V":
         f += 6 * r * N * nc
@@ -240,7 +243,7 @@ def run_gpu(a):
     pro = "V" if lo == 0 else None
     epi = "U" if hi == L else ("switch" if hi == h else None)
     avg_ms = statistics.mean(per_launch[dom])
-    flops = structured_flops(hi - lo, r, N, nrhs, pro, epi)
+    flops = structured_flops(hi - lo, r, N, nrhs, pro, epi, kd == ibf.K_FUSED_G)
     esz = 8
     bytes_alg = 0
     bytes_alg += (N * nrhs * esz) if pro == "V" else (N * r * nrhs * esz)          # input

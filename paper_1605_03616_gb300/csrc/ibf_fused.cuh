@@ -56,9 +56,28 @@ struct CT<double> {
 enum { PRO_LAMBDA = 0, PRO_V = 1, PRO_UADJ = 2 };
 enum { EPI_LAMBDA = 0, EPI_SWITCH = 1, EPI_U = 2, EPI_VADJ = 3 };
 
+// Even/odd form of the transfer matrices.  The Chebyshev grid is symmetric
+// (z_{r-1-t} = -z_t), so T_1 = J T_0 J with J the index reversal.  With
+// P = (I+J)/2 and Q = (I-J)/2:
+//   T_0 y0 + T_1 y1 = P T_0 (y0 + J y1) + Q T_0 (y0 - J y1)           (H form)
+//   T_0^T x = e + f,  T_1^T x = J (e - f),  e = T_0^T P x, f = T_0^T Q x   (G form)
+// Each needs r^2 real multiply-adds per complex vector pair instead of 2 r^2.
+template <int RP>
+struct EO {
+    static constexpr int HR = (RP + 1) / 2;   // even rows (incl. the middle one)
+    static constexpr int HQ = RP / 2;         // odd rows
+};
+
 template <typename Real, int RP>
 struct FusedParams {
-    Real T[2][RP][RP];           // T_c[t][s]; lives in the kernel parameter bank
+    // Pm[t][s] = (T0[t][s] + T0[RP-1-t][s]) / 2 (t < HQ); Pm[mid][s] = T0[mid][s]
+    // Qm[t][s] = (T0[t][s] - T0[RP-1-t][s]) / 2 (t < HQ)
+    // E[t][s]  = (T0[s][t] + T0[RP-1-s][t]) / 2 (s < HQ); E[t][mid] = T0[mid][t]
+    // F[t][s]  = (T0[s][t] - T0[RP-1-s][t]) / 2 (s < HQ)
+    Real Pm[EO<RP>::HR][RP];
+    Real Qm[EO<RP>::HQ > 0 ? EO<RP>::HQ : 1][RP];
+    Real E[RP][EO<RP>::HR];
+    Real F[RP][EO<RP>::HQ > 0 ? EO<RP>::HQ : 1];
     const void* D[kMaxFuse];     // phase table of step s at D[s-1]
     const void* in;              // Lambda at the launch's input level
     void* out;                   // Lambda at the launch's output level
@@ -207,95 +226,138 @@ __global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>
     __syncthreads();
 
     // --------------------------------------------------------------- levels
-    // A warp owns UW units x CW columns; lanes 0-15 compute output 0 and
-    // lanes 16-31 output 1 of the same (unit, column), so both inputs are read
-    // before either output overwrites them (in place, __syncwarp between).
     {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-        const int o = lane >> 4, l16 = lane & 15;
-        const int CW = rt < 16 ? rt : 16;
-        const int UW = 16 / CW;
+        constexpr int HR = EO<RP>::HR, HQ = EO<RP>::HQ;
+        constexpr bool ODD = RP & 1;
         const int nunit = G >> 1;
-        const int nug = (nunit + UW - 1) / UW, nch = rt / CW;
-        // TD forms use T_o^T; for o = 1 they run T_0^T on reversed vectors
-        // (T_1 = J T_0 J for the symmetric Chebyshev grid), so the matrix
-        // operand stays uniform across the warp.
+        // H form (forward H levels, adjoint G levels): one output per thread.
+        // Lanes 0-15 and 16-31 hold outputs 0 and 1 of the same (unit,
+        // column), so both inputs are read before either is overwritten
+        // (__syncwarp between).  G form (forward G levels, adjoint H levels):
+        // one thread per (unit, column) computes both outputs, which share
+        // e and f.
         constexpr bool TD = (!ADJ && KIND == 1) || (ADJ && KIND == 0);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
         for (int st = 0; st < k; ++st) {
             const int s = ADJ ? (k - st) : (st + 1);
             const int bit = s - 1;
             const cx* dl = dsm + (size_t)(s - 1) * nunit * DS;
-            for (int task = warp; task < nug * nch; task += nwarp) {
-                const int ug = task / nch, chn = task - ug * nch;
-                const int u = ug * UW + l16 / CW;
-                const int col = chn * CW + l16 % CW;
-                const bool valid = u < nunit && col < ncol;
-                const int uu = valid ? u : 0;
-                const int p0 = ((uu >> bit) << (bit + 1)) | (uu & ((1 << bit) - 1));
-                const int p1 = p0 | (1 << bit);
-                const int cc = valid ? col : 0;
-                const cx* x0p = sm + (size_t)p0 * RP * rt + cc;
-                const cx* x1p = sm + (size_t)p1 * RP * rt + cc;
-                const cx* du = dl + (size_t)uu * DS;
-                cx acc[RP];
+            if (!TD) {
+                const int o = lane >> 4, l16 = lane & 15;
+                const int CW = rt < 16 ? rt : 16;
+                const int UW = 16 / CW;
+                const int nug = (nunit + UW - 1) / UW, nch = rt / CW;
+                for (int task = warp; task < nug * nch; task += nwarp) {
+                    const int ug = task / nch, chn = task - ug * nch;
+                    const int u = ug * UW + l16 / CW;
+                    const int col = chn * CW + l16 % CW;
+                    const bool valid = u < nunit && col < ncol;
+                    const int uu = valid ? u : 0;
+                    const int p0 = ((uu >> bit) << (bit + 1)) | (uu & ((1 << bit) - 1));
+                    const int p1 = p0 | (1 << bit);
+                    const int cc = valid ? col : 0;
+                    const cx* x0p = sm + (size_t)p0 * RP * rt + cc;
+                    const cx* x1p = sm + (size_t)p1 * RP * rt + cc;
+                    const cx* du = dl + (size_t)uu * DS;
+                    // forward H: y_q = D_{o,q} x_q; adjoint G: y_q = conj(D_{q,o}) x_q
+                    const cx* d0 = du + (ADJ ? (0 * 2 + o) : (o * 2 + 0)) * RP;
+                    const cx* d1 = du + (ADJ ? (1 * 2 + o) : (o * 2 + 1)) * RP;
+                    cx we[HR], wo[HQ > 0 ? HQ : 1];
 #pragma unroll
-                for (int t = 0; t < RP; ++t) acc[t] = cz<cx>();
-                if (!TD) {
-                    // acc[t] = sum_q sum_s T_q[t][s] y_q[s],  y_q = D * x_q
+                    for (int t = 0; t < HR; ++t) we[t] = cz<cx>();
 #pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const cx* xp = q ? x1p : x0p;
-                        const cx* dd = du + (ADJ ? (q * 2 + o) : (o * 2 + q)) * RP;
+                    for (int t = 0; t < HQ; ++t) wo[t] = cz<cx>();
 #pragma unroll
-                        for (int s2 = 0; s2 < RP; ++s2) {
-                            const cx xv = xp[s2 * rt];
-                            const cx y = ADJ ? cmulc(dd[s2], xv) : cmul(dd[s2], xv);
+                    for (int s2 = 0; s2 < RP; ++s2) {
+                        const cx y0 = ADJ ? cmulc(d0[s2], x0p[s2 * rt]) : cmul(d0[s2], x0p[s2 * rt]);
+                        const cx y1 = ADJ ? cmulc(d1[RP - 1 - s2], x1p[(RP - 1 - s2) * rt])
+                                          : cmul(d1[RP - 1 - s2], x1p[(RP - 1 - s2) * rt]);
+                        const Real vpx = y0.x + y1.x, vpy = y0.y + y1.y;
+                        const Real vmx = y0.x - y1.x, vmy = y0.y - y1.y;
 #pragma unroll
-                            for (int t = 0; t < RP; ++t) {
-                                acc[t].x += P.T[q][t][s2] * y.x;
-                                acc[t].y += P.T[q][t][s2] * y.y;
-                            }
+                        for (int t = 0; t < HR; ++t) {
+                            we[t].x += P.Pm[t][s2] * vpx;
+                            we[t].y += P.Pm[t][s2] * vpy;
+                        }
+#pragma unroll
+                        for (int t = 0; t < HQ; ++t) {
+                            wo[t].x += P.Qm[t][s2] * vmx;
+                            wo[t].y += P.Qm[t][s2] * vmy;
                         }
                     }
-                } else {
-                    // acc[t] = sum_q D[t] (T_o^T x_q)[t]; lanes with o = 1 walk
-                    // x and D backwards (index RP-1-t) and use T_0
-                    const int xstep = o ? -rt : rt;
-                    const int dstep = o ? -1 : 1;
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const cx* xp = (q ? x1p : x0p) + (o ? (RP - 1) * rt : 0);
-                        const cx* dd = du + (ADJ ? (q * 2 + o) : (o * 2 + q)) * RP + (o ? RP - 1 : 0);
-                        cx xr[RP];
-#pragma unroll
-                        for (int s2 = 0; s2 < RP; ++s2) xr[s2] = xp[s2 * xstep];
-#pragma unroll
-                        for (int t = 0; t < RP; ++t) {
-                            cx y = cz<cx>();
-#pragma unroll
-                            for (int s2 = 0; s2 < RP; ++s2) {
-                                y.x += P.T[0][s2][t] * xr[s2].x;
-                                y.y += P.T[0][s2][t] * xr[s2].y;
-                            }
-                            const cx dv = dd[t * dstep];
-                            cacc(acc[t], ADJ ? cmulc(dv, y) : cmul(dv, y));
-                        }
-                    }
-                }
-                __syncwarp();
-                if (valid) {
-                    if (TD) {
-                        cx* dst = sm + (size_t)(o ? p1 : p0) * RP * rt + col + (o ? (RP - 1) * rt : 0);
-                        const int step = o ? -rt : rt;
-#pragma unroll
-                        for (int t = 0; t < RP; ++t) dst[t * step] = acc[t];
-                    } else {
+                    __syncwarp();
+                    if (valid) {
                         cx* dst = sm + (size_t)(o ? p1 : p0) * RP * rt + col;
 #pragma unroll
-                        for (int t = 0; t < RP; ++t) dst[t * rt] = acc[t];
+                        for (int t = 0; t < HQ; ++t) {
+                            cx a, b;
+                            a.x = we[t].x + wo[t].x;
+                            a.y = we[t].y + wo[t].y;
+                            b.x = we[t].x - wo[t].x;
+                            b.y = we[t].y - wo[t].y;
+                            dst[t * rt] = a;
+                            dst[(RP - 1 - t) * rt] = b;
+                        }
+                        if (ODD) dst[HQ * rt] = we[HQ];
+                    }
+                    __syncwarp();
+                }
+            } else {
+                for (int w = threadIdx.x; w < nunit * rt; w += blockDim.x) {
+                    const int c = w % rt, u = w / rt;
+                    if (c < ncol) {
+                        const int p0 = ((u >> bit) << (bit + 1)) | (u & ((1 << bit) - 1));
+                        const int p1 = p0 | (1 << bit);
+                        const cx* du = dl + (size_t)u * DS;
+                        // even and odd parts of both inputs (all reads before any write)
+                        cx xe[2][HR], xo[2][HQ > 0 ? HQ : 1];
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            const cx* xp = sm + (size_t)(q ? p1 : p0) * RP * rt + c;
+#pragma unroll
+                            for (int s2 = 0; s2 < HQ; ++s2) {
+                                const cx lo = xp[s2 * rt], hi = xp[(RP - 1 - s2) * rt];
+                                xe[q][s2].x = lo.x + hi.x;
+                                xe[q][s2].y = lo.y + hi.y;
+                                xo[q][s2].x = lo.x - hi.x;
+                                xo[q][s2].y = lo.y - hi.y;
+                            }
+                            if (ODD) xe[q][HQ] = xp[HQ * rt];
+                        }
+                        cx* o0 = sm + (size_t)p0 * RP * rt + c;
+                        cx* o1 = sm + (size_t)p1 * RP * rt + c;
+#pragma unroll
+                        for (int t = 0; t < RP; ++t) {
+                            cx a0 = cz<cx>(), a1 = cz<cx>();
+#pragma unroll
+                            for (int q = 0; q < 2; ++q) {
+                                cx e = cz<cx>(), f = cz<cx>();
+#pragma unroll
+                                for (int s2 = 0; s2 < HR; ++s2) {
+                                    e.x += P.E[t][s2] * xe[q][s2].x;
+                                    e.y += P.E[t][s2] * xe[q][s2].y;
+                                }
+#pragma unroll
+                                for (int s2 = 0; s2 < HQ; ++s2) {
+                                    f.x += P.F[t][s2] * xo[q][s2].x;
+                                    f.y += P.F[t][s2] * xo[q][s2].y;
+                                }
+                                cx z0, z1;   // (T_0^T x_q)[t] and (T_1^T x_q)[RP-1-t]
+                                z0.x = e.x + f.x;
+                                z0.y = e.y + f.y;
+                                z1.x = e.x - f.x;
+                                z1.y = e.y - f.y;
+                                // forward G: output a uses D_{a,q}; adjoint H: output c uses conj(D_{q,c})
+                                const cx* dA = du + (ADJ ? (q * 2 + 0) : (0 * 2 + q)) * RP;
+                                const cx* dB = du + (ADJ ? (q * 2 + 1) : (1 * 2 + q)) * RP;
+                                cacc(a0, ADJ ? cmulc(dA[t], z0) : cmul(dA[t], z0));
+                                cacc(a1, ADJ ? cmulc(dB[RP - 1 - t], z1) : cmul(dB[RP - 1 - t], z1));
+                            }
+                            o0[t * rt] = a0;
+                            o1[(RP - 1 - t) * rt] = a1;
+                        }
                     }
                 }
-                __syncwarp();
             }
             __syncthreads();
         }
@@ -413,6 +475,28 @@ inline int pow2ceil(int v)
     return p;
 }
 
+// even/odd matrices of T_0 (see struct EO), from the plan's FP64 T_0
+template <typename Real, int RP>
+inline void fill_even_odd(const ibf_plan* p, FusedParams<Real, RP>& P)
+{
+    constexpr int HQ = EO<RP>::HQ;
+    const auto& T0 = p->T[0];
+    for (int t = 0; t < HQ; ++t)
+        for (int s = 0; s < RP; ++s) {
+            P.Pm[t][s] = (Real)((T0[t][s] + T0[RP - 1 - t][s]) / 2);
+            P.Qm[t][s] = (Real)((T0[t][s] - T0[RP - 1 - t][s]) / 2);
+        }
+    if (RP & 1)
+        for (int s = 0; s < RP; ++s) P.Pm[HQ][s] = (Real)T0[HQ][s];
+    for (int t = 0; t < RP; ++t) {
+        for (int s = 0; s < HQ; ++s) {
+            P.E[t][s] = (Real)((T0[s][t] + T0[RP - 1 - s][t]) / 2);
+            P.F[t][s] = (Real)((T0[s][t] - T0[RP - 1 - s][t]) / 2);
+        }
+        if (RP & 1) P.E[t][HQ] = (Real)T0[HQ][t];
+    }
+}
+
 // dynamic shared memory of one fused CTA: the Lambda tile plus the staged
 // phase tables of its k levels (padded per-unit stride 4r+1)
 inline size_t fused_smem_bytes(int k, int rt, int RP, size_t esz)
@@ -470,9 +554,7 @@ static int fused_run(ibf_plan* p, const void* vin, void* vout, int nrhs, bool ad
     typedef typename CT<Real>::T cx;
     FusedParams<Real, RP> P;
     memset(&P, 0, sizeof(P));
-    for (int c = 0; c < 2; ++c)
-        for (int t = 0; t < RP; ++t)
-            for (int s = 0; s < RP; ++s) P.T[c][t][s] = (Real)p->T[c][t][s];
+    fill_even_odd(p, P);
     P.Vs = p->sV;
     P.Us = p->sU;
     P.Ms = p->sM;

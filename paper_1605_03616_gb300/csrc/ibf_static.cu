@@ -56,9 +56,7 @@ static int static_run(const ibf_plan* p, const void* vin, void* vout, int nrhs, 
     typedef typename CT<Real>::T cx;
     FusedParams<Real, RP> P;
     memset(&P, 0, sizeof(P));
-    for (int c = 0; c < 2; ++c)
-        for (int t = 0; t < RP; ++t)
-            for (int s = 0; s < RP; ++s) P.T[c][t][s] = (Real)p->T[c][t][s];
+    fill_even_odd(p, P);
     P.Vs = p->sV;
     P.Us = p->sU;
     P.Ms = p->sM;
