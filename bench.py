@@ -267,6 +267,8 @@ def run_gpu(a):
         roof = {"bound": "hbm", "achieved": ach_gb, "peak": float(pk["hbm_gbs"]), "unit": "GB/s",
                 "frac": frac_hbm, "traffic": None}
     roof.update({"kernel": kname, "avg_launch_ms": avg_ms, "launches_timed": len(per_launch[dom]),
+                 "launch_ms": {"%s %d..%d" % ("H" if kk == ibf.K_FUSED_H else "G", a0 + 1, b0):
+                               round(statistics.mean(v), 4) for (a0, b0, kk), v in per_launch.items()},
                  "peak_source": ("FP32 lanes x SMs x 2 x max SM clock (%s clock)" % pk_kind) if roof["bound"] == "alu"
                  else "%s hbm_gbs" % pk_kind,
                  "alu_frac": frac_alu, "hbm_frac": frac_hbm, "alg_flops": flops, "alg_bytes": bytes_alg})

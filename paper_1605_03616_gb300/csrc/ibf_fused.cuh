@@ -139,6 +139,9 @@ __global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>
 
     const int k = P.k, L = P.L, l0 = P.l0;
     const int rt = RT ? RT : P.rt;
+    // shared-memory stride between pair positions, padded by one element so
+    // that threads walking positions hit different banks
+    const int PS = RP * rt + 1;
     const int G = 1 << k;
     const int ntile = (P.nc + rt - 1) / rt;
     const int64_t grp = blockIdx.x / ntile;
@@ -160,7 +163,7 @@ __global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>
             const int64_t kx = (jb << k) + pos;
             cx gv = c < ncol ? g[kx + N * (col0 + c)] : cz<cx>();
 #pragma unroll
-            for (int t = 0; t < RP; ++t) sm[(pos * RP + t) * rt + c] = cmul(V[kx * RP + t], gv);
+            for (int t = 0; t < RP; ++t) sm[pos * PS + t * rt + c] = cmul(V[kx * RP + t], gv);
         }
     } else if (P.pro == PRO_UADJ) {
         // adjoint, top level L: Lambda^L_i[t] = sum_{n in leaf i} conj(U[n][t]) y[perm n]
@@ -182,7 +185,7 @@ __global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>
                 }
             }
 #pragma unroll
-            for (int t = 0; t < RP; ++t) sm[(pos * RP + t) * rt + c] = acc[t];
+            for (int t = 0; t < RP; ++t) sm[pos * PS + t * rt + c] = acc[t];
         }
     } else {
         const cx* in = (const cx*)P.in;
@@ -193,7 +196,7 @@ __global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>
                 pair = (i0 << (L - l0)) + (jb << k) + pos;
             else
                 pair = (((i0 << k) + brevk(pos, k)) << nbj) + jb;
-            sm[e] = c < ncol ? in[(pair * RP + t) * P.nc + col0 + c] : cz<cx>();
+            sm[pos * PS + t * rt + c] = c < ncol ? in[(pair * RP + t) * P.nc + col0 + c] : cz<cx>();
         }
     }
     __syncthreads();
@@ -202,7 +205,7 @@ __global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>
     // D entries of every unit of every fused level, [s-1][u][a][c][RP]; the
     // CTA reads each once from global memory.
     constexpr int DS = 4 * RP + 1;   // per-unit stride, padded against bank conflicts
-    cx* dsm = sm + (size_t)G * RP * rt;
+    cx* dsm = sm + (size_t)G * PS;
     {
         const int nunit = G >> 1;
         const int per_level = nunit * 4 * RP;
@@ -230,77 +233,86 @@ __global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>
         constexpr int HR = EO<RP>::HR, HQ = EO<RP>::HQ;
         constexpr bool ODD = RP & 1;
         const int nunit = G >> 1;
-        // H form (forward H levels, adjoint G levels): one output per thread.
-        // Lanes 0-15 and 16-31 hold outputs 0 and 1 of the same (unit,
-        // column), so both inputs are read before either is overwritten
-        // (__syncwarp between).  G form (forward G levels, adjoint H levels):
-        // one thread per (unit, column) computes both outputs, which share
-        // e and f.
+        // One thread per (unit, column) computes both outputs of the unit and
+        // writes them over its two inputs.  H form (forward H levels, adjoint
+        // G levels): out_a = P T_0 (y_a0 + J y_a1) + Q T_0 (y_a0 - J y_a1).
+        // G form (forward G levels, adjoint H levels): both outputs share
+        // e = T_0^T P x_q and f = T_0^T Q x_q.
         constexpr bool TD = (!ADJ && KIND == 1) || (ADJ && KIND == 0);
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
         for (int st = 0; st < k; ++st) {
             const int s = ADJ ? (k - st) : (st + 1);
             const int bit = s - 1;
             const cx* dl = dsm + (size_t)(s - 1) * nunit * DS;
             if (!TD) {
-                const int o = lane >> 4, l16 = lane & 15;
-                const int CW = rt < 16 ? rt : 16;
-                const int UW = 16 / CW;
-                const int nug = (nunit + UW - 1) / UW, nch = rt / CW;
-                for (int task = warp; task < nug * nch; task += nwarp) {
-                    const int ug = task / nch, chn = task - ug * nch;
-                    const int u = ug * UW + l16 / CW;
-                    const int col = chn * CW + l16 % CW;
-                    const bool valid = u < nunit && col < ncol;
-                    const int uu = valid ? u : 0;
-                    const int p0 = ((uu >> bit) << (bit + 1)) | (uu & ((1 << bit) - 1));
-                    const int p1 = p0 | (1 << bit);
-                    const int cc = valid ? col : 0;
-                    const cx* x0p = sm + (size_t)p0 * RP * rt + cc;
-                    const cx* x1p = sm + (size_t)p1 * RP * rt + cc;
-                    const cx* du = dl + (size_t)uu * DS;
-                    // forward H: y_q = D_{o,q} x_q; adjoint G: y_q = conj(D_{q,o}) x_q
-                    const cx* d0 = du + (ADJ ? (0 * 2 + o) : (o * 2 + 0)) * RP;
-                    const cx* d1 = du + (ADJ ? (1 * 2 + o) : (o * 2 + 1)) * RP;
-                    cx we[HR], wo[HQ > 0 ? HQ : 1];
+                for (int w = threadIdx.x; w < nunit * rt; w += blockDim.x) {
+                    const int c = w % rt, u = w / rt;
+                    if (c < ncol) {
+                        const int p0 = ((u >> bit) << (bit + 1)) | (u & ((1 << bit) - 1));
+                        const int p1 = p0 | (1 << bit);
+                        const cx* x0p = sm + (size_t)p0 * PS + c;
+                        const cx* x1p = sm + (size_t)p1 * PS + c;
+                        const cx* du = dl + (size_t)u * DS;
+                        // output a uses D_{a,q} (forward H) or conj(D_{q,a}) (adjoint G)
+                        const cx* d00 = du + (ADJ ? 0 : 0) * RP;
+                        const cx* d01 = du + (ADJ ? 2 : 1) * RP;
+                        const cx* d10 = du + (ADJ ? 1 : 2) * RP;
+                        const cx* d11 = du + 3 * RP;
+                        cx we0[HR], wo0[HQ > 0 ? HQ : 1], we1[HR], wo1[HQ > 0 ? HQ : 1];
 #pragma unroll
-                    for (int t = 0; t < HR; ++t) we[t] = cz<cx>();
+                        for (int t = 0; t < HR; ++t) we0[t] = we1[t] = cz<cx>();
 #pragma unroll
-                    for (int t = 0; t < HQ; ++t) wo[t] = cz<cx>();
+                        for (int t = 0; t < HQ; ++t) wo0[t] = wo1[t] = cz<cx>();
 #pragma unroll
-                    for (int s2 = 0; s2 < RP; ++s2) {
-                        const cx y0 = ADJ ? cmulc(d0[s2], x0p[s2 * rt]) : cmul(d0[s2], x0p[s2 * rt]);
-                        const cx y1 = ADJ ? cmulc(d1[RP - 1 - s2], x1p[(RP - 1 - s2) * rt])
-                                          : cmul(d1[RP - 1 - s2], x1p[(RP - 1 - s2) * rt]);
-                        const Real vpx = y0.x + y1.x, vpy = y0.y + y1.y;
-                        const Real vmx = y0.x - y1.x, vmy = y0.y - y1.y;
+                        for (int s2 = 0; s2 < RP; ++s2) {
+                            const cx xa = x0p[s2 * rt], xb = x1p[(RP - 1 - s2) * rt];
+                            const cx y00 = ADJ ? cmulc(d00[s2], xa) : cmul(d00[s2], xa);
+                            const cx y01 = ADJ ? cmulc(d01[RP - 1 - s2], xb) : cmul(d01[RP - 1 - s2], xb);
+                            const cx y10 = ADJ ? cmulc(d10[s2], xa) : cmul(d10[s2], xa);
+                            const cx y11 = ADJ ? cmulc(d11[RP - 1 - s2], xb) : cmul(d11[RP - 1 - s2], xb);
+                            const Real p0x = y00.x + y01.x, p0y = y00.y + y01.y;
+                            const Real m0x = y00.x - y01.x, m0y = y00.y - y01.y;
+                            const Real p1x = y10.x + y11.x, p1y = y10.y + y11.y;
+                            const Real m1x = y10.x - y11.x, m1y = y10.y - y11.y;
 #pragma unroll
-                        for (int t = 0; t < HR; ++t) {
-                            we[t].x += P.Pm[t][s2] * vpx;
-                            we[t].y += P.Pm[t][s2] * vpy;
+                            for (int t = 0; t < HR; ++t) {
+                                const Real pm = P.Pm[t][s2];
+                                we0[t].x += pm * p0x;
+                                we0[t].y += pm * p0y;
+                                we1[t].x += pm * p1x;
+                                we1[t].y += pm * p1y;
+                            }
+#pragma unroll
+                            for (int t = 0; t < HQ; ++t) {
+                                const Real qm = P.Qm[t][s2];
+                                wo0[t].x += qm * m0x;
+                                wo0[t].y += qm * m0y;
+                                wo1[t].x += qm * m1x;
+                                wo1[t].y += qm * m1y;
+                            }
                         }
-#pragma unroll
-                        for (int t = 0; t < HQ; ++t) {
-                            wo[t].x += P.Qm[t][s2] * vmx;
-                            wo[t].y += P.Qm[t][s2] * vmy;
-                        }
-                    }
-                    __syncwarp();
-                    if (valid) {
-                        cx* dst = sm + (size_t)(o ? p1 : p0) * RP * rt + col;
+                        cx* o0 = sm + (size_t)p0 * PS + c;
+                        cx* o1 = sm + (size_t)p1 * PS + c;
 #pragma unroll
                         for (int t = 0; t < HQ; ++t) {
                             cx a, b;
-                            a.x = we[t].x + wo[t].x;
-                            a.y = we[t].y + wo[t].y;
-                            b.x = we[t].x - wo[t].x;
-                            b.y = we[t].y - wo[t].y;
-                            dst[t * rt] = a;
-                            dst[(RP - 1 - t) * rt] = b;
+                            a.x = we0[t].x + wo0[t].x;
+                            a.y = we0[t].y + wo0[t].y;
+                            b.x = we0[t].x - wo0[t].x;
+                            b.y = we0[t].y - wo0[t].y;
+                            o0[t * rt] = a;
+                            o0[(RP - 1 - t) * rt] = b;
+                            a.x = we1[t].x + wo1[t].x;
+                            a.y = we1[t].y + wo1[t].y;
+                            b.x = we1[t].x - wo1[t].x;
+                            b.y = we1[t].y - wo1[t].y;
+                            o1[t * rt] = a;
+                            o1[(RP - 1 - t) * rt] = b;
                         }
-                        if (ODD) dst[HQ * rt] = we[HQ];
+                        if (ODD) {
+                            o0[HQ * rt] = we0[HQ];
+                            o1[HQ * rt] = we1[HQ];
+                        }
                     }
-                    __syncwarp();
                 }
             } else {
                 for (int w = threadIdx.x; w < nunit * rt; w += blockDim.x) {
@@ -313,7 +325,7 @@ __global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>
                         cx xe[2][HR], xo[2][HQ > 0 ? HQ : 1];
 #pragma unroll
                         for (int q = 0; q < 2; ++q) {
-                            const cx* xp = sm + (size_t)(q ? p1 : p0) * RP * rt + c;
+                            const cx* xp = sm + (size_t)(q ? p1 : p0) * PS + c;
 #pragma unroll
                             for (int s2 = 0; s2 < HQ; ++s2) {
                                 const cx lo = xp[s2 * rt], hi = xp[(RP - 1 - s2) * rt];
@@ -324,8 +336,8 @@ __global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>
                             }
                             if (ODD) xe[q][HQ] = xp[HQ * rt];
                         }
-                        cx* o0 = sm + (size_t)p0 * RP * rt + c;
-                        cx* o1 = sm + (size_t)p1 * RP * rt + c;
+                        cx* o0 = sm + (size_t)p0 * PS + c;
+                        cx* o1 = sm + (size_t)p1 * PS + c;
 #pragma unroll
                         for (int t = 0; t < RP; ++t) {
                             cx a0 = cz<cx>(), a1 = cz<cx>();
@@ -374,7 +386,7 @@ __global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>
                 pair = (((i0 << k) + brevk(pos, k)) << nbj) + jb;
             else
                 pair = (i0 << (L - l0)) + (jb << k) + pos;
-            out[(pair * RP + t) * P.nc + col0 + c] = sm[e];
+            out[(pair * RP + t) * P.nc + col0 + c] = sm[pos * PS + t * rt + c];
         }
     } else if (P.epi == EPI_SWITCH) {
         // forward: Lambda~ = M~' Lambda at level h; adjoint: Lambda = M~'^* Lambda~
@@ -390,7 +402,7 @@ __global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>
                 pair = (i0 << (L - l0)) + (jb << k) + pos;
             cx x[RP];
 #pragma unroll
-            for (int t = 0; t < RP; ++t) x[t] = sm[(pos * RP + t) * rt + c];
+            for (int t = 0; t < RP; ++t) x[t] = sm[pos * PS + t * rt + c];
             const cx* Mp = M + pair * RP * RP;
 #pragma unroll
             for (int t = 0; t < RP; ++t) {
@@ -416,7 +428,7 @@ __global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>
             const int64_t leaf = (i0 << k) + il;
             cx x[RP];
 #pragma unroll
-            for (int t = 0; t < RP; ++t) x[t] = sm[(pos * RP + t) * rt + c];
+            for (int t = 0; t < RP; ++t) x[t] = sm[pos * PS + t * rt + c];
             const int32_t n1 = P.off[leaf + 1];
             for (int32_t n = P.off[leaf]; n < n1; ++n) {
                 cx acc = cz<cx>();
@@ -435,7 +447,7 @@ __global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>
             const int64_t kx = (jb << k) + pos;
             cx acc = cz<cx>();
 #pragma unroll
-            for (int t = 0; t < RP; ++t) cacc(acc, cmulc(V[kx * RP + t], sm[(pos * RP + t) * rt + c]));
+            for (int t = 0; t < RP; ++t) cacc(acc, cmulc(V[kx * RP + t], sm[pos * PS + t * rt + c]));
             g[kx + N * (col0 + c)] = acc;
         }
     }
@@ -502,7 +514,7 @@ inline void fill_even_odd(const ibf_plan* p, FusedParams<Real, RP>& P)
 inline size_t fused_smem_bytes(int k, int rt, int RP, size_t esz)
 {
     const size_t G = (size_t)1 << k;
-    return (G * RP * rt + (size_t)k * (G / 2) * (4 * RP + 1)) * esz;
+    return (G * ((size_t)RP * rt + 1) + (size_t)k * (G / 2) * (4 * RP + 1)) * esz;
 }
 
 // largest fusion depth whose CTA fits the shared-memory budget that keeps
@@ -535,7 +547,7 @@ static int launch_one(const FusedParams<Real, RP>& P, int64_t ngroups, cudaStrea
     const int G = 1 << P.k;
     size_t smem = fused_smem_bytes(P.k, P.rt, RP, sizeof(cx));
     int ntile = (P.nc + P.rt - 1) / P.rt;
-    int threads = std::min(FusedTraits<Real>::kThreads, std::max(32, G * P.rt));
+    int threads = std::min(FusedTraits<Real>::kThreads, std::max(32, (G / 2) * P.rt));
     threads = (threads + 31) / 32 * 32;
     int64_t blocks = ngroups * ntile;
     if (P.rt == 32) {
