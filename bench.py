@@ -145,6 +145,65 @@ def run_reference(a):
     return 0
 
 
+# ------------------------------------------------------- batched workload
+def run_batch(ibf, torch, reps=5, count=256, seed=4):
+    """256 independent 1D FIO transforms, N = 2^e with e uniform in 10..16,
+    nrhs uniform in 1..64, complex64, r = 9: the batched launch captured in a
+    CUDA graph vs a loop of per-transform applies, both with CUDA events."""
+    gen = W.rng(workload=seed)
+    es = gen.integers(10, 17, count)
+    nr = gen.integers(1, 65, count)
+    plans = [ibf.Plan(ibf.PHASE_FIO1D, 1 << int(e), 9, ibf.C64_FP32, max_nrhs=int(k)) for e, k in zip(es, nr)]
+    ins = [torch.from_numpy(W.complex_normal((int(k), 1 << int(e)), gen, dtype=np.complex64)).cuda()
+           for e, k in zip(es, nr)]
+    outs = [torch.empty_like(t) for t in ins]
+    batch = ibf.Batch(plans, ins, outs)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            batch.apply(stream=stream)
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        batch.apply(stream=stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    t_graph = e0.elapsed_time(e1) / reps
+    ref = [o.clone() for o in outs]
+    cs = torch.cuda.current_stream().cuda_stream
+
+    def loop():
+        for p, g, u in zip(plans, ins, outs):
+            p.apply_raw(g.data_ptr(), u.data_ptr(), g.shape[0], cs)
+    loop()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        loop()
+    e1.record()
+    torch.cuda.synchronize()
+    t_loop = e0.elapsed_time(e1) / reps
+    err = max(float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)) for a, b in zip(outs, ref))
+    vec = int(nr.sum())
+    res = {"workload": "256 x 1D FIO, N=2^e e~U{10..16}, nrhs~U{1..64}, r=9, complex64",
+           "vectors": vec, "graph_ms": t_graph, "loop_ms": t_loop,
+           "graph_vectors_per_s": vec / (t_graph / 1e3), "loop_vectors_per_s": vec / (t_loop / 1e3),
+           "speedup_vs_loop": t_loop / t_graph, "launches_graph": batch.query(ibf.BQ_LAUNCHES),
+           "launches_loop": sum(p.query(ibf.Q_LAUNCHES) for p in plans), "max_rel_diff_graph_vs_loop": err}
+    batch.close()
+    for p in plans:
+        p.close()
+    return res
+
+
 # ------------------------------------------------------------------ GPU arm
 def structured_flops(kind_levels, r, N, nc, pro, epi, kind_g):
     """Algorithmic FP32 flops of one fused launch of the even/odd structured
@@ -329,6 +388,11 @@ def run_gpu(a):
         p64.close()
         del g64, u64, g4, u4
 
+    # ---- batched uneven workload (rank 0)
+    batch = None
+    if rank == 0 and not a.skip_batch:
+        batch = run_batch(ibf, torch)
+
     # ---- CPU oracle on the host cores (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not a.skip_cpu:
@@ -347,7 +411,7 @@ def run_gpu(a):
                            "l2": "inputs and workspace larger than L2 (no flush)",
                            "parallelism": "independent rhs batches per GPU (dp%d)" % world},
                 "clocks": clk, "e2e": e2e, "gpu_launches": a.steps * launches, "roofline": roof,
-                "fp64_plain": fp64, "cpu_baseline": cpu}
+                "fp64_plain": fp64, "batch256": batch, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:
@@ -366,6 +430,7 @@ def main():
     ap.add_argument("--nrhs", type=int, default=64)
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-batch", action="store_true")
     a = ap.parse_args()
     if a.warmup < 3 and a.impl == "ibf":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

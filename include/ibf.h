@@ -175,6 +175,47 @@ int ibf_apply_adjoint(ibf_plan* plan, const void* y, void* g, int nrhs, ibf_stre
  */
 int ibf_apply_static_scratch(const ibf_plan* plan, const void* g, void* u, int nrhs, ibf_stream_t stream);
 
+/*
+ * Batched apply of many plans of uneven size in few launches.  The paper
+ * applies one IBF at a time (Sec. 3); a batch runs the same factor products
+ * for many independent plans together.
+ *
+ * ibf_batch_create binds `count` structured-form plans (same dtype and r),
+ * their right-hand-side counts nrhs[b] >= 1 and device buffers in[b] (input,
+ * N_b x nrhs[b] column-major: g for the forward apply, y for the adjoint) and
+ * out[b] (output, same shape, overwritten); adjoint != 0 makes the batch
+ * compute K_b^* y_b instead of K_b g_b.  The batch owns a workspace of
+ * sum_b 2 N_b r nrhs[b] complex elements and a launch table; the plans and
+ * buffers must outlive it.  Synchronizes the device before returning.
+ *
+ * ibf_batch_apply runs the whole batch on `stream`: one launch runs fused
+ * chunk p of every plan with the same level kind and rhs tile width (1, 2,
+ * ..., 32), so the number of launches (IBF_BQ_LAUNCHES) is at most 12 times
+ * the largest number of chunks of any plan, independent of the number of
+ * plans.  It copies nothing from the host and
+ * allocates nothing, so it may be captured in a CUDA graph.  Calls on one
+ * batch must be ordered.
+ */
+typedef struct ibf_batch ibf_batch;
+int ibf_batch_create(ibf_plan* const* plans, int count, const int* nrhs, const void* const* in, void* const* out,
+                     int adjoint, ibf_batch** batch);
+int ibf_batch_apply(const ibf_batch* batch, ibf_stream_t stream);
+enum ibf_batch_query_key { IBF_BQ_LAUNCHES = 0, IBF_BQ_WORKSPACE_BYTES = 1, IBF_BQ_COUNT = 2 };
+int ibf_batch_query(const ibf_batch* batch, int what, int64_t* value);
+int ibf_batch_destroy(ibf_batch* batch);   /* NULL-safe; synchronizes the device */
+
+/*
+ * ibf_plan_autotune -- choose the structured form's launch shape (levels
+ * fused per launch, right-hand sides per CTA) for applies with `nrhs`
+ * columns by timing every candidate on scratch buffers (allocated and freed
+ * here) on `stream`, and store the fastest in the plan (it then behaves as if
+ * ibf_options.levels_per_launch / rhs_tile had been set).  Reports the choice
+ * and its time per apply in milliseconds through the optional out pointers.
+ * Structured plans only (else IBF_ERR_UNSUPPORTED).  Synchronizes.
+ */
+int ibf_plan_autotune(ibf_plan* plan, int nrhs, ibf_stream_t stream, int* levels_per_launch, int* rhs_tile,
+                      float* ms);
+
 /* Free the plan and all its device memory; NULL is accepted.  Synchronizes
  * the device first. */
 int ibf_plan_destroy(ibf_plan* plan);

@@ -39,7 +39,10 @@ STATUS = {0: "IBF_OK", 1: "IBF_ERR_INVALID", 2: "IBF_ERR_OOM", 3: "IBF_ERR_CUDA"
 # every symbol include/ibf.h declares
 EXPORTS = ("ibf_plan_create", "ibf_plan_create_ex", "ibf_apply", "ibf_apply_adjoint", "ibf_plan_destroy",
            "ibf_plan_query", "ibf_get_last_error", "ibf_plan_profile_begin", "ibf_plan_profile_end",
-           "ibf_apply_static_scratch")
+           "ibf_apply_static_scratch", "ibf_batch_create", "ibf_batch_apply", "ibf_batch_query",
+           "ibf_batch_destroy", "ibf_plan_autotune")
+
+BQ_LAUNCHES, BQ_WORKSPACE_BYTES, BQ_COUNT = range(3)
 
 K_EXPLICIT_INIT, K_EXPLICIT_LEVEL, K_EXPLICIT_SWITCH, K_EXPLICIT_TERM, K_FUSED_H, K_FUSED_G = range(6)
 
@@ -82,6 +85,11 @@ def load_library(path: str | None = None):
     L.ibf_plan_query.argtypes = [P, I, ctypes.POINTER(I64)]
     L.ibf_get_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     L.ibf_apply_static_scratch.argtypes = [P, P, P, I, P]
+    L.ibf_batch_create.argtypes = [P, I, P, P, P, I, ctypes.POINTER(P)]
+    L.ibf_batch_apply.argtypes = [P, P]
+    L.ibf_batch_query.argtypes = [P, I, ctypes.POINTER(I64)]
+    L.ibf_batch_destroy.argtypes = [P]
+    L.ibf_plan_autotune.argtypes = [P, I, P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_float)]
     L.ibf_plan_profile_begin.argtypes = [P, I]
     L.ibf_plan_profile_end.argtypes = [P, P, P, I, ctypes.POINTER(I)]
     for nm in EXPORTS:
@@ -204,6 +212,16 @@ class Plan:
         m = min(n.value, cap)
         return list(zip(kind[:m].tolist(), ms[:m].tolist()))
 
+    def autotune(self, nrhs: int, stream=None):
+        """Time every launch shape for `nrhs` columns and keep the fastest
+        (ibf_plan_autotune).  Returns (levels_per_launch, rhs_tile, ms)."""
+        torch = _torch()
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        k, rt, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        _check(self._lib.ibf_plan_autotune(self._p, nrhs, ctypes.c_void_p(s), ctypes.byref(k), ctypes.byref(rt),
+                                           ctypes.byref(ms)))
+        return k.value, rt.value, ms.value
+
     def apply_raw(self, g_ptr: int, u_ptr: int, nrhs: int, stream_ptr: int = 0) -> None:
         """Pointer-level ibf_apply for callers that manage their own buffers."""
         _check(self._lib.ibf_apply(self._p, ctypes.c_void_p(g_ptr), ctypes.c_void_p(u_ptr), nrhs,
@@ -212,3 +230,49 @@ class Plan:
     def adjoint_raw(self, y_ptr: int, g_ptr: int, nrhs: int, stream_ptr: int = 0) -> None:
         _check(self._lib.ibf_apply_adjoint(self._p, ctypes.c_void_p(y_ptr), ctypes.c_void_p(g_ptr), nrhs,
                                            ctypes.c_void_p(stream_ptr)))
+
+
+class Batch:
+    """Many structured plans applied together (ibf_batch_create/apply).
+
+    `inputs[b]` / `outputs[b]` are CUDA tensors of shape (nrhs_b, N_b) -- the
+    column-major N_b x nrhs_b layout of the C ABI -- bound at creation."""
+
+    def __init__(self, plans, inputs, outputs, adjoint: bool = False):
+        self._lib = load_library()
+        n = len(plans)
+        if not (len(inputs) == len(outputs) == n):
+            raise ValueError("plans, inputs and outputs must have the same length")
+        self.plans, self.inputs, self.outputs = list(plans), list(inputs), list(outputs)
+        P = ctypes.c_void_p
+        parr = (P * n)(*[p._p for p in plans])
+        nr = (ctypes.c_int * n)(*[int(t.shape[0]) for t in inputs])
+        iarr = (P * n)(*[t.data_ptr() for t in inputs])
+        oarr = (P * n)(*[t.data_ptr() for t in outputs])
+        for p, t, o in zip(plans, inputs, outputs):
+            if t.shape != o.shape or t.shape[1] != p.N or not (t.is_contiguous() and o.is_contiguous()):
+                raise ValueError("each input/output must be a contiguous (nrhs, N) tensor")
+        out = P()
+        _check(self._lib.ibf_batch_create(parr, n, nr, iarr, oarr, 1 if adjoint else 0, ctypes.byref(out)))
+        self._b = out
+
+    def apply(self, stream=None):
+        torch = _torch()
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        _check(self._lib.ibf_batch_apply(self._b, ctypes.c_void_p(s)))
+
+    def query(self, what: int) -> int:
+        v = ctypes.c_int64()
+        _check(self._lib.ibf_batch_query(self._b, what, ctypes.byref(v)))
+        return v.value
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._lib.ibf_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -27,6 +27,7 @@ UNITS = {
     "ibf_fused_f32.cu": [],
     "ibf_fused_f64.cu": [],
     "ibf_static.cu": [],
+    "ibf_batch.cu": [],
 }
 
 

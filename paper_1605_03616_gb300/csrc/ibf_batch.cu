@@ -1,0 +1,345 @@
+// Batched apply of many structured-form plans of uneven size, and the
+// launch-shape autotuner.
+//
+// A batch binds, once, a list of plans with their input/output buffers and
+// right-hand-side counts.  Each plan's apply is a short sequence of fused
+// chunks (levels fused per launch); the batch runs chunk p of every plan in
+// one launch of k_fused_batch per (level kind, tile width) (CTA ranges map to
+// plans through a prefix sum), so a batch of B plans costs at most
+// 12 max_b(chunks_b) launches, whatever B, instead of sum_b(chunks_b), and ibf_batch_apply issues nothing but
+// those launches: it can be captured in a CUDA graph.
+#include <algorithm>
+#include <vector>
+
+#include "ibf_fused.cuh"
+
+struct ibf_batch {
+    int dtype = 0, r = 0, adjoint = 0, count = 0;
+    std::vector<int> nrhs;
+    struct Phase {
+        ibf::FusedDesc* descs = nullptr;   // device
+        int64_t* start = nullptr;          // device, n entries
+        int n = 0;
+        int64_t blocks = 0;
+        size_t smem = 0;
+        int threads = 0;
+        int kind = 0, rt = 0;
+    };
+    std::vector<Phase> phases;
+    std::vector<ibf_plan*> plans;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    std::vector<void*> allocations;
+};
+
+namespace ibf {
+
+static int balloc(ibf_batch* b, void** ptr, size_t bytes)
+{
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return set_error(IBF_ERR_OOM, "batch: cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    b->allocations.push_back(*ptr);
+    return IBF_OK;
+}
+
+static void batch_free(ibf_batch* b)
+{
+    if (!b) return;
+    for (void* a : b->allocations) cudaFree(a);
+    delete b;
+}
+
+template <typename Real, int RP, bool ADJ, int KIND, int RT>
+static void batch_one(const FusedConsts<Real, RP>& C, const ibf_batch::Phase& ph, cudaStream_t st)
+{
+    static bool done = false;
+    if (!done) {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaFuncSetAttribute(k_fused_batch<Real, RP, ADJ, KIND, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin);
+        done = true;
+    }
+    k_fused_batch<Real, RP, ADJ, KIND, RT><<<(unsigned)ph.blocks, ph.threads, ph.smem, st>>>(C, ph.descs, ph.start,
+                                                                                            ph.n);
+}
+
+template <typename Real, int RP, bool ADJ>
+static void batch_kind(const FusedConsts<Real, RP>& C, const ibf_batch::Phase& ph, cudaStream_t st)
+{
+    if (ph.kind == 0) {
+        if (ph.rt == 32)
+            batch_one<Real, RP, ADJ, 0, 32>(C, ph, st);
+        else
+            batch_one<Real, RP, ADJ, 0, 0>(C, ph, st);
+    } else {
+        if (ph.rt == 32)
+            batch_one<Real, RP, ADJ, 1, 32>(C, ph, st);
+        else
+            batch_one<Real, RP, ADJ, 1, 0>(C, ph, st);
+    }
+}
+
+template <typename Real, int RP>
+static int batch_launch(const ibf_batch* b, cudaStream_t st)
+{
+    FusedConsts<Real, RP> C;
+    memset(&C, 0, sizeof(C));
+    fill_even_odd(b->plans[0], C);
+    for (const auto& ph : b->phases) {
+        if (b->adjoint)
+            batch_kind<Real, RP, true>(C, ph, st);
+        else
+            batch_kind<Real, RP, false>(C, ph, st);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? IBF_OK : cuda_error(e, "batch launch");
+}
+
+template <typename Real>
+static int batch_dispatch(const ibf_batch* b, cudaStream_t st)
+{
+    switch (b->r) {
+    case 5: return batch_launch<Real, 5>(b, st);
+    case 7: return batch_launch<Real, 7>(b, st);
+    case 9: return batch_launch<Real, 9>(b, st);
+    case 11: return batch_launch<Real, 11>(b, st);
+    default: return set_error(IBF_ERR_UNSUPPORTED, "batch: unsupported r");
+    }
+}
+
+}  // namespace ibf
+
+using namespace ibf;
+
+extern "C" int ibf_batch_create(ibf_plan* const* plans, int count, const int* nrhs, const void* const* in,
+                                void* const* out, int adjoint, ibf_batch** outb)
+{
+    if (!outb) return set_error(IBF_ERR_INVALID, "batch: out is NULL");
+    *outb = nullptr;
+    if (!plans || !nrhs || !in || !out || count < 1) return set_error(IBF_ERR_INVALID, "batch: bad arguments");
+    const ibf_plan* p0 = plans[0];
+    if (!p0) return set_error(IBF_ERR_INVALID, "batch: NULL plan");
+    for (int b = 0; b < count; ++b) {
+        const ibf_plan* p = plans[b];
+        if (!p) return set_error(IBF_ERR_INVALID, "batch: NULL plan");
+        if (p->form != IBF_FORM_STRUCTURED) return set_error(IBF_ERR_UNSUPPORTED, "batch: plans must be structured");
+        if (p->dtype != p0->dtype || p->r != p0->r)
+            return set_error(IBF_ERR_INVALID, "batch: plans must share dtype and r");
+        if (nrhs[b] < 1) return set_error(IBF_ERR_INVALID, "batch: nrhs must be >= 1");
+        if (!in[b] || !out[b]) return set_error(IBF_ERR_INVALID, "batch: NULL vector pointer");
+    }
+    const size_t esz = p0->dtype == IBF_C128 ? sizeof(double2) : sizeof(float2);
+    ibf_batch* B = new ibf_batch();
+    B->dtype = p0->dtype;
+    B->r = p0->r;
+    B->adjoint = adjoint ? 1 : 0;
+    B->count = count;
+    B->plans.assign(plans, plans + count);
+    B->nrhs.assign(nrhs, nrhs + count);
+
+    // per-plan schedules and workspace offsets
+    std::vector<std::vector<Chunk>> sched(count);
+    std::vector<int> rt(count);
+    std::vector<size_t> wsoff(count);
+    size_t ws = 0;
+    int nphase = 0;
+    for (int b = 0; b < count; ++b) {
+        const ibf_plan* p = plans[b];
+        rt[b] = std::min(32, pow2ceil(nrhs[b]));
+        if (p->user_rtile) rt[b] = std::min(rt[b], p->rtile);
+        int kmax = p->user_kfuse ? p->kfuse : fused_kmax(rt[b], p->r, esz);
+        sched[b] = fused_schedule(p->L, p->h, std::max(1, std::min(kmax, kMaxFuse)));
+        nphase = std::max(nphase, (int)sched[b].size());
+        wsoff[b] = ws;
+        ws += ((2 * esz * (size_t)p->N * p->r * nrhs[b]) + 255) / 256 * 256;
+    }
+    int rc = balloc(B, &B->ws, ws);
+    if (rc) {
+        batch_free(B);
+        return rc;
+    }
+    B->ws_bytes = ws;
+
+    // one launch per (chunk index, tile width): plans whose tiles differ get
+    // CTAs sized for their tile, (2^k / 2) * rt threads
+    const int cap = p0->dtype == IBF_C128 ? FusedTraits<double>::kThreads : FusedTraits<float>::kThreads;
+    for (int ph = 0; ph < nphase; ++ph) {
+        for (int kc = 0; kc < 2; ++kc)
+        for (int rtc = 1; rtc <= 32; rtc *= 2) {
+            std::vector<FusedDesc> descs;
+            std::vector<int64_t> start;
+            int64_t blocks = 0;
+            size_t smem = 0;
+            int threads = 32;
+            for (int b = 0; b < count; ++b) {
+                const int nch = (int)sched[b].size();
+                if (ph >= nch || rt[b] != rtc) continue;
+                const ibf_plan* p = plans[b];
+                const Chunk ch = B->adjoint ? sched[b][nch - 1 - ph] : sched[b][ph];
+                if (ch.kind != kc) continue;
+                FusedDesc d;
+                memset(&d, 0, sizeof(d));
+                d.k = ch.hi - ch.lo;
+                d.l0 = ch.lo;
+                d.kind = ch.kind;
+                for (int s = 1; s <= d.k; ++s) d.D[s - 1] = p->stab[ch.lo + s];
+                if (!B->adjoint) {
+                    d.pro = ch.lo == 0 ? PRO_V : PRO_LAMBDA;
+                    d.epi = ch.hi == p->L ? EPI_U : (ch.hi == p->h ? EPI_SWITCH : EPI_LAMBDA);
+                } else {
+                    d.pro = ch.hi == p->L ? PRO_UADJ : PRO_LAMBDA;
+                    d.epi = ch.lo == 0 ? EPI_VADJ : (ch.lo == p->h ? EPI_SWITCH : EPI_LAMBDA);
+                }
+                char* base = (char*)B->ws + wsoff[b];
+                const size_t half = esz * (size_t)p->N * p->r * nrhs[b];
+                d.in = base + (ph & 1) * half;
+                d.out = base + ((ph & 1) ^ 1) * half;
+                d.vin = in[b];
+                d.vout = out[b];
+                d.Vs = p->sV;
+                d.Us = p->sU;
+                d.Ms = p->sM;
+                d.perm = p->d_perm;
+                d.off = p->d_off;
+                d.N = p->N;
+                d.L = p->L;
+                d.nc = nrhs[b];
+                d.rt = rt[b];
+                descs.push_back(d);
+                start.push_back(blocks);
+                const int64_t ntile = (nrhs[b] + rt[b] - 1) / rt[b];
+                blocks += (1LL << (p->L - d.k)) * ntile;
+                smem = std::max(smem, fused_smem_bytes(d.k, rt[b], p->r, esz));
+                threads = std::max(threads, std::min(cap, (1 << (d.k - 1)) * rt[b]));
+            }
+            if (descs.empty()) continue;
+            ibf_batch::Phase P;
+            P.n = (int)descs.size();
+            P.blocks = blocks;
+            P.smem = smem;
+            P.threads = (threads + 31) / 32 * 32;
+            P.kind = kc;
+            P.rt = rtc;
+            if ((rc = balloc(B, (void**)&P.descs, sizeof(FusedDesc) * descs.size())) ||
+                (rc = balloc(B, (void**)&P.start, sizeof(int64_t) * start.size()))) {
+                batch_free(B);
+                return rc;
+            }
+            cudaMemcpy(P.descs, descs.data(), sizeof(FusedDesc) * descs.size(), cudaMemcpyHostToDevice);
+            cudaMemcpy(P.start, start.data(), sizeof(int64_t) * start.size(), cudaMemcpyHostToDevice);
+            B->phases.push_back(P);
+        }
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        batch_free(B);
+        return cuda_error(e, "batch set-up");
+    }
+    *outb = B;
+    return IBF_OK;
+}
+
+extern "C" int ibf_batch_apply(const ibf_batch* b, ibf_stream_t stream)
+{
+    if (!b) return set_error(IBF_ERR_INVALID, "batch is NULL");
+    if (b->dtype == IBF_C128) return batch_dispatch<double>(b, (cudaStream_t)stream);
+    return batch_dispatch<float>(b, (cudaStream_t)stream);
+}
+
+extern "C" int ibf_batch_query(const ibf_batch* b, int what, int64_t* v)
+{
+    if (!b || !v) return set_error(IBF_ERR_INVALID, "NULL argument");
+    switch (what) {
+    case IBF_BQ_LAUNCHES: *v = (int64_t)b->phases.size(); break;
+    case IBF_BQ_WORKSPACE_BYTES: *v = (int64_t)b->ws_bytes; break;
+    case IBF_BQ_COUNT: *v = b->count; break;
+    default: return set_error(IBF_ERR_INVALID, "unknown batch query");
+    }
+    return IBF_OK;
+}
+
+extern "C" int ibf_batch_destroy(ibf_batch* b)
+{
+    if (!b) return IBF_OK;
+    cudaDeviceSynchronize();
+    batch_free(b);
+    return IBF_OK;
+}
+
+// Launch-shape autotuner: time the forward apply of this plan for each
+// candidate (levels per launch, rhs tile) on scratch buffers and keep the
+// fastest.  Candidates: tiles 8, 16, 32 (not above the next power of two of
+// nrhs) and every fusion depth from 2 to the largest that keeps two CTAs per
+// SM.
+extern "C" int ibf_plan_autotune(ibf_plan* p, int nrhs, ibf_stream_t stream, int* best_k, int* best_rt,
+                                 float* best_ms)
+{
+    if (!p || nrhs < 1) return set_error(IBF_ERR_INVALID, "autotune: bad arguments");
+    if (p->form != IBF_FORM_STRUCTURED) return set_error(IBF_ERR_UNSUPPORTED, "autotune: structured plans only");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t esz = p->dtype == IBF_C128 ? sizeof(double2) : sizeof(float2);
+    const size_t bytes = esz * (size_t)p->N * nrhs;
+    void *g = nullptr, *u = nullptr;
+    if (cudaMalloc(&g, bytes) != cudaSuccess || cudaMalloc(&u, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(g);
+        return set_error(IBF_ERR_OOM, "autotune: scratch allocation failed");
+    }
+    cudaMemsetAsync(g, 0, bytes, st);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const bool uk = p->user_kfuse, ur = p->user_rtile;
+    const int ok = p->kfuse, orr = p->rtile;
+    float best = 1e30f;
+    int bk = ok, br = orr, rc = IBF_OK;
+    const int rmax = std::min(32, pow2ceil(std::min(nrhs, p->max_nrhs)));
+    for (int rt = 8; rt <= 32; rt *= 2) {
+        if (rt > rmax && rt != 8) break;
+        const int rtc = std::min(rt, rmax);
+        for (int k = 2; k <= fused_kmax(rtc, p->r, esz); ++k) {
+            p->user_kfuse = p->user_rtile = true;
+            p->kfuse = k;
+            p->rtile = rtc;
+            rc = fused_apply(p, g, u, nrhs, false, st);   // warm-up
+            if (rc) break;
+            cudaEventRecord(e0, st);
+            for (int it = 0; it < 3; ++it) fused_apply(p, g, u, nrhs, false, st);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= 3;
+            if (ms < best) {
+                best = ms;
+                bk = k;
+                br = rtc;
+            }
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(g);
+    cudaFree(u);
+    if (rc) {
+        p->user_kfuse = uk;
+        p->user_rtile = ur;
+        p->kfuse = ok;
+        p->rtile = orr;
+        return rc;
+    }
+    p->user_kfuse = p->user_rtile = true;
+    p->kfuse = bk;
+    p->rtile = br;
+    if (best_k) *best_k = bk;
+    if (best_rt) *best_rt = br;
+    if (best_ms) *best_ms = best;
+    return IBF_OK;
+}

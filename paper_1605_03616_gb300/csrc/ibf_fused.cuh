@@ -68,8 +68,9 @@ struct EO {
     static constexpr int HQ = RP / 2;         // odd rows
 };
 
+// Constants of the transfer matrices, shared by every launch with this r.
 template <typename Real, int RP>
-struct FusedParams {
+struct FusedConsts {
     // Pm[t][s] = (T0[t][s] + T0[RP-1-t][s]) / 2 (t < HQ); Pm[mid][s] = T0[mid][s]
     // Qm[t][s] = (T0[t][s] - T0[RP-1-t][s]) / 2 (t < HQ)
     // E[t][s]  = (T0[s][t] + T0[RP-1-s][t]) / 2 (s < HQ); E[t][mid] = T0[mid][t]
@@ -78,6 +79,10 @@ struct FusedParams {
     Real Qm[EO<RP>::HQ > 0 ? EO<RP>::HQ : 1][RP];
     Real E[RP][EO<RP>::HR];
     Real F[RP][EO<RP>::HQ > 0 ? EO<RP>::HQ : 1];
+};
+
+// One fused launch of one transform: k levels starting at l0.
+struct FusedDesc {
     const void* D[kMaxFuse];     // phase table of step s at D[s-1]
     const void* in;              // Lambda at the launch's input level
     void* out;                   // Lambda at the launch's output level
@@ -89,7 +94,13 @@ struct FusedParams {
     const int32_t* perm;
     const int32_t* off;
     int64_t N;
-    int L, l0, k, nc, rt, pro, epi;
+    int L, l0, k, nc, rt, pro, epi, kind;
+};
+
+template <typename Real, int RP>
+struct FusedParams {
+    FusedConsts<Real, RP> C;
+    FusedDesc d;
 };
 
 __device__ __forceinline__ int brevk(int v, int nbits)
@@ -131,10 +142,10 @@ __device__ __forceinline__ void cacc(C& a, C b)
 // KIND: 0 = H levels (1..h), 1 = G levels (h+1..L).  RT: the rhs tile width
 // when it is known at compile time (32, the batched case), 0 otherwise.
 template <typename Real, int RP, bool ADJ, int KIND, int RT>
-__global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>::kMinBlocks) k_fused(const __grid_constant__ FusedParams<Real, RP> P)
+__device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const FusedDesc& P, int64_t blk,
+                                           unsigned char* smraw)
 {
     typedef typename CT<Real>::T cx;
-    extern __shared__ __align__(16) unsigned char smraw[];
     cx* sm = reinterpret_cast<cx*>(smraw);
 
     const int k = P.k, L = P.L, l0 = P.l0;
@@ -144,8 +155,8 @@ __global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>
     const int PS = RP * rt + 1;
     const int G = 1 << k;
     const int ntile = (P.nc + rt - 1) / rt;
-    const int64_t grp = blockIdx.x / ntile;
-    const int tile = blockIdx.x - (int)(grp * ntile);
+    const int64_t grp = blk / ntile;
+    const int tile = (int)(blk - grp * ntile);
     const int col0 = tile * rt;
     const int ncol = min(rt, P.nc - col0);
     const int nbj = L - l0 - k;                 // bits of jb
@@ -275,7 +286,7 @@ __global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>
                             const Real m1x = y10.x - y11.x, m1y = y10.y - y11.y;
 #pragma unroll
                             for (int t = 0; t < HR; ++t) {
-                                const Real pm = P.Pm[t][s2];
+                                const Real pm = C.Pm[t][s2];
                                 we0[t].x += pm * p0x;
                                 we0[t].y += pm * p0y;
                                 we1[t].x += pm * p1x;
@@ -283,7 +294,7 @@ __global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>
                             }
 #pragma unroll
                             for (int t = 0; t < HQ; ++t) {
-                                const Real qm = P.Qm[t][s2];
+                                const Real qm = C.Qm[t][s2];
                                 wo0[t].x += qm * m0x;
                                 wo0[t].y += qm * m0y;
                                 wo1[t].x += qm * m1x;
@@ -346,13 +357,13 @@ __global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>
                                 cx e = cz<cx>(), f = cz<cx>();
 #pragma unroll
                                 for (int s2 = 0; s2 < HR; ++s2) {
-                                    e.x += P.E[t][s2] * xe[q][s2].x;
-                                    e.y += P.E[t][s2] * xe[q][s2].y;
+                                    e.x += C.E[t][s2] * xe[q][s2].x;
+                                    e.y += C.E[t][s2] * xe[q][s2].y;
                                 }
 #pragma unroll
                                 for (int s2 = 0; s2 < HQ; ++s2) {
-                                    f.x += P.F[t][s2] * xo[q][s2].x;
-                                    f.y += P.F[t][s2] * xo[q][s2].y;
+                                    f.x += C.F[t][s2] * xo[q][s2].x;
+                                    f.y += C.F[t][s2] * xo[q][s2].y;
                                 }
                                 cx z0, z1;   // (T_0^T x_q)[t] and (T_1^T x_q)[RP-1-t]
                                 z0.x = e.x + f.x;
@@ -453,6 +464,36 @@ __global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>
     }
 }
 
+// Single-transform launch.
+template <typename Real, int RP, bool ADJ, int KIND, int RT>
+__global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>::kMinBlocks)
+    k_fused(const __grid_constant__ FusedParams<Real, RP> P)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    fused_body<Real, RP, ADJ, KIND, RT>(P.C, P.d, blockIdx.x, smraw);
+}
+
+// Batched launch: CTA blocks [start[b], start[b+1]) run descriptor b, so one
+// launch covers one fused chunk of many transforms of a batch whatever their
+// sizes (all descriptors of a launch share the level kind and tile width).
+template <typename Real, int RP, bool ADJ, int KIND, int RT>
+__global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>::kMinBlocks)
+    k_fused_batch(const __grid_constant__ FusedConsts<Real, RP> C, const FusedDesc* __restrict__ descs,
+                  const int64_t* __restrict__ start, int n)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    int lo = 0, hi = n - 1;
+    const int64_t b = blockIdx.x;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    fused_body<Real, RP, ADJ, KIND, RT>(C, descs[lo], b - start[lo], smraw);
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -489,23 +530,23 @@ inline int pow2ceil(int v)
 
 // even/odd matrices of T_0 (see struct EO), from the plan's FP64 T_0
 template <typename Real, int RP>
-inline void fill_even_odd(const ibf_plan* p, FusedParams<Real, RP>& P)
+inline void fill_even_odd(const ibf_plan* p, FusedConsts<Real, RP>& C)
 {
     constexpr int HQ = EO<RP>::HQ;
     const auto& T0 = p->T[0];
     for (int t = 0; t < HQ; ++t)
         for (int s = 0; s < RP; ++s) {
-            P.Pm[t][s] = (Real)((T0[t][s] + T0[RP - 1 - t][s]) / 2);
-            P.Qm[t][s] = (Real)((T0[t][s] - T0[RP - 1 - t][s]) / 2);
+            C.Pm[t][s] = (Real)((T0[t][s] + T0[RP - 1 - t][s]) / 2);
+            C.Qm[t][s] = (Real)((T0[t][s] - T0[RP - 1 - t][s]) / 2);
         }
     if (RP & 1)
-        for (int s = 0; s < RP; ++s) P.Pm[HQ][s] = (Real)T0[HQ][s];
+        for (int s = 0; s < RP; ++s) C.Pm[HQ][s] = (Real)T0[HQ][s];
     for (int t = 0; t < RP; ++t) {
         for (int s = 0; s < HQ; ++s) {
-            P.E[t][s] = (Real)((T0[s][t] + T0[RP - 1 - s][t]) / 2);
-            P.F[t][s] = (Real)((T0[s][t] - T0[RP - 1 - s][t]) / 2);
+            C.E[t][s] = (Real)((T0[s][t] + T0[RP - 1 - s][t]) / 2);
+            C.F[t][s] = (Real)((T0[s][t] - T0[RP - 1 - s][t]) / 2);
         }
-        if (RP & 1) P.E[t][HQ] = (Real)T0[HQ][t];
+        if (RP & 1) C.E[t][HQ] = (Real)T0[HQ][t];
     }
 }
 
@@ -544,13 +585,13 @@ template <typename Real, int RP, bool ADJ, int KIND>
 static int launch_one(const FusedParams<Real, RP>& P, int64_t ngroups, cudaStream_t st)
 {
     typedef typename CT<Real>::T cx;
-    const int G = 1 << P.k;
-    size_t smem = fused_smem_bytes(P.k, P.rt, RP, sizeof(cx));
-    int ntile = (P.nc + P.rt - 1) / P.rt;
-    int threads = std::min(FusedTraits<Real>::kThreads, std::max(32, (G / 2) * P.rt));
+    const int G = 1 << P.d.k;
+    size_t smem = fused_smem_bytes(P.d.k, P.d.rt, RP, sizeof(cx));
+    int ntile = (P.d.nc + P.d.rt - 1) / P.d.rt;
+    int threads = std::min(FusedTraits<Real>::kThreads, std::max(32, (G / 2) * P.d.rt));
     threads = (threads + 31) / 32 * 32;
     int64_t blocks = ngroups * ntile;
-    if (P.rt == 32) {
+    if (P.d.rt == 32) {
         set_smem_attr<Real, RP, ADJ, KIND, 32>();
         k_fused<Real, RP, ADJ, KIND, 32><<<(unsigned)blocks, threads, smem, st>>>(P);
     } else {
@@ -566,14 +607,14 @@ static int fused_run(ibf_plan* p, const void* vin, void* vout, int nrhs, bool ad
     typedef typename CT<Real>::T cx;
     FusedParams<Real, RP> P;
     memset(&P, 0, sizeof(P));
-    fill_even_odd(p, P);
-    P.Vs = p->sV;
-    P.Us = p->sU;
-    P.Ms = p->sM;
-    P.perm = p->d_perm;
-    P.off = p->d_off;
-    P.N = p->N;
-    P.L = p->L;
+    fill_even_odd(p, P.C);
+    P.d.Vs = p->sV;
+    P.d.Us = p->sU;
+    P.d.Ms = p->sM;
+    P.d.perm = p->d_perm;
+    P.d.off = p->d_off;
+    P.d.N = p->N;
+    P.d.L = p->L;
     const int64_t N = p->N;
     for (int c0 = 0; c0 < nrhs; c0 += p->max_nrhs) {
         const int nc = std::min(p->max_nrhs, nrhs - c0);
@@ -581,30 +622,31 @@ static int fused_run(ibf_plan* p, const void* vin, void* vout, int nrhs, bool ad
         int kmax = p->user_kfuse ? p->kfuse : fused_kmax(rt, RP, sizeof(cx));
         kmax = std::max(1, std::min(kmax, kMaxFuse));
         std::vector<Chunk> sched = fused_schedule(p->L, p->h, kmax);
-        P.nc = nc;
-        P.rt = rt;
-        P.vin = (const cx*)vin + N * c0;
-        P.vout = (cx*)vout + N * c0;
+        P.d.nc = nc;
+        P.d.rt = rt;
+        P.d.vin = (const cx*)vin + N * c0;
+        P.d.vout = (cx*)vout + N * c0;
         void* bufs[2] = {p->ws[0], p->ws[1]};
         int cur = 0;   // buffer holding the current Lambda
         const int nch = (int)sched.size();
         prof_start(p, st);
         for (int ci = 0; ci < nch; ++ci) {
             const Chunk ch = adj ? sched[nch - 1 - ci] : sched[ci];
-            P.l0 = ch.lo;
-            P.k = ch.hi - ch.lo;
-            for (int s = 1; s <= P.k; ++s) P.D[s - 1] = p->stab[ch.lo + s];
-            for (int s = P.k; s < kMaxFuse; ++s) P.D[s] = nullptr;
+            P.d.l0 = ch.lo;
+            P.d.kind = ch.kind;
+            P.d.k = ch.hi - ch.lo;
+            for (int s = 1; s <= P.d.k; ++s) P.d.D[s - 1] = p->stab[ch.lo + s];
+            for (int s = P.d.k; s < kMaxFuse; ++s) P.d.D[s] = nullptr;
             if (!adj) {
-                P.pro = ch.lo == 0 ? PRO_V : PRO_LAMBDA;
-                P.epi = ch.hi == p->L ? EPI_U : (ch.hi == p->h ? EPI_SWITCH : EPI_LAMBDA);
+                P.d.pro = ch.lo == 0 ? PRO_V : PRO_LAMBDA;
+                P.d.epi = ch.hi == p->L ? EPI_U : (ch.hi == p->h ? EPI_SWITCH : EPI_LAMBDA);
             } else {
-                P.pro = ch.hi == p->L ? PRO_UADJ : PRO_LAMBDA;
-                P.epi = ch.lo == 0 ? EPI_VADJ : (ch.lo == p->h ? EPI_SWITCH : EPI_LAMBDA);
+                P.d.pro = ch.hi == p->L ? PRO_UADJ : PRO_LAMBDA;
+                P.d.epi = ch.lo == 0 ? EPI_VADJ : (ch.lo == p->h ? EPI_SWITCH : EPI_LAMBDA);
             }
-            P.in = bufs[cur];
-            P.out = bufs[cur ^ 1];
-            const int64_t ngroups = 1LL << (p->L - P.k);
+            P.d.in = bufs[cur];
+            P.d.out = bufs[cur ^ 1];
+            const int64_t ngroups = 1LL << (p->L - P.d.k);
             int rc;
             if (!adj)
                 rc = ch.kind == 0 ? launch_one<Real, RP, false, 0>(P, ngroups, st)

@@ -56,36 +56,37 @@ static int static_run(const ibf_plan* p, const void* vin, void* vout, int nrhs, 
     typedef typename CT<Real>::T cx;
     FusedParams<Real, RP> P;
     memset(&P, 0, sizeof(P));
-    fill_even_odd(p, P);
-    P.Vs = p->sV;
-    P.Us = p->sU;
-    P.Ms = p->sM;
-    P.perm = p->d_perm;
-    P.off = p->d_off;
-    P.N = p->N;
-    P.L = p->L;
+    fill_even_odd(p, P.C);
+    P.d.Vs = p->sV;
+    P.d.Us = p->sU;
+    P.d.Ms = p->sM;
+    P.d.perm = p->d_perm;
+    P.d.off = p->d_off;
+    P.d.N = p->N;
+    P.d.L = p->L;
     const int64_t N = p->N;
     for (int c0 = 0; c0 < nrhs; c0 += max_cols) {
         const int nc = std::min(max_cols, nrhs - c0);
         const int rt = std::min(32, pow2ceil(nc));
         const int kmax = fused_kmax(rt, RP, sizeof(cx));
         std::vector<Chunk> sched = fused_schedule(p->L, p->h, kmax);
-        P.nc = nc;
-        P.rt = rt;
-        P.vin = (const cx*)vin + N * c0;
-        P.vout = (cx*)vout + N * c0;
+        P.d.nc = nc;
+        P.d.rt = rt;
+        P.d.vin = (const cx*)vin + N * c0;
+        P.d.vout = (cx*)vout + N * c0;
         void* bufs[2] = {buf0, buf1};
         int cur = 0;
         for (const Chunk& ch : sched) {
-            P.l0 = ch.lo;
-            P.k = ch.hi - ch.lo;
-            for (int s = 1; s <= P.k; ++s) P.D[s - 1] = p->stab[ch.lo + s];
-            for (int s = P.k; s < kMaxFuse; ++s) P.D[s] = nullptr;
-            P.pro = ch.lo == 0 ? PRO_V : PRO_LAMBDA;
-            P.epi = ch.hi == p->L ? EPI_U : (ch.hi == p->h ? EPI_SWITCH : EPI_LAMBDA);
-            P.in = bufs[cur];
-            P.out = bufs[cur ^ 1];
-            const int64_t ngroups = 1LL << (p->L - P.k);
+            P.d.l0 = ch.lo;
+            P.d.kind = ch.kind;
+            P.d.k = ch.hi - ch.lo;
+            for (int s = 1; s <= P.d.k; ++s) P.d.D[s - 1] = p->stab[ch.lo + s];
+            for (int s = P.d.k; s < kMaxFuse; ++s) P.d.D[s] = nullptr;
+            P.d.pro = ch.lo == 0 ? PRO_V : PRO_LAMBDA;
+            P.d.epi = ch.hi == p->L ? EPI_U : (ch.hi == p->h ? EPI_SWITCH : EPI_LAMBDA);
+            P.d.in = bufs[cur];
+            P.d.out = bufs[cur ^ 1];
+            const int64_t ngroups = 1LL << (p->L - P.d.k);
             if (ch.kind == 0)
                 launch_one<Real, RP, false, 0>(P, ngroups, st);
             else

@@ -1,0 +1,86 @@
+"""Batched apply of many uneven plans (one launch per fused chunk index),
+its CUDA-graph capture, and the launch-shape autotuner."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ibf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1605_03616_gb300 as m
+    return m
+
+
+def _rel(a, b):
+    return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+
+def _make(ibf, count, seed, emin=6, emax=12, nmax=40):
+    rng = W.rng(seed)
+    Ns = [1 << int(e) for e in rng.integers(emin, emax + 1, count)]
+    nrhs = [int(v) for v in rng.integers(1, nmax + 1, count)]
+    plans = [ibf.Plan(ibf.PHASE_FIO1D, N, 9, ibf.C64_FP32, max_nrhs=k) for N, k in zip(Ns, nrhs)]
+    ins = [torch.from_numpy(W.complex_normal((k, N), rng, dtype=np.complex64)).cuda() for N, k in zip(Ns, nrhs)]
+    outs = [torch.full_like(t, float("nan")) for t in ins]
+    return Ns, nrhs, plans, ins, outs
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_batch_matches_per_plan_and_oracle(ibf, adjoint):
+    Ns, nrhs, plans, ins, outs = _make(ibf, 12, 200 + adjoint)
+    batch = ibf.Batch(plans, ins, outs, adjoint=adjoint)
+    assert batch.query(ibf.BQ_LAUNCHES) <= 12 * (max(p.query(ibf.Q_LAUNCHES) for p in plans) + 2)
+    batch.apply()
+    torch.cuda.synchronize()
+    for b, (p, g, u) in enumerate(zip(plans, ins, outs)):
+        ref = torch.empty_like(g)
+        raw = p.adjoint_raw if adjoint else p.apply_raw
+        raw(g.data_ptr(), ref.data_ptr(), g.shape[0], torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert _rel(u, ref) < 1e-6, b
+        if b < 3:
+            x = W.uniform_x(Ns[b])
+            gn = g.cpu().numpy().T.astype(np.complex128)
+            fn = O.ibf_adjoint_1d if adjoint else O.ibf_apply_1d
+            assert O.rel_l2(u.cpu().numpy().T, fn(O.PHASE_FIO1D, Ns[b], 9, x, gn)) < 1e-5
+
+
+def test_batch_graph_capture(ibf):
+    Ns, nrhs, plans, ins, outs = _make(ibf, 8, 300)
+    batch = ibf.Batch(plans, ins, outs)
+    batch.apply()
+    torch.cuda.synchronize()
+    first = [o.clone() for o in outs]
+    for o in outs:
+        o.fill_(0)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        batch.apply(stream=s)
+    graph.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(outs, first):
+        assert torch.equal(a, b)
+
+
+def test_autotune_keeps_results(ibf):
+    N, nrhs = 1 << 12, 24
+    plan = ibf.Plan(ibf.PHASE_FIO1D, N, 9, ibf.C64_FP32, max_nrhs=nrhs)
+    g = torch.from_numpy(W.complex_normal((N, nrhs), W.rng(400), dtype=np.complex64)).cuda()
+    before = plan.apply(g)
+    k, rt, ms = plan.autotune(nrhs)
+    assert 2 <= k <= 10 and rt in (8, 16, 32) and ms > 0
+    assert plan.query(ibf.Q_LEVELS_PER_LAUNCH) == k and plan.query(ibf.Q_RHS_TILE) == rt
+    after = plan.apply(g)
+    assert _rel(after, before) < 1e-6
