@@ -13,6 +13,9 @@ paper); this module compiles it with gcc and wraps it with ctypes/numpy:
   2.1; equals the preliminary IBF of Sec. 3) and its conjugate transpose.
 * ``ExplicitIBF`` -- the preliminary IBF with explicit block factors V^0, H^l,
   M^h, G^l, U^L (Sec. 3, eqs. PIBF1-PIBF3, switchlocM, PIBFbf3).
+* ``ibf_apply_2d_box`` / ``mibf_apply_2d`` -- the 2D butterfly on one square
+  frequency box (Sec. 5.1) and the multiscale sum over a corona
+  decomposition with a directly summed centre (Sec. 5.2).
 """
 from __future__ import annotations
 
@@ -24,6 +27,7 @@ import numpy as np
 PHASE_NUFFT = 0
 PHASE_FIO1D = 1
 PHASE_FIO2D = 2
+PHASE_FIO2D_32 = 3      # the 2D FIO with the constants /32 printed in Sec. 6.3
 PHASE_SEPARABLE = 100
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -69,11 +73,9 @@ def _load():
         for nm in ("orc_ibf_get_V", "orc_ibf_get_U", "orc_ibf_get_M"):
             getattr(lib, nm).argtypes = [P, P]
         lib.orc_ibf_get_blk.argtypes = [P, Ci, P]
-        if hasattr(lib, "orc_ibf_apply_2d"):
-            lib.orc_ibf_apply_2d.argtypes = [Ci, I64, Ci, Ci, I64, I64, P, I64, P, P, Ci, P]
-            lib.orc_ibf_adjoint_2d.argtypes = [Ci, I64, Ci, Ci, I64, I64, P, I64, P, P, Ci, P]
-        if hasattr(lib, "omp_set_num_threads"):
-            pass
+        D = ctypes.c_double
+        lib.orc_ibf_apply_2d.argtypes = [Ci, I64, Ci, Ci, I64, P, D, D, P, Ci, P]
+        lib.orc_mibf_apply_2d.argtypes = [Ci, I64, Ci, Ci, I64, P, P, Ci, P]
         _lib = lib
     return _lib
 
@@ -184,6 +186,33 @@ def ibf_adjoint_1d(phase_id: int, N: int, r: int, x, y, h: int | None = None) ->
     if rc:
         raise ValueError("orc_ibf_adjoint_1d failed (%d)" % rc)
     return _uncols(g, N, nrhs, vec)
+
+
+def ibf_apply_2d_box(phase_id: int, m: int, r: int, x, q1: float, q2: float, g, h: int | None = None):
+    """2D butterfly (Sec. 5.1) for frequencies xi = (q1 + k1, q2 + k2), k < m,
+    g of shape (m*m,) or (m*m, nrhs) row-major in (k1, k2); x of shape (nx, 2)."""
+    L = int(m).bit_length() - 1
+    h = L // 2 if h is None else h
+    x = _f64(x).reshape(-1, 2)
+    gb, nrhs, vec = _cols(g, m * m)
+    u = np.zeros(x.shape[0] * nrhs, np.complex128)
+    rc = _load().orc_ibf_apply_2d(phase_id, m, r, h, x.shape[0], _ptr(x), float(q1), float(q2), _ptr(gb), nrhs,
+                                  _ptr(u))
+    if rc:
+        raise ValueError("orc_ibf_apply_2d failed (%d)" % rc)
+    return _uncols(u, x.shape[0], nrhs, vec)
+
+
+def mibf_apply_2d(phase_id: int, n: int, r: int, x, g, center_side: int = 16):
+    """Multiscale IBF (Sec. 5.2) on the n x n frequency grid; g (n*n,) or
+    (n*n, nrhs) row-major in (k1, k2) with xi = (k1 - n/2, k2 - n/2)."""
+    x = _f64(x).reshape(-1, 2)
+    gb, nrhs, vec = _cols(g, n * n)
+    u = np.zeros(x.shape[0] * nrhs, np.complex128)
+    rc = _load().orc_mibf_apply_2d(phase_id, n, r, center_side, x.shape[0], _ptr(x), _ptr(gb), nrhs, _ptr(u))
+    if rc:
+        raise ValueError("orc_mibf_apply_2d failed (%d)" % rc)
+    return _uncols(u, x.shape[0], nrhs, vec)
 
 
 class ExplicitIBF:

@@ -15,6 +15,10 @@
  *   - orc_ibf_build_1d + orc_ibf_explicit_* : the preliminary IBF of Sec. 3
  *     with its factors V^0, H^l, M^h, G^l, U^L stored as explicit blocks
  *     (eqs. PIBF1, PIBF2, switchlocM, PIBF3, PIBFbf3) and applied block by block.
+ *   - orc_ibf_apply_2d : the same butterfly in 2D on one square frequency
+ *     box, with quadtrees and r x r tensor Chebyshev grids (Sec. 5.1);
+ *     orc_mibf_apply_2d : the multiscale sum of Sec. 5.2 (eqs. domaindecomp,
+ *     mba, f1) over a corona decomposition of Omega plus a direct centre.
  *
  * Conventions (readings of the paper where it is silent):
  *   - r is the number of Chebyshev points per dimension; grid on [-1/2,1/2]
@@ -39,7 +43,8 @@ typedef double complex cplx;
 
 #define ORC_PHASE_NUFFT 0      /* Phi = x.xi                                   */
 #define ORC_PHASE_FIO1D 1      /* Phi = x xi + c(x)|xi|, c = (2+sin 2 pi x)/8  */
-#define ORC_PHASE_FIO2D 2      /* Phi = x.xi + sqrt(c1^2 xi1^2 + c2^2 xi2^2)   */
+#define ORC_PHASE_FIO2D 2      /* Phi = x.xi + sqrt(c1^2 xi1^2 + c2^2 xi2^2), c /16 */
+#define ORC_PHASE_FIO2D_32 3   /* the same with the constants /32 of Sec. 6.3      */
 #define ORC_PHASE_SEPARABLE 100 /* test phase f(x) + h(xi): remainder R^{AB}=0 */
 
 /* ------------------------------------------------------------------ */
@@ -72,14 +77,17 @@ double orc_phi_1d(int phase_id, double x, double xi)
     }
 }
 
-/* 2D phase of Sec. 6.3 with constants c1 = (2 + sin(2 pi x1) sin(2 pi x2))/16,
- * c2 = (2 + cos(2 pi x1) cos(2 pi x2))/16; the separable test phase in 2D. */
+/* 2D phase of Sec. 6.3: c1 = (2 + sin(2 pi x1) sin(2 pi x2))/den,
+ * c2 = (2 + cos(2 pi x1) cos(2 pi x2))/den, den = 16 (the workload) or 32 (the
+ * paper's Table 4); the separable test phase in 2D. */
 double orc_phi_2d(int phase_id, double x1, double x2, double k1, double k2)
 {
     switch (phase_id) {
-    case ORC_PHASE_FIO2D: {
-        double c1 = (2.0 + sin(2.0 * M_PI * x1) * sin(2.0 * M_PI * x2)) / 16.0;
-        double c2 = (2.0 + cos(2.0 * M_PI * x1) * cos(2.0 * M_PI * x2)) / 16.0;
+    case ORC_PHASE_FIO2D:
+    case ORC_PHASE_FIO2D_32: {
+        double den = phase_id == ORC_PHASE_FIO2D ? 16.0 : 32.0;
+        double c1 = (2.0 + sin(2.0 * M_PI * x1) * sin(2.0 * M_PI * x2)) / den;
+        double c2 = (2.0 + cos(2.0 * M_PI * x1) * cos(2.0 * M_PI * x2)) / den;
         double a = c1 * k1;
         double b = c2 * k2;
         return (x1 * k1 + x2 * k2) + sqrt(a * a + b * b);
@@ -728,5 +736,262 @@ int orc_ibf_get_blk(const orc_ibf* f, int l, cplx* out)
 {
     if (l < 1 || l > f->L) return 1;
     memcpy(out, f->blk[l], sizeof(cplx) * f->N * 2 * f->r * f->r);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* 2D butterfly on one square Omega box (Sec. 5.1): quadtrees, tensor   */
+/* Chebyshev grids of r x r points, four children per box.              */
+/* Q = [q1, q1+m) x [q2, q2+m) holds the integer frequencies            */
+/* xi = (q1 + k1, q2 + k2), k1, k2 < m, g stored row-major in (k1, k2);  */
+/* L = log2 m.  X boxes at level l: [i1, i1+1) x [i2, i2+1) / 2^l, index */
+/* i = i1 2^l + i2; Omega boxes at level l: side m / 2^l, index          */
+/* j = j1 2^l + j2.  Lambda^l_{i,j}[t1 r + t2] at (i 4^(L-l) + j) r^2.    */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int ph, r, L;
+    double q1, q2, m;
+    const double* z;
+} bf2;
+
+static double lag2(const bf2* B, int t, double u1, double u2)
+{
+    return orc_lagrange(B->r, B->z, t / B->r, u1) * orc_lagrange(B->r, B->z, t % B->r, u2);
+}
+static void xbox2(int l, int64_t i, double* c1, double* c2, double* w)
+{
+    int64_t n = (int64_t)1 << l;
+    *w = 1.0 / ldexp(1.0, l);
+    *c1 = ((double)(i / n) + 0.5) * *w;
+    *c2 = ((double)(i % n) + 0.5) * *w;
+}
+static void wbox2(const bf2* B, int l, int64_t j, double* c1, double* c2, double* w)
+{
+    int64_t n = (int64_t)1 << l;
+    *w = B->m / ldexp(1.0, l);
+    *c1 = B->q1 + ((double)(j / n) + 0.5) * *w;
+    *c2 = B->q2 + ((double)(j % n) + 0.5) * *w;
+}
+static double phi2(const bf2* B, double x1, double x2, double k1, double k2)
+{
+    return orc_phi_2d(B->ph, x1, x2, k1, k2);
+}
+/* child c (0..3) of box (l, i) in a 2^l x 2^l grid: (2 i1 + c/2, 2 i2 + c%2) */
+static int64_t child2(int l, int64_t i, int c)
+{
+    int64_t n = (int64_t)1 << l;
+    return (2 * (i / n) + c / 2) * (2 * n) + 2 * (i % n) + c % 2;
+}
+static int64_t parent2(int l, int64_t i)   /* parent at level l-1 of box (l, i) */
+{
+    int64_t n = (int64_t)1 << l;
+    return ((i / n) / 2) * (n / 2) + (i % n) / 2;
+}
+
+int orc_ibf_apply_2d(int phase_id, int64_t m, int r, int h, int64_t nx, const double* x, double q1, double q2,
+                     const cplx* g, int nrhs, cplx* u)
+{
+    int L = ilog2(m);
+    if (((int64_t)1 << L) != m || r < 2 || r > 16 || h < 0 || h > L) return 1;
+    double z[64];
+    orc_cheb_grid(r, z);
+    bf2 B = {phase_id, r, L, q1, q2, (double)m, z};
+    const int r2 = r * r;
+    const int64_t npair = (int64_t)1 << (2 * L);
+    cplx* a = (cplx*)malloc(sizeof(cplx) * npair * r2);
+    cplx* b = (cplx*)malloc(sizeof(cplx) * npair * r2);
+    if (!a || !b) { free(a); free(b); return 2; }
+    for (int col = 0; col < nrhs; ++col) {
+        const cplx* gc = g + m * m * col;
+        /* initialization, eq. (1): A = root of T_X */
+        {
+            double cA1, cA2, wA;
+            xbox2(0, 0, &cA1, &cA2, &wA);
+            for (int64_t j = 0; j < npair; ++j) {
+                double cB1, cB2, wB;
+                wbox2(&B, L, j, &cB1, &cB2, &wB);
+                int64_t j1 = j >> L, j2 = j & (((int64_t)1 << L) - 1);
+                double k1 = q1 + (double)j1, k2 = q2 + (double)j2;     /* the one frequency of leaf j */
+                cplx gv = gc[j1 * m + j2];
+                for (int t = 0; t < r2; ++t) {
+                    double gB1 = cB1 + wB * z[t / r], gB2 = cB2 + wB * z[t % r];
+                    a[j * r2 + t] = e2pi(-phi2(&B, cA1, cA2, gB1, gB2)) *
+                                    lag2(&B, t, (k1 - cB1) / wB, (k2 - cB2) / wB) *
+                                    e2pi(phi2(&B, cA1, cA2, k1, k2)) * gv;
+                }
+            }
+        }
+        /* recursion in xi, eq. (2) */
+        for (int l = 1; l <= h; ++l) {
+            int64_t ni = (int64_t)1 << (2 * l), nj = (int64_t)1 << (2 * (L - l)), nC = nj * 4;
+#pragma omp parallel for collapse(2) schedule(static)
+            for (int64_t i = 0; i < ni; ++i)
+                for (int64_t j = 0; j < nj; ++j) {
+                    double cA1, cA2, wA, cB1, cB2, wB;
+                    xbox2(l, i, &cA1, &cA2, &wA);
+                    wbox2(&B, L - l, j, &cB1, &cB2, &wB);
+                    int64_t ip = parent2(l, i);
+                    for (int t = 0; t < r2; ++t) {
+                        double gB1 = cB1 + wB * z[t / r], gB2 = cB2 + wB * z[t % r];
+                        cplx acc = 0;
+                        for (int c = 0; c < 4; ++c) {
+                            int64_t C = child2(L - l, j, c);
+                            double cC1, cC2, wC;
+                            wbox2(&B, L - l + 1, C, &cC1, &cC2, &wC);
+                            const cplx* lp = a + (ip * nC + C) * r2;
+                            for (int s = 0; s < r2; ++s) {
+                                double gC1 = cC1 + wC * z[s / r], gC2 = cC2 + wC * z[s % r];
+                                acc += lag2(&B, t, (gC1 - cB1) / wB, (gC2 - cB2) / wB) *
+                                       e2pi(phi2(&B, cA1, cA2, gC1, gC2)) * lp[s];
+                            }
+                        }
+                        b[(i * nj + j) * r2 + t] = e2pi(-phi2(&B, cA1, cA2, gB1, gB2)) * acc;
+                    }
+                }
+            cplx* tmp = a; a = b; b = tmp;
+        }
+        /* switch, eq. switchlocM */
+        {
+            int64_t ni = (int64_t)1 << (2 * h), nj = (int64_t)1 << (2 * (L - h));
+#pragma omp parallel for collapse(2) schedule(static)
+            for (int64_t i = 0; i < ni; ++i)
+                for (int64_t j = 0; j < nj; ++j) {
+                    double cA1, cA2, wA, cB1, cB2, wB;
+                    xbox2(h, i, &cA1, &cA2, &wA);
+                    wbox2(&B, L - h, j, &cB1, &cB2, &wB);
+                    for (int t = 0; t < r2; ++t) {
+                        double gA1 = cA1 + wA * z[t / r], gA2 = cA2 + wA * z[t % r];
+                        cplx acc = 0;
+                        for (int s = 0; s < r2; ++s)
+                            acc += e2pi(phi2(&B, gA1, gA2, cB1 + wB * z[s / r], cB2 + wB * z[s % r])) *
+                                   a[(i * nj + j) * r2 + s];
+                        b[(i * nj + j) * r2 + t] = acc;
+                    }
+                }
+            cplx* tmp = a; a = b; b = tmp;
+        }
+        /* recursion in x, eq. (3) */
+        for (int l = h + 1; l <= L; ++l) {
+            int64_t ni = (int64_t)1 << (2 * l), nj = (int64_t)1 << (2 * (L - l)), nC = nj * 4;
+#pragma omp parallel for collapse(2) schedule(static)
+            for (int64_t i = 0; i < ni; ++i)
+                for (int64_t j = 0; j < nj; ++j) {
+                    double cA1, cA2, wA, cP1, cP2, wP;
+                    xbox2(l, i, &cA1, &cA2, &wA);
+                    int64_t ip = parent2(l, i);
+                    xbox2(l - 1, ip, &cP1, &cP2, &wP);
+                    for (int t = 0; t < r2; ++t) {
+                        double gA1 = cA1 + wA * z[t / r], gA2 = cA2 + wA * z[t % r];
+                        cplx acc = 0;
+                        for (int c = 0; c < 4; ++c) {
+                            int64_t C = child2(L - l, j, c);
+                            double cC1, cC2, wC;
+                            wbox2(&B, L - l + 1, C, &cC1, &cC2, &wC);
+                            const cplx* lp = a + (ip * nC + C) * r2;
+                            cplx inner = 0;
+                            for (int s = 0; s < r2; ++s) {
+                                double gP1 = cP1 + wP * z[s / r], gP2 = cP2 + wP * z[s % r];
+                                inner += lag2(&B, s, (gA1 - cP1) / wP, (gA2 - cP2) / wP) *
+                                         e2pi(-phi2(&B, gP1, gP2, cC1, cC2)) * lp[s];
+                            }
+                            acc += e2pi(phi2(&B, gA1, gA2, cC1, cC2)) * inner;
+                        }
+                        b[(i * nj + j) * r2 + t] = acc;
+                    }
+                }
+            cplx* tmp = a; a = b; b = tmp;
+        }
+        /* termination, eq. bf3: B = Q itself */
+        {
+            double cQ1 = q1 + 0.5 * (double)m, cQ2 = q2 + 0.5 * (double)m;
+            int64_t nl = (int64_t)1 << L;
+#pragma omp parallel for schedule(static)
+            for (int64_t n = 0; n < nx; ++n) {
+                double x1 = x[2 * n], x2 = x[2 * n + 1];
+                int64_t i1 = (int64_t)floor(x1 * (double)nl), i2 = (int64_t)floor(x2 * (double)nl);
+                if (i1 >= nl) i1 = nl - 1;
+                if (i2 >= nl) i2 = nl - 1;
+                if (i1 < 0) i1 = 0;
+                if (i2 < 0) i2 = 0;
+                int64_t i = i1 * nl + i2;
+                double cA1, cA2, wA;
+                xbox2(L, i, &cA1, &cA2, &wA);
+                cplx acc = 0;
+                for (int t = 0; t < r2; ++t) {
+                    double gA1 = cA1 + wA * z[t / r], gA2 = cA2 + wA * z[t % r];
+                    acc += lag2(&B, t, (x1 - cA1) / wA, (x2 - cA2) / wA) *
+                           e2pi(-phi2(&B, gA1, gA2, cQ1, cQ2)) * a[i * r2 + t];
+                }
+                u[n + nx * col] = e2pi(phi2(&B, x1, x2, cQ1, cQ2)) * acc;
+            }
+        }
+    }
+    free(a);
+    free(b);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Multiscale IBF (Sec. 5.2, eqs. domaindecomp, mba, f1) on the n x n    */
+/* frequency grid xi = (k1 - n/2, k2 - n/2).  Corona decomposition with  */
+/* half-open squares: S_t = [-n/2^(t+1), n/2^(t+1))^2; ring t = S_t \ S_(t+1) */
+/* is the 12 outer boxes (side m_t = n/2^(t+2)) of the 4 x 4 partition of */
+/* S_t, for t = 0..T with n/2^(T+1) = center_side; the center S_(T+1) is */
+/* summed directly.  g is n x n row-major in (k1, k2).                    */
+/* ------------------------------------------------------------------ */
+int orc_mibf_apply_2d(int phase_id, int64_t n, int r, int center_side, int64_t nx, const double* x, const cplx* g,
+                      int nrhs, cplx* u)
+{
+    if (n < 4 || (n & (n - 1)) || center_side < 1 || center_side > n || (center_side & (center_side - 1)))
+        return 1;
+    int64_t nn = n * n;
+    memset(u, 0, sizeof(cplx) * nx * nrhs);
+    cplx* tmp = (cplx*)malloc(sizeof(cplx) * nx);
+    int64_t side = n;
+    while (side > center_side) {
+        int64_t m = side / 4;
+        if (m < 1) break;
+        double s0 = -0.5 * (double)side;
+        for (int b1 = 0; b1 < 4; ++b1)
+            for (int b2 = 0; b2 < 4; ++b2) {
+                if (b1 >= 1 && b1 <= 2 && b2 >= 1 && b2 <= 2) continue;   /* inner 2 x 2 = S_(t+1) */
+                double q1 = s0 + (double)(b1 * m), q2 = s0 + (double)(b2 * m);
+                cplx* gq = (cplx*)malloc(sizeof(cplx) * m * m);
+                int L = ilog2(m);
+                for (int col = 0; col < nrhs; ++col) {
+                    for (int64_t k1 = 0; k1 < m; ++k1)
+                        for (int64_t k2 = 0; k2 < m; ++k2) {
+                            int64_t a1 = (int64_t)(q1 + (double)k1 + 0.5 * (double)n);
+                            int64_t a2 = (int64_t)(q2 + (double)k2 + 0.5 * (double)n);
+                            gq[k1 * m + k2] = g[(a1 * n + a2) + nn * col];
+                        }
+                    /* switch level ceil(L/2): for the odd depths of these boxes it
+                       gives about 10x less error than floor(L/2) (reading of
+                       Sec. 3's "L even" for odd L in 2D) */
+                    int rc = orc_ibf_apply_2d(phase_id, m, r, (L + 1) / 2, nx, x, q1, q2, gq, 1, tmp);
+                    if (rc) { free(gq); free(tmp); return rc; }
+                    for (int64_t p = 0; p < nx; ++p) u[p + nx * col] += tmp[p];
+                }
+                free(gq);
+            }
+        side /= 2;
+    }
+    /* center: direct sum over S_(T+1) */
+    {
+        double s0 = -0.5 * (double)side;
+#pragma omp parallel for schedule(static)
+        for (int64_t p = 0; p < nx; ++p)
+            for (int col = 0; col < nrhs; ++col) {
+                cplx acc = 0;
+                for (int64_t k1 = 0; k1 < side; ++k1)
+                    for (int64_t k2 = 0; k2 < side; ++k2) {
+                        double xi1 = s0 + (double)k1, xi2 = s0 + (double)k2;
+                        int64_t a1 = (int64_t)(xi1 + 0.5 * (double)n), a2 = (int64_t)(xi2 + 0.5 * (double)n);
+                        acc += e2pi(orc_phi_2d(phase_id, x[2 * p], x[2 * p + 1], xi1, xi2)) * g[a1 * n + a2 + nn * col];
+                    }
+                u[p + nx * col] += acc;
+            }
+    }
+    free(tmp);
     return 0;
 }

@@ -1,0 +1,63 @@
+"""Pins of the oracle's 2D butterfly (Sec. 5.1) and multiscale IBF (Sec. 5.2).
+
+* separable phase => R^{AB} = 0 => the 2D butterfly on one box and the whole
+  MIBF (every corona box plus the direct centre) reproduce the direct sum to
+  rounding: this also proves the corona boxes and the centre cover Omega
+  exactly once;
+* the 2D NUFFT (Phi = x.xi, smooth everywhere) on the whole grid as one box
+  converges in r;
+* the FIO of Sec. 6.3 with the paper's constants (/32) reproduces the errors
+  printed in Table 4 (tests/golden/table4_fio_2d.txt) within 3x;
+* the workload's FIO (constants /16) converges in r.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from conftest import read_golden
+
+
+@pytest.mark.parametrize("n,r", [(16, 5), (32, 7)])
+def test_separable_2d_box_and_mibf_exact(n, r):
+    x = W.grid_x_2d(n)
+    xi = W.omega_2d(n)
+    g = W.complex_normal((n * n, 2), W.rng(501))
+    ud = O.direct_2d(O.PHASE_SEPARABLE, x, xi, g)
+    ub = O.ibf_apply_2d_box(O.PHASE_SEPARABLE, n, r, x, -n / 2, -n / 2, g)
+    assert O.rel_l2(ub, ud) < 1e-12
+    center = 8 if n == 16 else 16
+    um = O.mibf_apply_2d(O.PHASE_SEPARABLE, n, r, x, g, center_side=center // 2 if n == 16 else center)
+    assert O.rel_l2(um, ud) < 1e-12
+
+
+def test_nufft_2d_single_box_converges():
+    n = 32
+    x = W.grid_x_2d(n)
+    g = W.complex_normal(n * n, W.rng(502))
+    ud = O.direct_2d(O.PHASE_NUFFT, x, W.omega_2d(n), g)
+    errs = [O.rel_l2(O.ibf_apply_2d_box(O.PHASE_NUFFT, n, r, x, -n / 2, -n / 2, g), ud) for r in (4, 5, 6, 7)]
+    assert all(a > 2 * b for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < 1e-3
+
+
+def test_mibf_matches_table4():
+    for n, r, eps in read_golden("table4_fio_2d.txt"):
+        n, r = int(n), int(r)
+        if n > 32:
+            continue
+        x = W.grid_x_2d(n)
+        g = W.complex_normal(n * n, W.rng(503))
+        ud = O.direct_2d(O.PHASE_FIO2D_32, x, W.omega_2d(n), g)
+        err = O.rel_l2(O.mibf_apply_2d(O.PHASE_FIO2D_32, n, r, x, g), ud)
+        assert eps / 3 < err < eps * 3, (n, r, err, eps)
+
+
+def test_mibf_workload_phase_converges():
+    n = 32
+    x = W.grid_x_2d(n)
+    g = W.complex_normal(n * n, W.rng(504))
+    ud = O.direct_2d(O.PHASE_FIO2D, x, W.omega_2d(n), g)
+    errs = [O.rel_l2(O.mibf_apply_2d(O.PHASE_FIO2D, n, r, x, g), ud) for r in (5, 7, 9)]
+    assert errs[0] > 5 * errs[1] > 25 * errs[2], errs
+    assert errs[1] < 1e-3
