@@ -204,6 +204,33 @@ def run_batch(ibf, torch, reps=5, count=256, seed=4):
     return res
 
 
+# ------------------------------------------------------------ 2D workload
+def run_2d(ibf, torch, n=512, r=7, nrhs=32, reps=5):
+    """2D FIO (Sec. 6.3 form, constants /16) on the n x n grid, multiscale IBF
+    with a 16 x 16 centre, r = 7 per dimension, nrhs complex64 vectors."""
+    N = n * n
+    plan = ibf.Plan(ibf.PHASE_FIO2D, N, r, ibf.C64_FP32, d=2, max_nrhs=nrhs)
+    g = torch.from_numpy(W.complex_normal((nrhs, N), W.rng(workload=3), dtype=np.complex64)).cuda()
+    u = torch.empty_like(g)
+    cs = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):
+        plan.apply_raw(g.data_ptr(), u.data_ptr(), nrhs, cs)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        plan.apply_raw(g.data_ptr(), u.data_ptr(), nrhs, cs)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    res = {"workload": "2D FIO n=%d (N=%d) r=%d nrhs=%d complex64, MIBF with 16x16 centre" % (n, N, r, nrhs),
+           "ms_per_apply": ms, "vectors_per_s": nrhs / (ms / 1e3), "launches": plan.query(ibf.Q_LAUNCHES),
+           "factor_bytes": plan.query(ibf.Q_FACTOR_BYTES)}
+    plan.close()
+    return res
+
+
 # ------------------------------------------------------------------ GPU arm
 def structured_flops(kind_levels, r, N, nc, pro, epi, kind_g):
     """Algorithmic FP32 flops of one fused launch of the even/odd structured
@@ -393,6 +420,10 @@ def run_gpu(a):
     if rank == 0 and not a.skip_batch:
         batch = run_batch(ibf, torch)
 
+    fio2d = None
+    if rank == 0 and not a.skip_2d:
+        fio2d = run_2d(ibf, torch)
+
     # ---- CPU oracle on the host cores (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not a.skip_cpu:
@@ -411,7 +442,7 @@ def run_gpu(a):
                            "l2": "inputs and workspace larger than L2 (no flush)",
                            "parallelism": "independent rhs batches per GPU (dp%d)" % world},
                 "clocks": clk, "e2e": e2e, "gpu_launches": a.steps * launches, "roofline": roof,
-                "fp64_plain": fp64, "batch256": batch, "cpu_baseline": cpu}
+                "fp64_plain": fp64, "batch256": batch, "fio2d": fio2d, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:
@@ -431,6 +462,7 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--skip-2d", action="store_true")
     a = ap.parse_args()
     if a.warmup < 3 and a.impl == "ibf":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -57,8 +57,14 @@ enum ibf_phase {
     IBF_PHASE_NUFFT = 0,        /* Phi = x . xi  (Sec. 6.1, eq. 1D-FT with K = e(+x xi))  */
     IBF_PHASE_FIO1D = 1,        /* Phi = x xi + c(x)|xi|, c = (2 + sin 2 pi x)/8
                                    (Sec. 6.2, eq. 1D-FIO-kernal)                       */
-    IBF_PHASE_FIO2D = 2,        /* Phi = x.xi + sqrt(c1^2 xi1^2 + c2^2 xi2^2), Sec. 6.3
-                                   (reserved: 2D plans return IBF_ERR_UNSUPPORTED)     */
+    IBF_PHASE_FIO2D = 2,        /* Phi = x.xi + sqrt(c1^2 xi1^2 + c2^2 xi2^2) with
+                                   c1 = (2 + sin 2 pi x1 sin 2 pi x2)/16,
+                                   c2 = (2 + cos 2 pi x1 cos 2 pi x2)/16 (Sec. 6.3's
+                                   form; the paper prints /32).  d = 2 only.
+                                   IBF_PHASE_NUFFT and IBF_PHASE_SEPARABLE also
+                                   have 2D forms: x.xi and 0.75 sin(2 pi x1)
+                                   cos(2 pi x2) + 0.125|xi| + 0.3 sin(0.1 xi1 -
+                                   0.07 xi2).                                         */
     IBF_PHASE_SEPARABLE = 100   /* test phase f(x) + h(xi), f = 0.75 sin 2 pi x,
                                    h = 0.125|xi| + 0.3 sin(0.1 xi); the remainder
                                    R^{AB} of eq. RAB vanishes, so the IBF is exact    */
@@ -100,9 +106,18 @@ typedef struct ibf_options {
  * ibf_plan_create -- build the preliminary IBF (Sec. 3) for the uniform grid
  * X = {j/N} (eq. X) and Omega = {k - N/2} (eq. Omega).
  *   phase_id : enum ibf_phase.
- *   d        : dimension; only d = 1 is implemented (d = 2 returns
- *              IBF_ERR_UNSUPPORTED).
- *   N        : number of points, a power of two, 4 <= N <= 2^24.
+ *   d        : dimension, 1 or 2.  d = 2 builds the multiscale IBF of
+ *              Sec. 5.2 on the n x n grids X = {(n1, n2)/n} and
+ *              Omega = {(k1 - n/2, k2 - n/2)}, N = n^2: the frequency square is
+ *              split into corona rings -- ring t is the 12 outer boxes (side
+ *              n/2^(t+2)) of the 4 x 4 partition of [-n/2^(t+1), n/2^(t+1))^2
+ *              -- down to a 16 x 16 centre that is summed directly; every box
+ *              gets a 2D butterfly of depth log2(side) switching at
+ *              ceil(depth/2) (Sec. 5.1).  2D plans: structured form, r in
+ *              {5, 7, 9}, the grid X only (x = NULL), forward apply only.
+ *              Vectors are n x n row-major in (n1, n2) and (k1, k2).
+ *   N        : number of points, a power of two, 4 <= N <= 2^24 (d = 1), or
+ *              n^2 with n a power of two, 32 <= n <= 2048 (d = 2).
  *   r        : Chebyshev points per box (the paper's r_eps), 3 <= r <= 16;
  *              the structured form supports r in {5, 7, 9, 11}.
  *   dtype    : enum ibf_dtype.
@@ -250,7 +265,7 @@ int ibf_plan_query(const ibf_plan* plan, int what, int64_t* value);
  */
 enum ibf_kernel_kind {
     IBF_K_EXPLICIT_INIT = 0, IBF_K_EXPLICIT_LEVEL = 1, IBF_K_EXPLICIT_SWITCH = 2, IBF_K_EXPLICIT_TERM = 3,
-    IBF_K_FUSED_H = 4, IBF_K_FUSED_G = 5
+    IBF_K_FUSED_H = 4, IBF_K_FUSED_G = 5, IBF_K_2D = 6
 };
 int ibf_plan_profile_begin(ibf_plan* plan, int cap);
 int ibf_plan_profile_end(ibf_plan* plan, float* ms, int* kind, int cap_out, int* count);

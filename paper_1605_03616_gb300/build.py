@@ -28,6 +28,8 @@ UNITS = {
     "ibf_fused_f64.cu": [],
     "ibf_static.cu": [],
     "ibf_batch.cu": [],
+    "ibf_2d_build.cu": ["-fmad=false"],
+    "ibf_2d_apply.cu": [],
 }
 
 

@@ -58,8 +58,8 @@ struct ibf_plan {
     void* sU = nullptr;
     std::vector<void*> stab;   // index 1..L
 
-    // BF16x3 tensor-core form: split transfer matrices (device)
-    void* tc_T = nullptr;
+    // 2D multiscale plan (struct Plan2D, ibf_2d.h), d = 2 only
+    void* p2d = nullptr;
 
     void* ws[2] = {nullptr, nullptr};   // apply workspace (ping-pong Lambda buffers)
     size_t factor_bytes = 0, ws_bytes = 0;

@@ -13,6 +13,7 @@
 #include <cstring>
 #include <numeric>
 
+#include "ibf_2d.h"
 #include "ibf_internal.h"
 
 namespace ibf {
@@ -376,6 +377,7 @@ void prof_mark(ibf_plan* p, cudaStream_t s, int kind)
 static void free_plan(ibf_plan* p)
 {
     if (!p) return;
+    delete (Plan2D*)p->p2d;
     for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
     for (void* a : p->allocations) cudaFree(a);
     delete p;
@@ -396,12 +398,67 @@ extern "C" int ibf_plan_create(int phase_id, int d, int64_t N, int r, int dtype,
     return ibf_plan_create_ex(phase_id, d, N, r, dtype, nullptr, nullptr, out);
 }
 
+// 2D multiscale plan (Sec. 5.2); see include/ibf.h
+static int create_2d(int phase_id, int64_t N, int r, int dtype, const double* x, const ibf_options* opt,
+                     ibf_plan** out)
+{
+    if (phase_id != IBF_PHASE_FIO2D && phase_id != IBF_PHASE_NUFFT && phase_id != IBF_PHASE_SEPARABLE)
+        return set_error(IBF_ERR_INVALID, "unknown 2D phase id " + std::to_string(phase_id));
+    int n = 1;
+    while ((int64_t)n * n < N && n < (1 << 12)) n *= 2;
+    if ((int64_t)n * n != N || n < 32 || n > 2048)
+        return set_error(IBF_ERR_INVALID, "2D: N must be n^2 with n a power of two in [32, 2048]");
+    if (r != 5 && r != 7 && r != 9) return set_error(IBF_ERR_UNSUPPORTED, "2D: r must be 5, 7 or 9");
+    if (dtype != IBF_C128 && dtype != IBF_C64_FP32) return set_error(IBF_ERR_UNSUPPORTED, "2D: dtype");
+    if (x) return set_error(IBF_ERR_UNSUPPORTED, "2D: only the uniform grid X is supported");
+    ibf_options o;
+    memset(&o, 0, sizeof(o));
+    if (opt) o = *opt;
+    if (o.form == IBF_FORM_EXPLICIT) return set_error(IBF_ERR_UNSUPPORTED, "2D: structured form only");
+    ibf_plan* p = new ibf_plan();
+    p->phase_id = phase_id;
+    p->d = 2;
+    p->r = r;
+    p->dtype = dtype;
+    p->form = IBF_FORM_STRUCTURED;
+    p->N = N;
+    p->nx = N;
+    p->L = 0;
+    while ((1 << p->L) < n) ++p->L;
+    p->h = (p->L + 1) / 2;
+    p->max_nrhs = o.max_nrhs > 0 ? o.max_nrhs : 32;
+    host_grid(p);
+    Plan2D* P = new Plan2D();
+    P->n = n;
+    P->center = 16;
+    p->p2d = P;
+    int rc = build_2d(p);
+    if (rc) {
+        free_plan(p);
+        return rc;
+    }
+    const size_t esz = dtype == IBF_C128 ? sizeof(double2) : sizeof(float2);
+    for (int b = 0; b < 2; ++b)
+        if ((rc = dalloc(p, &P->ws[b], esz * P->ws_elems, false))) {
+            free_plan(p);
+            return rc;
+        }
+    p->ws_bytes = 2 * esz * P->ws_elems;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        free_plan(p);
+        return cuda_error(e, "2D plan construction");
+    }
+    *out = p;
+    return IBF_OK;
+}
+
 extern "C" int ibf_plan_create_ex(int phase_id, int d, int64_t N, int r, int dtype, const double* x,
                                   const ibf_options* opt, ibf_plan** out)
 {
     if (!out) return set_error(IBF_ERR_INVALID, "out is NULL");
     *out = nullptr;
-    if (d == 2) return set_error(IBF_ERR_UNSUPPORTED, "2D plans are not implemented");
+    if (d == 2) return create_2d(phase_id, N, r, dtype, x, opt, out);
     if (d != 1) return set_error(IBF_ERR_INVALID, "d must be 1 or 2");
     if (phase_id != IBF_PHASE_NUFFT && phase_id != IBF_PHASE_FIO1D && phase_id != IBF_PHASE_SEPARABLE)
         return set_error(IBF_ERR_INVALID, "unknown 1D phase id " + std::to_string(phase_id));
@@ -536,6 +593,7 @@ extern "C" int ibf_apply(ibf_plan* p, const void* g, void* u, int nrhs, ibf_stre
 {
     int rc = check_apply(p, g, u, nrhs);
     if (rc) return rc;
+    if (p->d == 2) return apply_2d(p, g, u, nrhs, (cudaStream_t)stream);
     if (p->form == IBF_FORM_EXPLICIT) return explicit_apply(p, g, u, nrhs, (cudaStream_t)stream);
     return fused_apply(p, g, u, nrhs, false, (cudaStream_t)stream);
 }
@@ -544,6 +602,7 @@ extern "C" int ibf_apply_adjoint(ibf_plan* p, const void* y, void* g, int nrhs, 
 {
     int rc = check_apply(p, y, g, nrhs);
     if (rc) return rc;
+    if (p->d == 2) return set_error(IBF_ERR_UNSUPPORTED, "2D plans have no adjoint apply");
     if (p->form == IBF_FORM_EXPLICIT) return explicit_adjoint(p, y, g, nrhs, (cudaStream_t)stream);
     return fused_apply(p, y, g, nrhs, true, (cudaStream_t)stream);
 }
@@ -609,7 +668,9 @@ extern "C" int ibf_plan_query(const ibf_plan* p, int what, int64_t* v)
     case IBF_Q_WORKSPACE_BYTES: *v = (int64_t)p->ws_bytes; break;
     case IBF_Q_MAX_NRHS: *v = p->max_nrhs; break;
     case IBF_Q_NNZ: *v = p->nnz; break;
-    case IBF_Q_LAUNCHES: *v = p->form == IBF_FORM_EXPLICIT ? explicit_launches(p) : fused_launches(p); break;
+    case IBF_Q_LAUNCHES:
+        *v = p->d == 2 ? launches_2d(p) : (p->form == IBF_FORM_EXPLICIT ? explicit_launches(p) : fused_launches(p));
+        break;
     case IBF_Q_LEVELS_PER_LAUNCH: *v = p->kfuse; break;
     case IBF_Q_RHS_TILE: *v = p->rtile; break;
     default: return set_error(IBF_ERR_INVALID, "unknown query");

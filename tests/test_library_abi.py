@@ -54,7 +54,10 @@ def test_argument_validation_without_gpu(lib):
     assert _create(lib, phase=7)[0] == 1
     assert _create(lib, d=3)[0] == 1
     assert _create(lib, dtype=9)[0] == 1
-    assert _create(lib, d=2)[0] == 4              # 2D not implemented: unsupported
+    assert _create(lib, d=2)[0] == 1              # 1D phase id in 2D
+    assert _create(lib, d=2, phase=2, r=11)[0] == 4   # 2D supports r in {5, 7, 9}
+    assert _create(lib, d=2, phase=2, N=1000)[0] == 1
+    assert _create(lib, d=2, phase=2, N=256)[0] == 1  # n = 16 < 32
     assert _create(lib, r=6)[0] == 4              # structured form: r in {5,7,9,11}
     assert "r" in ibf.last_error()
     assert lib.ibf_plan_create(1, 1, 1024, 9, 1, None) == 1
