@@ -103,6 +103,18 @@ struct FusedParams {
     FusedDesc d;
 };
 
+// Elements of the shared-memory region after the Lambda tile: the staged
+// phase tables of the k levels (padded per-unit stride 4r+1), reused by the
+// epilogues for the switch blocks (padded stride r^2+1) and U^L rows, and by
+// the prologue for the V^0 rows.
+__host__ __device__ __forceinline__ size_t fused_region_elems(int k, int RP)
+{
+    const size_t G = (size_t)1 << k;
+    const size_t tables = (size_t)k * (G / 2) * (4 * RP + 1);
+    const size_t mblocks = G * ((size_t)RP * RP + 1);
+    return tables > mblocks ? tables : mblocks;
+}
+
 __device__ __forceinline__ int brevk(int v, int nbits)
 {
     return nbits ? (int)(__brev((unsigned)v) >> (32 - nbits)) : 0;
@@ -168,13 +180,17 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
     if (P.pro == PRO_V) {
         // forward, l0 = 0: Lambda^0_{0,j} = V^0-expansion of g(xi_j), j = jb 2^k + pos
         const cx* g = (const cx*)P.vin;
-        const cx* V = (const cx*)P.Vs;
+        // the CTA's V^0 rows are contiguous: stage them after the Lambda tile
+        cx* vs = sm + (size_t)G * PS;
+        const cx* Vg = (const cx*)P.Vs + (jb << k) * RP;
+        for (int e = threadIdx.x; e < G * RP; e += blockDim.x) vs[e] = Vg[e];
+        __syncthreads();
         for (int e = threadIdx.x; e < G * rt; e += blockDim.x) {
             const int pos = e & (G - 1), c = e >> k;
             const int64_t kx = (jb << k) + pos;
             cx gv = c < ncol ? g[kx + N * (col0 + c)] : cz<cx>();
 #pragma unroll
-            for (int t = 0; t < RP; ++t) sm[pos * PS + t * rt + c] = cmul(V[kx * RP + t], gv);
+            for (int t = 0; t < RP; ++t) sm[pos * PS + t * rt + c] = cmul(vs[pos * RP + t], gv);
         }
     } else if (P.pro == PRO_UADJ) {
         // adjoint, top level L: Lambda^L_i[t] = sum_{n in leaf i} conj(U[n][t]) y[perm n]
@@ -200,14 +216,25 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
         }
     } else {
         const cx* in = (const cx*)P.in;
-        for (int e = threadIdx.x; e < G * RP * rt; e += blockDim.x) {
-            const int c = e % rt, t = (e / rt) % RP, pos = e / (rt * RP);
-            int64_t pair;
-            if (!ADJ)
-                pair = (i0 << (L - l0)) + (jb << k) + pos;
-            else
-                pair = (((i0 << k) + brevk(pos, k)) << nbj) + jb;
-            sm[pos * PS + t * rt + c] = c < ncol ? in[(pair * RP + t) * P.nc + col0 + c] : cz<cx>();
+        if (RT == 32) {
+            // one warp per (position, t) row of 32 columns
+            const int lane = threadIdx.x & 31;
+            for (int row = threadIdx.x >> 5; row < G * RP; row += blockDim.x >> 5) {
+                const int pos = row / RP, t = row - pos * RP;
+                const int64_t pair = !ADJ ? (i0 << (L - l0)) + (jb << k) + pos
+                                          : (((i0 << k) + brevk(pos, k)) << nbj) + jb;
+                sm[pos * PS + t * 32 + lane] = lane < ncol ? in[(pair * RP + t) * P.nc + col0 + lane] : cz<cx>();
+            }
+        } else {
+            for (int e = threadIdx.x; e < G * RP * rt; e += blockDim.x) {
+                const int c = e % rt, t = (e / rt) % RP, pos = e / (rt * RP);
+                int64_t pair;
+                if (!ADJ)
+                    pair = (i0 << (L - l0)) + (jb << k) + pos;
+                else
+                    pair = (((i0 << k) + brevk(pos, k)) << nbj) + jb;
+                sm[pos * PS + t * rt + c] = c < ncol ? in[(pair * RP + t) * P.nc + col0 + c] : cz<cx>();
+            }
         }
     }
     __syncthreads();
@@ -389,20 +416,39 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
     // ---------------------------------------------------------------- store
     if (P.epi == EPI_LAMBDA) {
         cx* out = (cx*)P.out;
-        for (int e = threadIdx.x; e < G * RP * rt; e += blockDim.x) {
-            const int c = e % rt, t = (e / rt) % RP, pos = e / (rt * RP);
-            if (c >= ncol) continue;
-            int64_t pair;
-            if (!ADJ)
-                pair = (((i0 << k) + brevk(pos, k)) << nbj) + jb;
-            else
-                pair = (i0 << (L - l0)) + (jb << k) + pos;
-            out[(pair * RP + t) * P.nc + col0 + c] = sm[pos * PS + t * rt + c];
+        if (RT == 32) {
+            const int lane = threadIdx.x & 31;
+            for (int row = threadIdx.x >> 5; row < G * RP; row += blockDim.x >> 5) {
+                const int pos = row / RP, t = row - pos * RP;
+                const int64_t pair = !ADJ ? (((i0 << k) + brevk(pos, k)) << nbj) + jb
+                                          : (i0 << (L - l0)) + (jb << k) + pos;
+                if (lane < ncol) out[(pair * RP + t) * P.nc + col0 + lane] = sm[pos * PS + t * 32 + lane];
+            }
+        } else {
+            for (int e = threadIdx.x; e < G * RP * rt; e += blockDim.x) {
+                const int c = e % rt, t = (e / rt) % RP, pos = e / (rt * RP);
+                if (c >= ncol) continue;
+                int64_t pair;
+                if (!ADJ)
+                    pair = (((i0 << k) + brevk(pos, k)) << nbj) + jb;
+                else
+                    pair = (i0 << (L - l0)) + (jb << k) + pos;
+                out[(pair * RP + t) * P.nc + col0 + c] = sm[pos * PS + t * rt + c];
+            }
         }
     } else if (P.epi == EPI_SWITCH) {
-        // forward: Lambda~ = M~' Lambda at level h; adjoint: Lambda = M~'^* Lambda~
+        // forward: Lambda~ = M~' Lambda at level h; adjoint: Lambda = M~'^* Lambda~.
+        // The CTA's G blocks of r x r are staged in the table region first.
         cx* out = (cx*)P.out;
-        const cx* M = (const cx*)P.Ms;
+        constexpr int MS = RP * RP + 1;   // padded block stride
+        cx* msm = sm + (size_t)G * PS;
+        for (int e = threadIdx.x; e < G * RP * RP; e += blockDim.x) {
+            const int pos = e / (RP * RP), rem = e - pos * (RP * RP);
+            const int64_t pair = !ADJ ? (((i0 << k) + brevk(pos, k)) << nbj) + jb
+                                      : (i0 << (L - l0)) + (jb << k) + pos;
+            msm[pos * MS + rem] = ((const cx*)P.Ms)[pair * RP * RP + rem];
+        }
+        __syncthreads();
         for (int e = threadIdx.x; e < G * rt; e += blockDim.x) {
             const int c = e % rt, pos = e / rt;
             if (c >= ncol) continue;
@@ -414,16 +460,16 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
             cx x[RP];
 #pragma unroll
             for (int t = 0; t < RP; ++t) x[t] = sm[pos * PS + t * rt + c];
-            const cx* Mp = M + pair * RP * RP;
+            const cx* Mp = msm + pos * MS;
 #pragma unroll
             for (int t = 0; t < RP; ++t) {
                 cx acc = cz<cx>();
                 if (!ADJ) {
 #pragma unroll
-                    for (int s2 = 0; s2 < RP; ++s2) cacc(acc, cmul(__ldg(Mp + t * RP + s2), x[s2]));
+                    for (int s2 = 0; s2 < RP; ++s2) cacc(acc, cmul(Mp[t * RP + s2], x[s2]));
                 } else {
 #pragma unroll
-                    for (int s2 = 0; s2 < RP; ++s2) cacc(acc, cmulc(__ldg(Mp + s2 * RP + t), x[s2]));
+                    for (int s2 = 0; s2 < RP; ++s2) cacc(acc, cmulc(Mp[s2 * RP + t], x[s2]));
                 }
                 out[(pair * RP + t) * P.nc + col0 + c] = acc;
             }
@@ -431,7 +477,17 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
     } else if (P.epi == EPI_U) {
         // forward, level L: u(x_n) = sum_t U[n][t] Lambda^L_{leaf(n)}[t]
         cx* u = (cx*)P.vout;
-        const cx* U = (const cx*)P.Us;
+        // the CTA's leaves are contiguous, so are their points [nb0, nb1);
+        // their U rows are staged in the table region when they fit
+        const int32_t nb0 = P.off[i0 << k], nb1 = P.off[(i0 + 1) << k];
+        const bool staged = (int64_t)(nb1 - nb0) * RP <= (int64_t)fused_region_elems(k, RP);
+        const cx* U = staged ? sm + (size_t)G * PS - (int64_t)nb0 * RP : (const cx*)P.Us;
+        if (staged) {
+            cx* us = sm + (size_t)G * PS;
+            const cx* Ug = (const cx*)P.Us + (int64_t)nb0 * RP;
+            for (int e = threadIdx.x; e < (nb1 - nb0) * RP; e += blockDim.x) us[e] = Ug[e];
+            __syncthreads();
+        }
         for (int e = threadIdx.x; e < G * rt; e += blockDim.x) {
             const int il = e & (G - 1), c = e >> k;
             if (c >= ncol) continue;
@@ -555,7 +611,7 @@ inline void fill_even_odd(const ibf_plan* p, FusedConsts<Real, RP>& C)
 inline size_t fused_smem_bytes(int k, int rt, int RP, size_t esz)
 {
     const size_t G = (size_t)1 << k;
-    return (G * ((size_t)RP * rt + 1) + (size_t)k * (G / 2) * (4 * RP + 1)) * esz;
+    return (G * ((size_t)RP * rt + 1) + fused_region_elems(k, RP)) * esz;
 }
 
 // largest fusion depth whose CTA fits the shared-memory budget that keeps
