@@ -104,6 +104,23 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------- multi-GPU helpers
+def max_over_ranks(value_ms: float, world: int, dist=None, device=None) -> float:
+    """Largest per-rank time: the whole job is as slow as its slowest rank."""
+    if world <= 1 or dist is None:
+        return value_ms
+    import torch
+    t = torch.tensor([float(value_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(vectors_per_rank: int, steps: int, world: int, max_ms: float) -> float:
+    """Weak scaling: every rank applies its own batch of vectors per step, so
+    the job processes world * vectors_per_rank * steps vectors in max_ms."""
+    return world * vectors_per_rank * steps / (max_ms / 1e3)
+
+
 # ------------------------------------------------------------ CPU oracle arm
 def oracle_vectors_per_s(a, threads: int):
     """Time the FP64 oracle (matrix-free butterfly) on one vector of the
@@ -274,6 +291,10 @@ def run_gpu(a):
     g_host = W.complex_normal((nrhs, N), W.rng(workload=2 + 1000 * rank), dtype=np.complex64)  # row = column
     g = torch.from_numpy(g_host).to(dev)            # column-major N x nrhs
     u = torch.empty_like(g)
+    tuned = None
+    if not a.no_autotune:
+        k_, rt_, ms_ = plan.autotune(nrhs)
+        tuned = {"levels_per_launch": k_, "rhs_tile": rt_, "ms": ms_}
     launches = plan.query(ibf.Q_LAUNCHES)
 
     def step():
@@ -299,16 +320,14 @@ def run_gpu(a):
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     prof = plan.profile_end()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * nrhs * a.steps / (ms / 1e3)
+    ms = max_over_ranks(ms, world, dist if world > 1 else None, dev)
+    value = job_throughput(nrhs, a.steps, world, ms)
 
     # ---- dominant kernel and its roofline (per-launch CUDA events, timed region)
     sched = []
     L, h = plan.L, plan.h
     kfuse = plan.query(ibf.Q_LEVELS_PER_LAUNCH)
+    rtile = plan.query(ibf.Q_RHS_TILE)
 
     def split(lo, hi, kind):
         n = hi - lo
@@ -345,7 +364,8 @@ def run_gpu(a):
     ach_gb = bytes_alg / (avg_ms / 1e3) / 1e9
     frac_alu = ach_tf / fp32_peak
     frac_hbm = ach_gb / float(pk["hbm_gbs"])
-    kname = "k_fused<float,%d,fwd,%s> levels %d..%d" % (r, "H" if kd == ibf.K_FUSED_H else "G", lo + 1, hi)
+    kname = "k_fused<float,%d,fwd,%s,tile %d> levels %d..%d" % (r, "H" if kd == ibf.K_FUSED_H else "G", rtile,
+                                                                 lo + 1, hi)
     if frac_alu >= frac_hbm:
         roof = {"bound": "alu", "achieved": ach_tf, "peak": fp32_peak, "unit": "TFLOP/s", "frac": frac_alu,
                 "traffic": None}
@@ -377,12 +397,8 @@ def run_gpu(a):
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e = {"value": world * nrhs * a.steps / (e2e_ms / 1e3), "unit": "vectors/s",
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dist if world > 1 else None, dev)
+    e2e = {"value": job_throughput(nrhs, a.steps, world, e2e_ms), "unit": "vectors/s",
            "h2d_bytes_per_step": int(g.numel() * 8), "d2h_bytes_per_step": int(u.numel() * 8)}
 
     # ---- plain FP64 explicit single-vector form on the same GPU, and accuracy
@@ -439,6 +455,7 @@ def run_gpu(a):
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": workload_name(a), "N": N, "r": r, "nrhs_per_gpu": nrhs, "phase": "FIO1D",
                            "form": "structured, %d fused launches/apply" % launches,
+                           "autotuned_shape": tuned,
                            "l2": "inputs and workspace larger than L2 (no flush)",
                            "parallelism": "independent rhs batches per GPU (dp%d)" % world},
                 "clocks": clk, "e2e": e2e, "gpu_launches": a.steps * launches, "roofline": roof,
@@ -463,6 +480,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-2d", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     a = ap.parse_args()
     if a.warmup < 3 and a.impl == "ibf":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -650,6 +650,9 @@ static int launch_one(const FusedParams<Real, RP>& P, int64_t ngroups, cudaStrea
     if (P.d.rt == 32) {
         set_smem_attr<Real, RP, ADJ, KIND, 32>();
         k_fused<Real, RP, ADJ, KIND, 32><<<(unsigned)blocks, threads, smem, st>>>(P);
+    } else if (P.d.rt == 16 && sizeof(Real) == 4) {
+        set_smem_attr<Real, RP, ADJ, KIND, 16>();
+        k_fused<Real, RP, ADJ, KIND, 16><<<(unsigned)blocks, threads, smem, st>>>(P);
     } else {
         set_smem_attr<Real, RP, ADJ, KIND, 0>();
         k_fused<Real, RP, ADJ, KIND, 0><<<(unsigned)blocks, threads, smem, st>>>(P);
