@@ -217,13 +217,31 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
     } else {
         const cx* in = (const cx*)P.in;
         if (RT == 32) {
-            // one warp per (position, t) row of 32 columns
-            const int lane = threadIdx.x & 31;
-            for (int row = threadIdx.x >> 5; row < G * RP; row += blockDim.x >> 5) {
-                const int pos = row / RP, t = row - pos * RP;
-                const int64_t pair = !ADJ ? (i0 << (L - l0)) + (jb << k) + pos
-                                          : (((i0 << k) + brevk(pos, k)) << nbj) + jb;
-                sm[pos * PS + t * 32 + lane] = lane < ncol ? in[(pair * RP + t) * P.nc + col0 + lane] : cz<cx>();
+            // one warp per (position, t) row of 32 columns; each warp issues
+            // the loads of 8 rows before it stores any, so their latencies overlap
+            const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+            constexpr int BR = 8;
+            for (int row0 = threadIdx.x >> 5; row0 < G * RP; row0 += BR * nw) {
+                cx v[BR];
+#pragma unroll
+                for (int b = 0; b < BR; ++b) {
+                    const int row = row0 + b * nw;
+                    v[b] = cz<cx>();
+                    if (row < G * RP && lane < ncol) {
+                        const int pos = row / RP, t = row - pos * RP;
+                        const int64_t pair = !ADJ ? (i0 << (L - l0)) + (jb << k) + pos
+                                                  : (((i0 << k) + brevk(pos, k)) << nbj) + jb;
+                        v[b] = in[(pair * RP + t) * P.nc + col0 + lane];
+                    }
+                }
+#pragma unroll
+                for (int b = 0; b < BR; ++b) {
+                    const int row = row0 + b * nw;
+                    if (row < G * RP) {
+                        const int pos = row / RP, t = row - pos * RP;
+                        sm[pos * PS + t * 32 + lane] = v[b];
+                    }
+                }
             }
         } else {
             for (int e = threadIdx.x; e < G * RP * rt; e += blockDim.x) {
@@ -247,21 +265,35 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
     {
         const int nunit = G >> 1;
         const int per_level = nunit * 4 * RP;
-        for (int st1 = 0; st1 < k; ++st1) {      // level s = st1 + 1 of the launch
-            const int s = st1 + 1, bit = st1;
-            const int64_t ldC = 1LL << (L - l0 - s + 1);
-            const cx* Dg = (const cx*)P.D[st1];
-            for (int e = threadIdx.x; e < per_level; e += blockDim.x) {
-                const int u = e / (4 * RP);
-                const int rem = e - u * (4 * RP);
-                const int ac = rem / RP;                 // a * 2 + c
-                const int t = rem - ac * RP;
-                const int p0 = ((u >> bit) << (bit + 1)) | (u & ((1 << bit) - 1));
-                const int low = p0 & ((1 << bit) - 1);
-                const int64_t ia = (i0 << s) + ((int64_t)brevk(low, bit) << 1) + (ac >> 1);
-                const int64_t C = (((jb << (k - s)) + (p0 >> s)) << 1) + (ac & 1);
-                dsm[((size_t)st1 * nunit + u) * DS + rem] = __ldg(Dg + (ia * ldC + C) * RP + t);
+        const int total = k * per_level;
+        constexpr int BD = 8;   // loads in flight per thread before their stores
+        for (int e0 = threadIdx.x; e0 < total; e0 += BD * blockDim.x) {
+            cx v[BD];
+            int dst[BD];
+#pragma unroll
+            for (int b = 0; b < BD; ++b) {
+                const int e = e0 + b * blockDim.x;
+                dst[b] = -1;
+                if (e < total) {
+                    const int st1 = e / per_level;          // level s = st1 + 1 of the launch
+                    const int rem0 = e - st1 * per_level;
+                    const int s = st1 + 1, bit = st1;
+                    const int u = rem0 / (4 * RP);
+                    const int rem = rem0 - u * (4 * RP);
+                    const int ac = rem / RP;                 // a * 2 + c
+                    const int t = rem - ac * RP;
+                    const int p0 = ((u >> bit) << (bit + 1)) | (u & ((1 << bit) - 1));
+                    const int low = p0 & ((1 << bit) - 1);
+                    const int64_t ia = (i0 << s) + ((int64_t)brevk(low, bit) << 1) + (ac >> 1);
+                    const int64_t C = (((jb << (k - s)) + (p0 >> s)) << 1) + (ac & 1);
+                    const int64_t ldC = 1LL << (L - l0 - s + 1);
+                    v[b] = __ldg((const cx*)P.D[st1] + (ia * ldC + C) * RP + t);
+                    dst[b] = (st1 * nunit + u) * DS + rem;
+                }
             }
+#pragma unroll
+            for (int b = 0; b < BD; ++b)
+                if (dst[b] >= 0) dsm[dst[b]] = v[b];
         }
     }
     __syncthreads();
@@ -442,11 +474,30 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
         cx* out = (cx*)P.out;
         constexpr int MS = RP * RP + 1;   // padded block stride
         cx* msm = sm + (size_t)G * PS;
-        for (int e = threadIdx.x; e < G * RP * RP; e += blockDim.x) {
-            const int pos = e / (RP * RP), rem = e - pos * (RP * RP);
-            const int64_t pair = !ADJ ? (((i0 << k) + brevk(pos, k)) << nbj) + jb
-                                      : (i0 << (L - l0)) + (jb << k) + pos;
-            msm[pos * MS + rem] = ((const cx*)P.Ms)[pair * RP * RP + rem];
+        {
+            constexpr int BM = 8;
+            const int total = G * RP * RP;
+            for (int e0 = threadIdx.x; e0 < total; e0 += BM * blockDim.x) {
+                cx v[BM];
+#pragma unroll
+                for (int b = 0; b < BM; ++b) {
+                    const int e = e0 + b * blockDim.x;
+                    if (e < total) {
+                        const int pos = e / (RP * RP), rem = e - pos * (RP * RP);
+                        const int64_t pair = !ADJ ? (((i0 << k) + brevk(pos, k)) << nbj) + jb
+                                                  : (i0 << (L - l0)) + (jb << k) + pos;
+                        v[b] = ((const cx*)P.Ms)[pair * RP * RP + rem];
+                    }
+                }
+#pragma unroll
+                for (int b = 0; b < BM; ++b) {
+                    const int e = e0 + b * blockDim.x;
+                    if (e < total) {
+                        const int pos = e / (RP * RP), rem = e - pos * (RP * RP);
+                        msm[pos * MS + rem] = v[b];
+                    }
+                }
+            }
         }
         __syncthreads();
         for (int e = threadIdx.x; e < G * rt; e += blockDim.x) {
