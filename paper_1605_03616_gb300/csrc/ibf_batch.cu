@@ -88,9 +88,8 @@ static void batch_kind(const FusedConsts<Real, RP>& C, const ibf_batch::Phase& p
 template <typename Real, int RP>
 static int batch_launch(const ibf_batch* b, cudaStream_t st)
 {
-    FusedConsts<Real, RP> C;
+    FusedConsts<Real, RP> C;   // kernel argument kept for the launch signature
     memset(&C, 0, sizeof(C));
-    fill_even_odd(b->plans[0], C);
     for (const auto& ph : b->phases) {
         if (b->adjoint)
             batch_kind<Real, RP, true>(C, ph, st);
@@ -235,6 +234,11 @@ extern "C" int ibf_batch_create(ibf_plan* const* plans, int count, const int* nr
             cudaMemcpy(P.start, start.data(), sizeof(int64_t) * start.size(), cudaMemcpyHostToDevice);
             B->phases.push_back(P);
         }
+    }
+    rc = p0->dtype == IBF_C128 ? fused_upload_consts<double>(p0) : fused_upload_consts<float>(p0);
+    if (rc) {
+        batch_free(B);
+        return rc;
     }
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {

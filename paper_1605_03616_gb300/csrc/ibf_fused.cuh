@@ -81,6 +81,12 @@ struct FusedConsts {
     Real F[RP][EO<RP>::HQ > 0 ? EO<RP>::HQ : 1];
 };
 
+// The weights depend only on r, so every translation unit that launches the
+// fused kernels keeps one copy per (precision, r) in constant memory, filled
+// once per device by fused_upload_consts (plan or batch creation).
+template <typename Real, int RP>
+__constant__ FusedConsts<Real, RP> c_eo;
+
 // One fused launch of one transform: k levels starting at l0.
 struct FusedDesc {
     const void* D[kMaxFuse];     // phase table of step s at D[s-1]
@@ -577,7 +583,7 @@ __global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>
     k_fused(const __grid_constant__ FusedParams<Real, RP> P)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    fused_body<Real, RP, ADJ, KIND, RT>(P.C, P.d, blockIdx.x, smraw);
+    fused_body<Real, RP, ADJ, KIND, RT>(c_eo<Real, RP>, P.d, blockIdx.x, smraw);
 }
 
 // Batched launch: CTA blocks [start[b], start[b+1]) run descriptor b, so one
@@ -598,7 +604,7 @@ __global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>
         else
             hi = mid - 1;
     }
-    fused_body<Real, RP, ADJ, KIND, RT>(C, descs[lo], b - start[lo], smraw);
+    fused_body<Real, RP, ADJ, KIND, RT>(c_eo<Real, RP>, descs[lo], b - start[lo], smraw);
 }
 
 // ---------------------------------------------------------------------------
@@ -654,6 +660,38 @@ inline void fill_even_odd(const ibf_plan* p, FusedConsts<Real, RP>& C)
             C.F[t][s] = (Real)((T0[s][t] - T0[RP - 1 - s][t]) / 2);
         }
         if (RP & 1) C.E[t][HQ] = (Real)T0[HQ][t];
+    }
+}
+
+// copy the even/odd weights of r = RP into this translation unit's constant
+// memory on the current device (idempotent; synchronous, so call it outside
+// stream capture -- plan and batch creation do).  Static, not inline: each
+// translation unit has its own copy of c_eo and so its own "done" flags.
+template <typename Real, int RP>
+static int fused_upload_consts_t(const ibf_plan* p)
+{
+    static bool done[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && done[dev]) return IBF_OK;
+    FusedConsts<Real, RP> h;
+    memset(&h, 0, sizeof(h));
+    fill_even_odd(p, h);
+    cudaError_t e = cudaMemcpyToSymbol(c_eo<Real, RP>, &h, sizeof(h));
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyToSymbol(even/odd weights)");
+    if (dev >= 0 && dev < 64) done[dev] = true;
+    return IBF_OK;
+}
+
+template <typename Real>
+static int fused_upload_consts(const ibf_plan* p)
+{
+    switch (p->r) {
+    case 5: return fused_upload_consts_t<Real, 5>(p);
+    case 7: return fused_upload_consts_t<Real, 7>(p);
+    case 9: return fused_upload_consts_t<Real, 9>(p);
+    case 11: return fused_upload_consts_t<Real, 11>(p);
+    default: return IBF_OK;
     }
 }
 
@@ -717,7 +755,8 @@ static int fused_run(ibf_plan* p, const void* vin, void* vout, int nrhs, bool ad
     typedef typename CT<Real>::T cx;
     FusedParams<Real, RP> P;
     memset(&P, 0, sizeof(P));
-    fill_even_odd(p, P.C);
+    int urc = fused_upload_consts_t<Real, RP>(p);
+    if (urc) return urc;
     P.d.Vs = p->sV;
     P.d.Us = p->sU;
     P.d.Ms = p->sM;

@@ -8,4 +8,6 @@ int fused_apply_f64(ibf_plan* p, const void* vin, void* vout, int nrhs, bool adj
     return fused_apply_t<double>(p, vin, vout, nrhs, adj, st);
 }
 
+int fused_prepare_f64(const ibf_plan* p) { return fused_upload_consts<double>(p); }
+
 }  // namespace ibf

@@ -56,7 +56,8 @@ static int static_run(const ibf_plan* p, const void* vin, void* vout, int nrhs, 
     typedef typename CT<Real>::T cx;
     FusedParams<Real, RP> P;
     memset(&P, 0, sizeof(P));
-    fill_even_odd(p, P.C);
+    int urc = fused_upload_consts_t<Real, RP>(p);   // first call on a device only
+    if (urc) return urc;
     P.d.Vs = p->sV;
     P.d.Us = p->sU;
     P.d.Ms = p->sM;
