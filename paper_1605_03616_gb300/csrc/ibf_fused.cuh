@@ -71,12 +71,13 @@ struct EO {
 // Constants of the transfer matrices, shared by every launch with this r.
 template <typename Real, int RP>
 struct FusedConsts {
-    // Pm[t][s] = (T0[t][s] + T0[RP-1-t][s]) / 2 (t < HQ); Pm[mid][s] = T0[mid][s]
-    // Qm[t][s] = (T0[t][s] - T0[RP-1-t][s]) / 2 (t < HQ)
+    // Pm[s][t] = (T0[t][s] + T0[RP-1-t][s]) / 2 (t < HQ); Pm[s][mid] = T0[mid][s]
+    // Qm[s][t] = (T0[t][s] - T0[RP-1-t][s]) / 2 (t < HQ)
+    // (stored by input index s, so one step of the H form reads a contiguous run)
     // E[t][s]  = (T0[s][t] + T0[RP-1-s][t]) / 2 (s < HQ); E[t][mid] = T0[mid][t]
     // F[t][s]  = (T0[s][t] - T0[RP-1-s][t]) / 2 (s < HQ)
-    Real Pm[EO<RP>::HR][RP];
-    Real Qm[EO<RP>::HQ > 0 ? EO<RP>::HQ : 1][RP];
+    Real Pm[RP][EO<RP>::HR];
+    Real Qm[RP][EO<RP>::HQ > 0 ? EO<RP>::HQ : 1];
     Real E[RP][EO<RP>::HR];
     Real F[RP][EO<RP>::HQ > 0 ? EO<RP>::HQ : 1];
 };
@@ -223,31 +224,20 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
     } else {
         const cx* in = (const cx*)P.in;
         if (RT == 32) {
-            // one warp per (position, t) row of 32 columns; each warp issues
-            // the loads of 8 rows before it stores any, so their latencies overlap
+            // one warp per position: its r rows of 32 columns are loaded
+            // together (r loads in flight per lane), then stored
             const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-            constexpr int BR = 8;
-            for (int row0 = threadIdx.x >> 5; row0 < G * RP; row0 += BR * nw) {
-                cx v[BR];
+            const bool on = lane < ncol;
+            for (int pos = threadIdx.x >> 5; pos < G; pos += nw) {
+                const int64_t pair = !ADJ ? (i0 << (L - l0)) + (jb << k) + pos
+                                          : (((i0 << k) + brevk(pos, k)) << nbj) + jb;
+                const cx* src = in + pair * RP * P.nc + col0 + lane;
+                cx v[RP];
 #pragma unroll
-                for (int b = 0; b < BR; ++b) {
-                    const int row = row0 + b * nw;
-                    v[b] = cz<cx>();
-                    if (row < G * RP && lane < ncol) {
-                        const int pos = row / RP, t = row - pos * RP;
-                        const int64_t pair = !ADJ ? (i0 << (L - l0)) + (jb << k) + pos
-                                                  : (((i0 << k) + brevk(pos, k)) << nbj) + jb;
-                        v[b] = in[(pair * RP + t) * P.nc + col0 + lane];
-                    }
-                }
+                for (int t = 0; t < RP; ++t) v[t] = on ? src[(int64_t)t * P.nc] : cz<cx>();
+                cx* dst = sm + pos * PS + lane;
 #pragma unroll
-                for (int b = 0; b < BR; ++b) {
-                    const int row = row0 + b * nw;
-                    if (row < G * RP) {
-                        const int pos = row / RP, t = row - pos * RP;
-                        sm[pos * PS + t * 32 + lane] = v[b];
-                    }
-                }
+                for (int t = 0; t < RP; ++t) dst[t * 32] = v[t];
             }
         } else {
             for (int e = threadIdx.x; e < G * RP * rt; e += blockDim.x) {
@@ -351,7 +341,7 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
                             const Real m1x = y10.x - y11.x, m1y = y10.y - y11.y;
 #pragma unroll
                             for (int t = 0; t < HR; ++t) {
-                                const Real pm = C.Pm[t][s2];
+                                const Real pm = C.Pm[s2][t];
                                 we0[t].x += pm * p0x;
                                 we0[t].y += pm * p0y;
                                 we1[t].x += pm * p1x;
@@ -359,7 +349,7 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
                             }
 #pragma unroll
                             for (int t = 0; t < HQ; ++t) {
-                                const Real qm = C.Qm[t][s2];
+                                const Real qm = C.Qm[s2][t];
                                 wo0[t].x += qm * m0x;
                                 wo0[t].y += qm * m0y;
                                 wo1[t].x += qm * m1x;
@@ -455,13 +445,16 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
     if (P.epi == EPI_LAMBDA) {
         cx* out = (cx*)P.out;
         if (RT == 32) {
-            const int lane = threadIdx.x & 31;
-            for (int row = threadIdx.x >> 5; row < G * RP; row += blockDim.x >> 5) {
-                const int pos = row / RP, t = row - pos * RP;
-                const int64_t pair = !ADJ ? (((i0 << k) + brevk(pos, k)) << nbj) + jb
-                                          : (i0 << (L - l0)) + (jb << k) + pos;
-                if (lane < ncol) out[(pair * RP + t) * P.nc + col0 + lane] = sm[pos * PS + t * 32 + lane];
-            }
+            const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+            if (lane < ncol)
+                for (int pos = threadIdx.x >> 5; pos < G; pos += nw) {
+                    const int64_t pair = !ADJ ? (((i0 << k) + brevk(pos, k)) << nbj) + jb
+                                              : (i0 << (L - l0)) + (jb << k) + pos;
+                    cx* dst = out + pair * RP * P.nc + col0 + lane;
+                    const cx* srcs = sm + pos * PS + lane;
+#pragma unroll
+                    for (int t = 0; t < RP; ++t) dst[(int64_t)t * P.nc] = srcs[t * 32];
+                }
         } else {
             for (int e = threadIdx.x; e < G * RP * rt; e += blockDim.x) {
                 const int c = e % rt, t = (e / rt) % RP, pos = e / (rt * RP);
@@ -649,11 +642,11 @@ inline void fill_even_odd(const ibf_plan* p, FusedConsts<Real, RP>& C)
     const auto& T0 = p->T[0];
     for (int t = 0; t < HQ; ++t)
         for (int s = 0; s < RP; ++s) {
-            C.Pm[t][s] = (Real)((T0[t][s] + T0[RP - 1 - t][s]) / 2);
-            C.Qm[t][s] = (Real)((T0[t][s] - T0[RP - 1 - t][s]) / 2);
+            C.Pm[s][t] = (Real)((T0[t][s] + T0[RP - 1 - t][s]) / 2);
+            C.Qm[s][t] = (Real)((T0[t][s] - T0[RP - 1 - t][s]) / 2);
         }
     if (RP & 1)
-        for (int s = 0; s < RP; ++s) C.Pm[HQ][s] = (Real)T0[HQ][s];
+        for (int s = 0; s < RP; ++s) C.Pm[s][HQ] = (Real)T0[HQ][s];
     for (int t = 0; t < RP; ++t) {
         for (int s = 0; s < HQ; ++s) {
             C.E[t][s] = (Real)((T0[s][t] + T0[RP - 1 - s][t]) / 2);
