@@ -259,37 +259,26 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
     constexpr int DS = 4 * RP + 1;   // per-unit stride, padded against bank conflicts
     cx* dsm = sm + (size_t)G * PS;
     {
+        // one thread per (level, unit, a, c) row of r contiguous table entries
         const int nunit = G >> 1;
-        const int per_level = nunit * 4 * RP;
-        const int total = k * per_level;
-        constexpr int BD = 8;   // loads in flight per thread before their stores
-        for (int e0 = threadIdx.x; e0 < total; e0 += BD * blockDim.x) {
-            cx v[BD];
-            int dst[BD];
+        const int rows_per_level = nunit * 4;
+        for (int row = threadIdx.x; row < k * rows_per_level; row += blockDim.x) {
+            const int st1 = row / rows_per_level;          // level s = st1 + 1 of the launch
+            const int rr = row - st1 * rows_per_level;
+            const int u = rr >> 2, ac = rr & 3;             // ac = a * 2 + c
+            const int s = st1 + 1, bit = st1;
+            const int p0 = ((u >> bit) << (bit + 1)) | (u & ((1 << bit) - 1));
+            const int low = p0 & ((1 << bit) - 1);
+            const int64_t ia = (i0 << s) + ((int64_t)brevk(low, bit) << 1) + (ac >> 1);
+            const int64_t C = (((jb << (k - s)) + (p0 >> s)) << 1) + (ac & 1);
+            const int64_t ldC = 1LL << (L - l0 - s + 1);
+            const cx* src = (const cx*)P.D[st1] + (ia * ldC + C) * RP;
+            cx v[RP];
 #pragma unroll
-            for (int b = 0; b < BD; ++b) {
-                const int e = e0 + b * blockDim.x;
-                dst[b] = -1;
-                if (e < total) {
-                    const int st1 = e / per_level;          // level s = st1 + 1 of the launch
-                    const int rem0 = e - st1 * per_level;
-                    const int s = st1 + 1, bit = st1;
-                    const int u = rem0 / (4 * RP);
-                    const int rem = rem0 - u * (4 * RP);
-                    const int ac = rem / RP;                 // a * 2 + c
-                    const int t = rem - ac * RP;
-                    const int p0 = ((u >> bit) << (bit + 1)) | (u & ((1 << bit) - 1));
-                    const int low = p0 & ((1 << bit) - 1);
-                    const int64_t ia = (i0 << s) + ((int64_t)brevk(low, bit) << 1) + (ac >> 1);
-                    const int64_t C = (((jb << (k - s)) + (p0 >> s)) << 1) + (ac & 1);
-                    const int64_t ldC = 1LL << (L - l0 - s + 1);
-                    v[b] = __ldg((const cx*)P.D[st1] + (ia * ldC + C) * RP + t);
-                    dst[b] = (st1 * nunit + u) * DS + rem;
-                }
-            }
+            for (int t = 0; t < RP; ++t) v[t] = __ldg(src + t);
+            cx* dst = dsm + (st1 * nunit + u) * DS + ac * RP;
 #pragma unroll
-            for (int b = 0; b < BD; ++b)
-                if (dst[b] >= 0) dsm[dst[b]] = v[b];
+            for (int t = 0; t < RP; ++t) dst[t] = v[t];
         }
     }
     __syncthreads();
@@ -499,6 +488,34 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
             }
         }
         __syncthreads();
+        if (RT == 32) {
+            // two columns (c, c + 16) per thread: each staged weight feeds both
+            for (int e = threadIdx.x; e < G * 16; e += blockDim.x) {
+                const int c = e & 15, pos = e >> 4;
+                const int64_t pair = !ADJ ? (((i0 << k) + brevk(pos, k)) << nbj) + jb
+                                          : (i0 << (L - l0)) + (jb << k) + pos;
+                cx xa[RP], xb[RP];
+#pragma unroll
+                for (int t = 0; t < RP; ++t) {
+                    xa[t] = sm[pos * PS + t * 32 + c];
+                    xb[t] = sm[pos * PS + t * 32 + c + 16];
+                }
+                const cx* Mp = msm + pos * MS;
+                cx* oa = out + pair * RP * P.nc + col0 + c;
+#pragma unroll
+                for (int t = 0; t < RP; ++t) {
+                    cx aa = cz<cx>(), ab = cz<cx>();
+#pragma unroll
+                    for (int s2 = 0; s2 < RP; ++s2) {
+                        const cx mv = ADJ ? Mp[s2 * RP + t] : Mp[t * RP + s2];
+                        cacc(aa, ADJ ? cmulc(mv, xa[s2]) : cmul(mv, xa[s2]));
+                        cacc(ab, ADJ ? cmulc(mv, xb[s2]) : cmul(mv, xb[s2]));
+                    }
+                    if (c < ncol) oa[(int64_t)t * P.nc] = aa;
+                    if (c + 16 < ncol) oa[(int64_t)t * P.nc + 16] = ab;
+                }
+            }
+        } else
         for (int e = threadIdx.x; e < G * rt; e += blockDim.x) {
             const int c = e % rt, pos = e / rt;
             if (c >= ncol) continue;
