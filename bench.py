@@ -36,6 +36,30 @@ import numpy as np  # noqa: E402
 import workloads as W  # noqa: E402
 
 FP32_LANES_PER_SM = 128
+
+# DRAM bytes (read + write) per launch of the fused kernels, from one
+# single-pass ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of
+# this benchmark at N = 2^20, r = 9, nrhs = 64, 4 levels per launch, tile 32
+# (profiles/k_fused_f32_fio1d_n2e20_nrhs64.md).  Keyed by the launch's level
+# range; valid only while the kernel sources hash to KERNEL_SRC_SHA.
+KERNEL_SRC_SHA = "58f3ab0e6f78eb5e"
+TRAFFIC_N20_R9_NRHS64_K4 = {
+    (0, 4, "H"): 1216650752 + 4772077824,
+    (4, 7, "H"): 5284976640 + 4779201280,
+    (7, 10, "H"): 5964457728 + 4783379200,
+    (10, 14, "G"): 5436062720 + 4780604160,
+    (14, 17, "G"): 5285076992 + 4780598528,
+    (17, 20, "G"): 5368861696 + 527849984,
+}
+
+
+def kernel_src_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("paper_1605_03616_gb300/csrc/ibf_fused.cuh", "paper_1605_03616_gb300/csrc/ibf_fused_f32.cu"):
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 METRIC = "IBF apply vectors/s (rel.err <= 1e-5 vs plain FP64 GPU form)"
 
 
@@ -292,7 +316,12 @@ def run_gpu(a):
     g = torch.from_numpy(g_host).to(dev)            # column-major N x nrhs
     u = torch.empty_like(g)
     tuned = None
-    if not a.no_autotune:
+    if a.levels_per_launch or a.rhs_tile:
+        plan.close()
+        plan = ibf.Plan(ibf.PHASE_FIO1D, N, r, ibf.C64_FP32, max_nrhs=nrhs, levels_per_launch=a.levels_per_launch,
+                        rhs_tile=a.rhs_tile)
+        tuned = {"levels_per_launch": a.levels_per_launch, "rhs_tile": a.rhs_tile, "ms": None, "forced": True}
+    elif not a.no_autotune:
         k_, rt_, ms_ = plan.autotune(nrhs)
         tuned = {"levels_per_launch": k_, "rhs_tile": rt_, "ms": ms_}
     launches = plan.query(ibf.Q_LAUNCHES)
@@ -372,6 +401,10 @@ def run_gpu(a):
     else:
         roof = {"bound": "hbm", "achieved": ach_gb, "peak": float(pk["hbm_gbs"]), "unit": "GB/s",
                 "frac": frac_hbm, "traffic": None}
+    traffic = None
+    if (N, r, nrhs, kfuse, rtile) == (1 << 20, 9, 64, 4, 32) and kernel_src_sha() == KERNEL_SRC_SHA:
+        traffic = TRAFFIC_N20_R9_NRHS64_K4.get((lo, hi, "H" if kd == ibf.K_FUSED_H else "G"))
+    roof["traffic"] = traffic
     roof.update({"kernel": kname, "avg_launch_ms": avg_ms, "launches_timed": len(per_launch[dom]),
                  "launch_ms": {"%s %d..%d" % ("H" if kk == ibf.K_FUSED_H else "G", a0 + 1, b0):
                                round(statistics.mean(v), 4) for (a0, b0, kk), v in per_launch.items()},
@@ -481,6 +514,8 @@ def main():
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-2d", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--levels-per-launch", type=int, default=0, help="force the fused depth (skips autotuning)")
+    ap.add_argument("--rhs-tile", type=int, default=0, help="force the rhs tile (skips autotuning)")
     a = ap.parse_args()
     if a.warmup < 3 and a.impl == "ibf":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
