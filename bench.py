@@ -233,12 +233,32 @@ def run_batch(ibf, torch, reps=5, count=256, seed=4):
     torch.cuda.synchronize()
     t_loop = e0.elapsed_time(e1) / reps
     err = max(float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)) for a, b in zip(outs, ref))
+    # the same batch as one persistent launch, also replayed from a CUDA graph
+    with torch.cuda.stream(stream):
+        batch.apply_persistent(stream=stream)
+    stream.synchronize()
+    pgraph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(pgraph, stream=stream):
+        batch.apply_persistent(stream=stream)
+    for _ in range(2):
+        pgraph.replay()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        pgraph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    t_pers = e0.elapsed_time(e1) / reps
+    perr = max(float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)) for a, b in zip(outs, ref))
+    pstatus = batch.status()
     vec = int(nr.sum())
     res = {"workload": "256 x 1D FIO, N=2^e e~U{10..16}, nrhs~U{1..64}, r=9, complex64",
            "vectors": vec, "graph_ms": t_graph, "loop_ms": t_loop,
            "graph_vectors_per_s": vec / (t_graph / 1e3), "loop_vectors_per_s": vec / (t_loop / 1e3),
            "speedup_vs_loop": t_loop / t_graph, "launches_graph": batch.query(ibf.BQ_LAUNCHES),
-           "launches_loop": sum(p.query(ibf.Q_LAUNCHES) for p in plans), "max_rel_diff_graph_vs_loop": err}
+           "launches_loop": sum(p.query(ibf.Q_LAUNCHES) for p in plans), "max_rel_diff_graph_vs_loop": err,
+           "persistent_ms": t_pers, "persistent_vectors_per_s": vec / (t_pers / 1e3), "persistent_launches": 1,
+           "persistent_max_rel_diff": perr, "persistent_status": pstatus}
     batch.close()
     for p in plans:
         p.close()

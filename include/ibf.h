@@ -215,8 +215,33 @@ typedef struct ibf_batch ibf_batch;
 int ibf_batch_create(ibf_plan* const* plans, int count, const int* nrhs, const void* const* in, void* const* out,
                      int adjoint, ibf_batch** batch);
 int ibf_batch_apply(const ibf_batch* batch, ibf_stream_t stream);
-enum ibf_batch_query_key { IBF_BQ_LAUNCHES = 0, IBF_BQ_WORKSPACE_BYTES = 1, IBF_BQ_COUNT = 2 };
+enum ibf_batch_query_key { IBF_BQ_LAUNCHES = 0, IBF_BQ_WORKSPACE_BYTES = 1, IBF_BQ_COUNT = 2,
+                           IBF_BQ_PERSIST_ITEMS = 3 };
 int ibf_batch_query(const ibf_batch* batch, int what, int64_t* value);
+
+/*
+ * ibf_batch_apply_persistent -- the same batch in ONE launch.  Persistent CTAs
+ * take work items (a CTA-sized block of one fused chunk of one plan) from a
+ * device counter in chunk-major order; an item of chunk c of a plan first
+ * waits until every item of that plan's chunk c-1 has finished (a device
+ * counter, polled with a bounded number of spins).  Items are handed out in
+ * dependency order to running CTAs only, so the waits cannot deadlock.  The
+ * call resets its counters with stream-ordered memsets and launches one
+ * kernel, so it can be captured in a CUDA graph.  Results equal
+ * ibf_batch_apply's.
+ *
+ * ibf_batch_status synchronizes with the device and returns IBF_ERR_TIMEOUT
+ * if a wait of the last persistent apply ran out of spins (every CTA then
+ * stops early and the outputs are incomplete), else IBF_OK.
+ * ibf_batch_set_wait_limit sets the spin limit (default 2^21, about a second).
+ * ibf_batch_test_withhold(batch, plan, 1) is a test hook: it makes the wait of
+ * that plan's second chunk unsatisfiable, so that a test can check that the
+ * kernel returns with IBF_ERR_TIMEOUT instead of hanging; (..., 0) restores it.
+ */
+int ibf_batch_apply_persistent(const ibf_batch* batch, ibf_stream_t stream);
+int ibf_batch_status(const ibf_batch* batch);
+int ibf_batch_set_wait_limit(ibf_batch* batch, long long spins);
+int ibf_batch_test_withhold(ibf_batch* batch, int plan, int withhold);
 int ibf_batch_destroy(ibf_batch* batch);   /* NULL-safe; synchronizes the device */
 
 /*

@@ -40,9 +40,10 @@ STATUS = {0: "IBF_OK", 1: "IBF_ERR_INVALID", 2: "IBF_ERR_OOM", 3: "IBF_ERR_CUDA"
 EXPORTS = ("ibf_plan_create", "ibf_plan_create_ex", "ibf_apply", "ibf_apply_adjoint", "ibf_plan_destroy",
            "ibf_plan_query", "ibf_get_last_error", "ibf_plan_profile_begin", "ibf_plan_profile_end",
            "ibf_apply_static_scratch", "ibf_batch_create", "ibf_batch_apply", "ibf_batch_query",
-           "ibf_batch_destroy", "ibf_plan_autotune")
+           "ibf_batch_destroy", "ibf_plan_autotune", "ibf_batch_apply_persistent", "ibf_batch_status",
+           "ibf_batch_set_wait_limit", "ibf_batch_test_withhold")
 
-BQ_LAUNCHES, BQ_WORKSPACE_BYTES, BQ_COUNT = range(3)
+BQ_LAUNCHES, BQ_WORKSPACE_BYTES, BQ_COUNT, BQ_PERSIST_ITEMS = range(4)
 
 K_EXPLICIT_INIT, K_EXPLICIT_LEVEL, K_EXPLICIT_SWITCH, K_EXPLICIT_TERM, K_FUSED_H, K_FUSED_G = range(6)
 
@@ -90,6 +91,10 @@ def load_library(path: str | None = None):
     L.ibf_batch_query.argtypes = [P, I, ctypes.POINTER(I64)]
     L.ibf_batch_destroy.argtypes = [P]
     L.ibf_plan_autotune.argtypes = [P, I, P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_float)]
+    L.ibf_batch_apply_persistent.argtypes = [P, P]
+    L.ibf_batch_status.argtypes = [P]
+    L.ibf_batch_set_wait_limit.argtypes = [P, ctypes.c_longlong]
+    L.ibf_batch_test_withhold.argtypes = [P, I, I]
     L.ibf_plan_profile_begin.argtypes = [P, I]
     L.ibf_plan_profile_end.argtypes = [P, P, P, I, ctypes.POINTER(I)]
     for nm in EXPORTS:
@@ -260,6 +265,16 @@ class Batch:
         torch = _torch()
         s = (stream or torch.cuda.current_stream()).cuda_stream
         _check(self._lib.ibf_batch_apply(self._b, ctypes.c_void_p(s)))
+
+    def apply_persistent(self, stream=None):
+        """The whole batch in one persistent launch (ibf_batch_apply_persistent)."""
+        torch = _torch()
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        _check(self._lib.ibf_batch_apply_persistent(self._b, ctypes.c_void_p(s)))
+
+    def status(self) -> int:
+        """IBF_OK (0) or IBF_ERR_TIMEOUT (5) for the last persistent apply."""
+        return self._lib.ibf_batch_status(self._b)
 
     def query(self, what: int) -> int:
         v = ctypes.c_int64()

@@ -26,6 +26,20 @@ struct ibf_batch {
         int kind = 0, rt = 0;
     };
     std::vector<Phase> phases;
+    // persistent single-launch form: descriptors in chunk-major order
+    ibf::FusedDesc* p_descs = nullptr;
+    int64_t* p_start = nullptr;
+    int* p_dep = nullptr;
+    int64_t* p_need = nullptr;
+    int* p_done = nullptr;
+    unsigned long long* p_next = nullptr;
+    int* p_status = nullptr;
+    int p_n = 0;
+    int64_t p_total = 0;
+    size_t p_smem = 0;
+    long long p_max_spin = 1LL << 21;
+    std::vector<int64_t> p_need_host;
+    std::vector<int> p_plan_of, p_chunk_of;
     std::vector<ibf_plan*> plans;
     void* ws = nullptr;
     size_t ws_bytes = 0;
@@ -98,6 +112,67 @@ static int batch_launch(const ibf_batch* b, cudaStream_t st)
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? IBF_OK : cuda_error(e, "batch launch");
+}
+
+template <typename Real, int RP>
+static int persist_launch(const ibf_batch* b, cudaStream_t st)
+{
+    static bool attr = false;
+    static int grid = 0;
+    if (!attr) {
+        int dev = 0, optin = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        // the kernel has a few bytes of static shared memory: the dynamic
+        // limit is the opt-in maximum minus those
+        cudaFuncAttributes fa;
+        cudaFuncGetAttributes(&fa, k_fused_persist<Real, RP, false>);
+        cudaFuncSetAttribute(k_fused_persist<Real, RP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes);
+        cudaFuncGetAttributes(&fa, k_fused_persist<Real, RP, true>);
+        cudaFuncSetAttribute(k_fused_persist<Real, RP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_persist<Real, RP, false>,
+                                                      FusedTraits<Real>::kThreads, 100 * 1024);
+        grid = nsm * std::max(1, per_sm);
+        attr = true;
+        cudaGetLastError();   // the occupancy query is advisory
+    }
+    PersistArgs A;
+    A.descs = b->p_descs;
+    A.start = b->p_start;
+    A.dep = b->p_dep;
+    A.need = b->p_need;
+    A.done = b->p_done;
+    A.next = b->p_next;
+    A.status = b->p_status;
+    A.total = b->p_total;
+    A.n = b->p_n;
+    A.max_spin = b->p_max_spin;
+    cudaMemsetAsync(b->p_done, 0, sizeof(int) * b->p_n, st);
+    cudaMemsetAsync(b->p_next, 0, sizeof(unsigned long long), st);
+    cudaMemsetAsync(b->p_status, 0, sizeof(int), st);
+    const unsigned g = (unsigned)std::min<int64_t>(grid, b->p_total);
+    if (b->adjoint)
+        k_fused_persist<Real, RP, true><<<g, FusedTraits<Real>::kThreads, b->p_smem, st>>>(A);
+    else
+        k_fused_persist<Real, RP, false><<<g, FusedTraits<Real>::kThreads, b->p_smem, st>>>(A);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? IBF_OK : cuda_error(e, "persistent batch launch");
+}
+
+template <typename Real>
+static int persist_dispatch(const ibf_batch* b, cudaStream_t st)
+{
+    switch (b->r) {
+    case 5: return persist_launch<Real, 5>(b, st);
+    case 7: return persist_launch<Real, 7>(b, st);
+    case 9: return persist_launch<Real, 9>(b, st);
+    case 11: return persist_launch<Real, 11>(b, st);
+    default: return set_error(IBF_ERR_UNSUPPORTED, "batch: unsupported r");
+    }
 }
 
 template <typename Real>
@@ -235,6 +310,81 @@ extern "C" int ibf_batch_create(ibf_plan* const* plans, int count, const int* nr
             B->phases.push_back(P);
         }
     }
+    // persistent form: the same chunks, chunk-major, each waiting for its plan's previous chunk
+    {
+        std::vector<FusedDesc> descs;
+        std::vector<int64_t> start, need;
+        std::vector<int> dep;
+        std::vector<int> last(count, -1);
+        std::vector<int64_t> last_blocks(count, 0);
+        int64_t total = 0;
+        size_t smem = 0;
+        for (int ph = 0; ph < nphase; ++ph)
+            for (int b = 0; b < count; ++b) {
+                const int nch = (int)sched[b].size();
+                if (ph >= nch) continue;
+                const ibf_plan* p = plans[b];
+                const Chunk ch = B->adjoint ? sched[b][nch - 1 - ph] : sched[b][ph];
+                FusedDesc d;
+                memset(&d, 0, sizeof(d));
+                d.k = ch.hi - ch.lo;
+                d.l0 = ch.lo;
+                d.kind = ch.kind;
+                for (int s = 1; s <= d.k; ++s) d.D[s - 1] = p->stab[ch.lo + s];
+                if (!B->adjoint) {
+                    d.pro = ch.lo == 0 ? PRO_V : PRO_LAMBDA;
+                    d.epi = ch.hi == p->L ? EPI_U : (ch.hi == p->h ? EPI_SWITCH : EPI_LAMBDA);
+                } else {
+                    d.pro = ch.hi == p->L ? PRO_UADJ : PRO_LAMBDA;
+                    d.epi = ch.lo == 0 ? EPI_VADJ : (ch.lo == p->h ? EPI_SWITCH : EPI_LAMBDA);
+                }
+                char* base = (char*)B->ws + wsoff[b];
+                const size_t half = esz * (size_t)p->N * p->r * nrhs[b];
+                d.in = base + (ph & 1) * half;
+                d.out = base + ((ph & 1) ^ 1) * half;
+                d.vin = in[b];
+                d.vout = out[b];
+                d.Vs = p->sV;
+                d.Us = p->sU;
+                d.Ms = p->sM;
+                d.perm = p->d_perm;
+                d.off = p->d_off;
+                d.N = p->N;
+                d.L = p->L;
+                d.nc = nrhs[b];
+                d.rt = rt[b];
+                const int64_t blocks = (1LL << (p->L - d.k)) * ((nrhs[b] + rt[b] - 1) / rt[b]);
+                dep.push_back(last[b]);
+                need.push_back(last[b] >= 0 ? last_blocks[b] : 0);
+                B->p_plan_of.push_back(b);
+                B->p_chunk_of.push_back(ph);
+                last[b] = (int)descs.size();
+                last_blocks[b] = blocks;
+                descs.push_back(d);
+                start.push_back(total);
+                total += blocks;
+                smem = std::max(smem, fused_smem_bytes(d.k, rt[b], p->r, esz));
+            }
+        B->p_n = (int)descs.size();
+        B->p_total = total;
+        B->p_smem = smem;
+        B->p_need_host = need;
+        if ((rc = balloc(B, (void**)&B->p_descs, sizeof(FusedDesc) * descs.size())) ||
+            (rc = balloc(B, (void**)&B->p_start, sizeof(int64_t) * start.size())) ||
+            (rc = balloc(B, (void**)&B->p_dep, sizeof(int) * dep.size())) ||
+            (rc = balloc(B, (void**)&B->p_need, sizeof(int64_t) * need.size())) ||
+            (rc = balloc(B, (void**)&B->p_done, sizeof(int) * descs.size())) ||
+            (rc = balloc(B, (void**)&B->p_next, sizeof(unsigned long long))) ||
+            (rc = balloc(B, (void**)&B->p_status, sizeof(int)))) {
+            batch_free(B);
+            return rc;
+        }
+        cudaMemcpy(B->p_descs, descs.data(), sizeof(FusedDesc) * descs.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(B->p_start, start.data(), sizeof(int64_t) * start.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(B->p_dep, dep.data(), sizeof(int) * dep.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(B->p_need, need.data(), sizeof(int64_t) * need.size(), cudaMemcpyHostToDevice);
+        cudaMemset(B->p_status, 0, sizeof(int));
+    }
     rc = p0->dtype == IBF_C128 ? fused_upload_consts<double>(p0) : fused_upload_consts<float>(p0);
     if (rc) {
         batch_free(B);
@@ -256,6 +406,44 @@ extern "C" int ibf_batch_apply(const ibf_batch* b, ibf_stream_t stream)
     return batch_dispatch<float>(b, (cudaStream_t)stream);
 }
 
+extern "C" int ibf_batch_apply_persistent(const ibf_batch* b, ibf_stream_t stream)
+{
+    if (!b) return set_error(IBF_ERR_INVALID, "batch is NULL");
+    if (b->p_total <= 0) return IBF_OK;
+    if (b->dtype == IBF_C128) return persist_dispatch<double>(b, (cudaStream_t)stream);
+    return persist_dispatch<float>(b, (cudaStream_t)stream);
+}
+
+extern "C" int ibf_batch_status(const ibf_batch* b)
+{
+    if (!b) return set_error(IBF_ERR_INVALID, "batch is NULL");
+    int st = 0;
+    cudaError_t e = cudaMemcpy(&st, b->p_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "batch status");
+    if (st) return set_error(IBF_ERR_TIMEOUT, "persistent batch: a dependency wait expired");
+    return IBF_OK;
+}
+
+extern "C" int ibf_batch_set_wait_limit(ibf_batch* b, long long spins)
+{
+    if (!b || spins < 1) return set_error(IBF_ERR_INVALID, "bad batch or spin limit");
+    b->p_max_spin = spins;
+    return IBF_OK;
+}
+
+extern "C" int ibf_batch_test_withhold(ibf_batch* b, int plan, int withhold)
+{
+    if (!b || plan < 0 || plan >= b->count) return set_error(IBF_ERR_INVALID, "bad batch or plan index");
+    for (int d = 0; d < b->p_n; ++d) {
+        if (b->p_plan_of[d] != plan || b->p_chunk_of[d] != 1) continue;
+        const int64_t v = withhold ? ((int64_t)1 << 40) : b->p_need_host[d];
+        cudaError_t e = cudaMemcpy(b->p_need + d, &v, sizeof(int64_t), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_error(e, "batch test hook");
+        return IBF_OK;
+    }
+    return set_error(IBF_ERR_INVALID, "plan has a single chunk: nothing to withhold");
+}
+
 extern "C" int ibf_batch_query(const ibf_batch* b, int what, int64_t* v)
 {
     if (!b || !v) return set_error(IBF_ERR_INVALID, "NULL argument");
@@ -263,6 +451,7 @@ extern "C" int ibf_batch_query(const ibf_batch* b, int what, int64_t* v)
     case IBF_BQ_LAUNCHES: *v = (int64_t)b->phases.size(); break;
     case IBF_BQ_WORKSPACE_BYTES: *v = (int64_t)b->ws_bytes; break;
     case IBF_BQ_COUNT: *v = b->count; break;
+    case IBF_BQ_PERSIST_ITEMS: *v = b->p_total; break;
     default: return set_error(IBF_ERR_INVALID, "unknown batch query");
     }
     return IBF_OK;

@@ -160,7 +160,7 @@ __device__ __forceinline__ void cacc(C& a, C b)
 
 // KIND: 0 = H levels (1..h), 1 = G levels (h+1..L).  RT: the rhs tile width
 // when it is known at compile time (32, the batched case), 0 otherwise.
-template <typename Real, int RP, bool ADJ, int KIND, int RT>
+template <typename Real, int RP, bool ADJ, int KIND, int RT, bool COH = false>
 __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const FusedDesc& P, int64_t blk,
                                            unsigned char* smraw)
 {
@@ -234,7 +234,8 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
                 const cx* src = in + pair * RP * P.nc + col0 + lane;
                 cx v[RP];
 #pragma unroll
-                for (int t = 0; t < RP; ++t) v[t] = on ? src[(int64_t)t * P.nc] : cz<cx>();
+                for (int t = 0; t < RP; ++t)
+                    v[t] = on ? (COH ? __ldcg(src + (int64_t)t * P.nc) : src[(int64_t)t * P.nc]) : cz<cx>();
                 cx* dst = sm + pos * PS + lane;
 #pragma unroll
                 for (int t = 0; t < RP; ++t) dst[t * 32] = v[t];
@@ -247,7 +248,8 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
                     pair = (i0 << (L - l0)) + (jb << k) + pos;
                 else
                     pair = (((i0 << k) + brevk(pos, k)) << nbj) + jb;
-                sm[pos * PS + t * rt + c] = c < ncol ? in[(pair * RP + t) * P.nc + col0 + c] : cz<cx>();
+                const cx* a = in + (pair * RP + t) * P.nc + col0 + c;
+                sm[pos * PS + t * rt + c] = c < ncol ? (COH ? __ldcg(a) : *a) : cz<cx>();
             }
         }
     }
@@ -615,6 +617,90 @@ __global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>
             hi = mid - 1;
     }
     fused_body<Real, RP, ADJ, KIND, RT>(c_eo<Real, RP>, descs[lo], b - start[lo], smraw);
+}
+
+// Persistent batched launch: CTAs take work items (one CTA-sized block of one
+// descriptor) from an atomic counter in descriptor order.  Descriptors are
+// ordered chunk-major, so every item a block waits for was handed out before
+// it, to a CTA that is already running: the waits cannot deadlock.  A block of
+// chunk c of a plan waits until all blocks of that plan's chunk c-1 have
+// finished (dep/need), with a bounded spin; on expiry it raises *status and
+// every CTA stops.  Inputs written earlier in the same launch are read with
+// L1-bypassing loads.
+struct PersistArgs {
+    const FusedDesc* descs;
+    const int64_t* start;      // first item of each descriptor (n entries)
+    const int* dep;            // descriptor this one waits for, or -1
+    const int64_t* need;       // blocks of dep that must be done
+    int* done;                 // finished blocks per descriptor (zeroed per apply)
+    unsigned long long* next;  // work counter (zeroed per apply)
+    int* status;               // 0, or 1 after a wait expired
+    int64_t total;
+    int n;
+    long long max_spin;
+};
+
+template <typename Real, int RP, bool ADJ>
+__global__ void __launch_bounds__(FusedTraits<Real>::kThreads, 1)
+    k_fused_persist(const __grid_constant__ PersistArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ long long s_item;
+    __shared__ int s_stop;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_item = (long long)atomicAdd(A.next, 1ULL);
+            s_stop = *(volatile int*)A.status;
+        }
+        __syncthreads();
+        const long long item = s_item;
+        const int stop = s_stop;
+        __syncthreads();
+        if (stop || item >= A.total) break;
+        int lo = 0, hi = A.n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (A.start[mid] <= item)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const FusedDesc& d = A.descs[lo];
+        const int dep = A.dep[lo];
+        if (dep >= 0) {
+            if (threadIdx.x == 0) {
+                long long spins = 0;
+                int ok = 1;
+                while (atomicAdd(A.done + dep, 0) < A.need[lo]) {
+                    if (++spins > A.max_spin || *(volatile int*)A.status) {
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(200);
+                }
+                if (!ok) atomicExch(A.status, 1);
+                __threadfence();
+                s_stop = !ok;
+            }
+            __syncthreads();
+            if (s_stop) break;
+        }
+        const int64_t blk = item - A.start[lo];
+        if (d.kind == 0) {
+            if (d.rt == 32)
+                fused_body<Real, RP, ADJ, 0, 32, true>(c_eo<Real, RP>, d, blk, smraw);
+            else
+                fused_body<Real, RP, ADJ, 0, 0, true>(c_eo<Real, RP>, d, blk, smraw);
+        } else {
+            if (d.rt == 32)
+                fused_body<Real, RP, ADJ, 1, 32, true>(c_eo<Real, RP>, d, blk, smraw);
+            else
+                fused_body<Real, RP, ADJ, 1, 0, true>(c_eo<Real, RP>, d, blk, smraw);
+        }
+        __threadfence();   // this thread's outputs are visible device-wide ...
+        __syncthreads();   // ... for every thread of the block ...
+        if (threadIdx.x == 0) atomicAdd(A.done + lo, 1);   // ... before the block counts as done
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -84,3 +84,61 @@ def test_autotune_keeps_results(ibf):
     assert plan.query(ibf.Q_LEVELS_PER_LAUNCH) == k and plan.query(ibf.Q_RHS_TILE) == rt
     after = plan.apply(g)
     assert _rel(after, before) < 1e-6
+
+
+def test_persistent_single_launch_matches(ibf):
+    Ns, nrhs, plans, ins, outs = _make(ibf, 10, 700)
+    batch = ibf.Batch(plans, ins, outs)
+    batch.apply_persistent()
+    assert batch.status() == 0
+    torch.cuda.synchronize()
+    for b, (p, g, u) in enumerate(zip(plans, ins, outs)):
+        ref = torch.empty_like(g)
+        p.apply_raw(g.data_ptr(), ref.data_ptr(), g.shape[0], torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert _rel(u, ref) < 1e-6, b
+    # adjoint, and replay inside a CUDA graph
+    Ns, nrhs, plans, ins, outs = _make(ibf, 6, 701)
+    batch = ibf.Batch(plans, ins, outs, adjoint=True)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        batch.apply_persistent(stream=s)
+    s.synchronize()
+    first = [o.clone() for o in outs]
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        batch.apply_persistent(stream=s)
+    for o in outs:
+        o.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert batch.status() == 0
+    for a, b in zip(outs, first):
+        assert torch.equal(a, b)
+
+
+def test_persistent_wait_expires_without_hanging(ibf):
+    """A dependency that is never satisfied (test hook) makes the bounded waits
+    run out: the kernel returns, the batch reports IBF_ERR_TIMEOUT, and the
+    context stays usable for a correct run afterwards."""
+    import time
+    Ns, nrhs, plans, ins, outs = _make(ibf, 4, 702, emin=8, emax=10)
+    batch = ibf.Batch(plans, ins, outs)
+    lib = ibf.load_library()
+    assert lib.ibf_batch_set_wait_limit(batch._b, 1 << 12) == 0
+    assert lib.ibf_batch_test_withhold(batch._b, 0, 1) == 0
+    t0 = time.time()
+    batch.apply_persistent()
+    assert batch.status() == 5          # IBF_ERR_TIMEOUT
+    assert time.time() - t0 < 30
+    assert lib.ibf_batch_test_withhold(batch._b, 0, 0) == 0
+    assert lib.ibf_batch_set_wait_limit(batch._b, 1 << 21) == 0
+    batch.apply_persistent()
+    assert batch.status() == 0
+    torch.cuda.synchronize()
+    for p, g, u in zip(plans, ins, outs):
+        ref = torch.empty_like(g)
+        p.apply_raw(g.data_ptr(), ref.data_ptr(), g.shape[0], torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert _rel(u, ref) < 1e-6
