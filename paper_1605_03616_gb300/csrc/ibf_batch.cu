@@ -319,12 +319,22 @@ extern "C" int ibf_batch_create(ibf_plan* const* plans, int count, const int* nr
         std::vector<int64_t> last_blocks(count, 0);
         int64_t total = 0;
         size_t smem = 0;
-        for (int ph = 0; ph < nphase; ++ph)
+        // one CTA shape for the whole launch: 32-column tiles and the fusion
+        // depth that fits them
+        std::vector<std::vector<Chunk>> psched(count);
+        int pphase = 0;
+        for (int b = 0; b < count; ++b) {
+            const ibf_plan* p = plans[b];
+            const int kmax = p->user_kfuse ? std::min(p->kfuse, fused_kmax(32, p->r, esz)) : fused_kmax(32, p->r, esz);
+            psched[b] = fused_schedule(p->L, p->h, std::max(1, kmax));
+            pphase = std::max(pphase, (int)psched[b].size());
+        }
+        for (int ph = 0; ph < pphase; ++ph)
             for (int b = 0; b < count; ++b) {
-                const int nch = (int)sched[b].size();
+                const int nch = (int)psched[b].size();
                 if (ph >= nch) continue;
                 const ibf_plan* p = plans[b];
-                const Chunk ch = B->adjoint ? sched[b][nch - 1 - ph] : sched[b][ph];
+                const Chunk ch = B->adjoint ? psched[b][nch - 1 - ph] : psched[b][ph];
                 FusedDesc d;
                 memset(&d, 0, sizeof(d));
                 d.k = ch.hi - ch.lo;
@@ -352,8 +362,8 @@ extern "C" int ibf_batch_create(ibf_plan* const* plans, int count, const int* nr
                 d.N = p->N;
                 d.L = p->L;
                 d.nc = nrhs[b];
-                d.rt = rt[b];
-                const int64_t blocks = (1LL << (p->L - d.k)) * ((nrhs[b] + rt[b] - 1) / rt[b]);
+                d.rt = 32;   // one CTA shape for the whole launch
+                const int64_t blocks = (1LL << (p->L - d.k)) * ((nrhs[b] + 31) / 32);
                 dep.push_back(last[b]);
                 need.push_back(last[b] >= 0 ? last_blocks[b] : 0);
                 B->p_plan_of.push_back(b);
@@ -363,7 +373,7 @@ extern "C" int ibf_batch_create(ibf_plan* const* plans, int count, const int* nr
                 descs.push_back(d);
                 start.push_back(total);
                 total += blocks;
-                smem = std::max(smem, fused_smem_bytes(d.k, rt[b], p->r, esz));
+                smem = std::max(smem, fused_smem_bytes(d.k, 32, p->r, esz));
             }
         B->p_n = (int)descs.size();
         B->p_total = total;

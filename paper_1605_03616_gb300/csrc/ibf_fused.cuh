@@ -641,7 +641,7 @@ struct PersistArgs {
 };
 
 template <typename Real, int RP, bool ADJ>
-__global__ void __launch_bounds__(FusedTraits<Real>::kThreads, 1)
+__global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>::kMinBlocks)
     k_fused_persist(const __grid_constant__ PersistArgs A)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -686,17 +686,11 @@ __global__ void __launch_bounds__(FusedTraits<Real>::kThreads, 1)
             if (s_stop) break;
         }
         const int64_t blk = item - A.start[lo];
-        if (d.kind == 0) {
-            if (d.rt == 32)
-                fused_body<Real, RP, ADJ, 0, 32, true>(c_eo<Real, RP>, d, blk, smraw);
-            else
-                fused_body<Real, RP, ADJ, 0, 0, true>(c_eo<Real, RP>, d, blk, smraw);
-        } else {
-            if (d.rt == 32)
-                fused_body<Real, RP, ADJ, 1, 32, true>(c_eo<Real, RP>, d, blk, smraw);
-            else
-                fused_body<Real, RP, ADJ, 1, 0, true>(c_eo<Real, RP>, d, blk, smraw);
-        }
+        // every descriptor of the persistent form uses 32-column tiles
+        if (d.kind == 0)
+            fused_body<Real, RP, ADJ, 0, 32, true>(c_eo<Real, RP>, d, blk, smraw);
+        else
+            fused_body<Real, RP, ADJ, 1, 32, true>(c_eo<Real, RP>, d, blk, smraw);
         __threadfence();   // this thread's outputs are visible device-wide ...
         __syncthreads();   // ... for every thread of the block ...
         if (threadIdx.x == 0) atomicAdd(A.done + lo, 1);   // ... before the block counts as done
