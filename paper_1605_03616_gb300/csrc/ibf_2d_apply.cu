@@ -47,11 +47,6 @@ __device__ __forceinline__ void addc(C& a, C b)
     a.y += b.y;
 }
 
-template <typename Real, int RP>
-struct Tmat {
-    Real T[2][RP][RP];   // T_c[t][s] = M_t((2c-1)/4 + z_s/2)
-};
-
 struct RingArgs {
     double q1[12], q2[12];
     int64_t v_stride, d_stride, m_stride;
@@ -105,20 +100,35 @@ __global__ void k2_init(const RingArgs A, int r2, const typename C2D<Real>::T* V
 // One 2D butterfly level l for all 12 boxes.  CTA = (box, unit, rhs tile),
 // unit = (X parent ip at level l-1, Omega box j at level Lq-l); inputs
 // (ip, child c of j), outputs (child a of ip, j), a, c = 2 c1 + c2.
-//   KIND 0 (H): out_a = sum_c (T_{c1} x T_{c2}) (D_{a,c} * in_c)
-//   KIND 1 (G): out_a = sum_c D_{a,c} * (T_{a1} x T_{a2})^T in_c
-template <typename Real, int RP, int KIND>
-__global__ void __launch_bounds__(256) k2_level(const __grid_constant__ Tmat<Real, RP> Tm, const RingArgs A, int l,
-                                                const typename C2D<Real>::T* __restrict__ D,
-                                                const typename C2D<Real>::T* __restrict__ in,
-                                                typename C2D<Real>::T* __restrict__ out, int rt)
+//   H: out_a = sum_c (T_{c1} x T_{c2}) (D_{a,c} * in_c)
+//   G: out_a = sum_c D_{a,c} * (T_{a1} x T_{a2})^T in_c
+
+// Even/odd weights of T_0 (T_1 = J T_0 J, as in 1D): H form rows by input
+// index (PmT[s][t], QmT[s][t]), G form rows by output index (E[t][s], F[t][s]).
+template <typename Real, int RP>
+struct EO2 {
+    static constexpr int HR = (RP + 1) / 2, HQ = RP / 2;
+    Real PmT[RP][HR];
+    Real QmT[RP][HQ];
+    Real E[RP][HR];
+    Real F[RP][HQ];
+};
+
+// 2D H level, even/odd in both tensor directions.  For output a:
+//   W_{c1}[s1][.] = P T_0 (Y_{c1,0}[s1] + J Y_{c1,1}[s1]) + Q T_0 (Y_{c1,0}[s1] - J Y_{c1,1}[s1]),
+//   Y_c = D_{a,c} * X_c, then the same over s1 for c1 = 0, 1.
+template <typename Real, int RP>
+__global__ void __launch_bounds__(256) k2_level_h(const __grid_constant__ EO2<Real, RP> W, const RingArgs A, int l,
+                                                  const typename C2D<Real>::T* __restrict__ D,
+                                                  const typename C2D<Real>::T* __restrict__ in,
+                                                  typename C2D<Real>::T* __restrict__ out, int rt)
 {
     typedef typename C2D<Real>::T cx;
-    constexpr int R2 = RP * RP;
+    constexpr int R2 = RP * RP, HR = EO2<Real, RP>::HR, HQ = EO2<Real, RP>::HQ;
     extern __shared__ __align__(16) unsigned char sraw[];
-    cx* X = reinterpret_cast<cx*>(sraw);          // [4][R2][rt]
-    cx* Wk = X + 4 * R2 * rt;                       // [4][R2][rt]
-    cx* Ds = Wk + 4 * R2 * rt;                      // [4][R2]  D_{a,c} for the current a
+    cx* X = reinterpret_cast<cx*>(sraw);            // [4][R2][rt]
+    cx* Ws = X + 4 * R2 * rt;                         // [2][RP s1][RP t2][rt]
+    cx* Ds = Ws + 2 * R2 * rt;                        // [4][R2]
     const int ntile = (A.nc + rt - 1) / rt;
     const int64_t units = (int64_t)A.m * A.m / 4;
     const int64_t blk = blockIdx.x;
@@ -126,14 +136,12 @@ __global__ void __launch_bounds__(256) k2_level(const __grid_constant__ Tmat<Rea
     const int64_t u = (blk / ntile) % units;
     const int b = (int)(blk / (ntile * units));
     const int col0 = tile * rt, ncol = min(rt, A.nc - col0);
-    const int64_t nj = 1LL << (2 * (A.Lq - l));          // Omega boxes at level Lq-l
+    const int64_t nj = 1LL << (2 * (A.Lq - l)), nC = nj * 4;
     const int64_t ip = u / nj, j = u % nj;
-    const int64_t nC = nj * 4;                            // Omega boxes at level Lq-l+1
     const int64_t mm = (int64_t)A.m * A.m;
     const cx* inb = in + (size_t)b * mm * R2 * A.nc;
     cx* outb = out + (size_t)b * mm * R2 * A.nc;
     const cx* Db = D + (size_t)b * A.d_stride;
-
     for (int e = threadIdx.x; e < 4 * R2 * rt; e += blockDim.x) {
         const int c = e / (R2 * rt), s = (e / rt) % R2, cl = e % rt;
         const int64_t Cc = child2(A.Lq - l, j, c);
@@ -141,82 +149,227 @@ __global__ void __launch_bounds__(256) k2_level(const __grid_constant__ Tmat<Rea
     }
     for (int a = 0; a < 4; ++a) {
         const int64_t Aa = child2(l - 1, ip, a);
-        __syncthreads();   // previous a is done with Ds / Wk
+        __syncthreads();
         for (int e = threadIdx.x; e < 4 * R2; e += blockDim.x) {
             const int c = e / R2, s = e % R2;
-            const int64_t Cc = child2(A.Lq - l, j, c);
-            Ds[e] = Db[(Aa * nC + Cc) * R2 + s];
+            Ds[e] = Db[(Aa * nC + child2(A.Lq - l, j, c)) * R2 + s];
         }
         __syncthreads();
-        const int a1 = a >> 1, a2 = a & 1;
-        if (KIND == 0) {
-            // W[c][s1][t2] = sum_s2 T_{c2}[t2][s2] D_{a,c}[s1,s2] X[c][s1,s2]
-            for (int e = threadIdx.x; e < 4 * R2 * rt; e += blockDim.x) {
-                const int c = e / (R2 * rt), st = (e / rt) % R2, cl = e % rt;
-                const int s1 = st / RP, t2 = st % RP;
-                const Real* Tc2 = Tm.T[c & 1][t2];
-                cx acc = zc<cx>();
+        // pass 1: task (c1, s1, col) -> W_{c1}[s1][t2], t2 = 0..RP-1
+        for (int e = threadIdx.x; e < 2 * RP * rt; e += blockDim.x) {
+            const int cl = e % rt, s1 = (e / rt) % RP, c1 = e / (RP * rt);
+            const int c0 = 2 * c1, cc1 = 2 * c1 + 1;   // children (c1, 0) and (c1, 1)
+            cx we[HR], wo[HQ > 0 ? HQ : 1];
 #pragma unroll
-                for (int s2 = 0; s2 < RP; ++s2) {
-                    const cx y = mulc(Ds[c * R2 + s1 * RP + s2], X[(c * R2 + s1 * RP + s2) * rt + cl]);
-                    acc.x += Tc2[s2] * y.x;
-                    acc.y += Tc2[s2] * y.y;
+            for (int t = 0; t < HR; ++t) we[t] = zc<cx>();
+#pragma unroll
+            for (int t = 0; t < HQ; ++t) wo[t] = zc<cx>();
+#pragma unroll
+            for (int s2 = 0; s2 < RP; ++s2) {
+                const int i0 = s1 * RP + s2, i1 = s1 * RP + (RP - 1 - s2);
+                const cx y0 = mulc(Ds[c0 * R2 + i0], X[(c0 * R2 + i0) * rt + cl]);
+                const cx y1 = mulc(Ds[cc1 * R2 + i1], X[(cc1 * R2 + i1) * rt + cl]);
+                const Real px = y0.x + y1.x, py = y0.y + y1.y, mx = y0.x - y1.x, my = y0.y - y1.y;
+#pragma unroll
+                for (int t = 0; t < HR; ++t) {
+                    we[t].x += W.PmT[s2][t] * px;
+                    we[t].y += W.PmT[s2][t] * py;
                 }
-                Wk[e] = acc;
-            }
-            __syncthreads();
-            // out_a[t1,t2] = sum_c sum_s1 T_{c1}[t1][s1] W[c][s1][t2]
-            for (int e = threadIdx.x; e < R2 * rt; e += blockDim.x) {
-                const int t = e / rt, cl = e % rt;
-                const int t1 = t / RP, t2 = t % RP;
-                cx acc = zc<cx>();
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const Real* Tc1 = Tm.T[c >> 1][t1];
-#pragma unroll
-                    for (int s1 = 0; s1 < RP; ++s1) {
-                        const cx w = Wk[(c * R2 + s1 * RP + t2) * rt + cl];
-                        acc.x += Tc1[s1] * w.x;
-                        acc.y += Tc1[s1] * w.y;
-                    }
+                for (int t = 0; t < HQ; ++t) {
+                    wo[t].x += W.QmT[s2][t] * mx;
+                    wo[t].y += W.QmT[s2][t] * my;
                 }
-                if (cl < ncol) outb[((Aa * nj + j) * R2 + t) * A.nc + col0 + cl] = acc;
             }
-        } else {
-            // W[c][t1][s2] = sum_s1 T_{a1}[s1][t1] X[c][s1,s2]
-            for (int e = threadIdx.x; e < 4 * R2 * rt; e += blockDim.x) {
-                const int c = e / (R2 * rt), ts = (e / rt) % R2, cl = e % rt;
-                const int t1 = ts / RP, s2 = ts % RP;
-                cx acc = zc<cx>();
+            cx* wd = Ws + ((c1 * RP + s1) * RP) * rt + cl;
 #pragma unroll
-                for (int s1 = 0; s1 < RP; ++s1) {
-                    const cx x = X[(c * R2 + s1 * RP + s2) * rt + cl];
-                    const Real tv = Tm.T[a1][s1][t1];
-                    acc.x += tv * x.x;
-                    acc.y += tv * x.y;
+            for (int t = 0; t < HQ; ++t) {
+                cx p, q;
+                p.x = we[t].x + wo[t].x;
+                p.y = we[t].y + wo[t].y;
+                q.x = we[t].x - wo[t].x;
+                q.y = we[t].y - wo[t].y;
+                wd[t * rt] = p;
+                wd[(RP - 1 - t) * rt] = q;
+            }
+            if (RP & 1) wd[HQ * rt] = we[HQ];
+        }
+        __syncthreads();
+        // pass 2: task (t2, col) -> out_a[t1][t2], t1 = 0..RP-1
+        for (int e = threadIdx.x; e < RP * rt; e += blockDim.x) {
+            const int cl = e % rt, t2 = e / rt;
+            cx we[HR], wo[HQ > 0 ? HQ : 1];
+#pragma unroll
+            for (int t = 0; t < HR; ++t) we[t] = zc<cx>();
+#pragma unroll
+            for (int t = 0; t < HQ; ++t) wo[t] = zc<cx>();
+#pragma unroll
+            for (int s1 = 0; s1 < RP; ++s1) {
+                const cx w0 = Ws[((0 * RP + s1) * RP + t2) * rt + cl];
+                const cx w1 = Ws[((1 * RP + (RP - 1 - s1)) * RP + t2) * rt + cl];
+                const Real px = w0.x + w1.x, py = w0.y + w1.y, mx = w0.x - w1.x, my = w0.y - w1.y;
+#pragma unroll
+                for (int t = 0; t < HR; ++t) {
+                    we[t].x += W.PmT[s1][t] * px;
+                    we[t].y += W.PmT[s1][t] * py;
                 }
-                Wk[e] = acc;
-            }
-            __syncthreads();
-            // out_a[t1,t2] = sum_c D_{a,c}[t] sum_s2 T_{a2}[s2][t2] W[c][t1][s2]
-            for (int e = threadIdx.x; e < R2 * rt; e += blockDim.x) {
-                const int t = e / rt, cl = e % rt;
-                const int t1 = t / RP, t2 = t % RP;
-                cx acc = zc<cx>();
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    cx z = zc<cx>();
-#pragma unroll
-                    for (int s2 = 0; s2 < RP; ++s2) {
-                        const cx w = Wk[(c * R2 + t1 * RP + s2) * rt + cl];
-                        const Real tv = Tm.T[a2][s2][t2];
-                        z.x += tv * w.x;
-                        z.y += tv * w.y;
-                    }
-                    addc(acc, mulc(Ds[c * R2 + t], z));
+                for (int t = 0; t < HQ; ++t) {
+                    wo[t].x += W.QmT[s1][t] * mx;
+                    wo[t].y += W.QmT[s1][t] * my;
                 }
-                if (cl < ncol) outb[((Aa * nj + j) * R2 + t) * A.nc + col0 + cl] = acc;
             }
+            if (cl < ncol) {
+                cx* od = outb + ((Aa * nj + j) * R2 + t2) * A.nc + col0 + cl;
+#pragma unroll
+                for (int t = 0; t < HQ; ++t) {
+                    cx p, q;
+                    p.x = we[t].x + wo[t].x;
+                    p.y = we[t].y + wo[t].y;
+                    q.x = we[t].x - wo[t].x;
+                    q.y = we[t].y - wo[t].y;
+                    od[(int64_t)(t * RP) * A.nc] = p;
+                    od[(int64_t)((RP - 1 - t) * RP) * A.nc] = q;
+                }
+                if (RP & 1) od[(int64_t)(HQ * RP) * A.nc] = we[HQ];
+            }
+        }
+    }
+}
+
+// 2D G level: loop over the four inputs c; per input both tensor directions
+// use e/f (T_0^T x = e + f, T_1^T x = J(e - f)) so the four outputs share them.
+// Thread (a1, t1, col) keeps out_{(a1,a2)}[t1][t2] for a2 = 0, 1 in registers.
+template <typename Real>
+constexpr int k2g_threads() { return sizeof(Real) == 8 ? 256 : 512; }
+
+template <typename Real, int RP>
+__global__ void __launch_bounds__(k2g_threads<Real>()) k2_level_g(const __grid_constant__ EO2<Real, RP> W, const RingArgs A, int l,
+                                                  const typename C2D<Real>::T* __restrict__ D,
+                                                  const typename C2D<Real>::T* __restrict__ in,
+                                                  typename C2D<Real>::T* __restrict__ out, int rt)
+{
+    typedef typename C2D<Real>::T cx;
+    constexpr int R2 = RP * RP, HR = EO2<Real, RP>::HR, HQ = EO2<Real, RP>::HQ;
+    extern __shared__ __align__(16) unsigned char sraw[];
+    cx* X = reinterpret_cast<cx*>(sraw);            // [4][R2][rt]
+    cx* Zs = X + 4 * R2 * rt;                         // [2 a1][RP t1][RP s2][rt]
+    cx* Ds = Zs + 2 * R2 * rt;                        // [4 a][4 c][R2]
+    const int ntile = (A.nc + rt - 1) / rt;
+    const int64_t units = (int64_t)A.m * A.m / 4;
+    const int64_t blk = blockIdx.x;
+    const int tile = (int)(blk % ntile);
+    const int64_t u = (blk / ntile) % units;
+    const int b = (int)(blk / (ntile * units));
+    const int col0 = tile * rt, ncol = min(rt, A.nc - col0);
+    const int64_t nj = 1LL << (2 * (A.Lq - l)), nC = nj * 4;
+    const int64_t ip = u / nj, j = u % nj;
+    const int64_t mm = (int64_t)A.m * A.m;
+    const cx* inb = in + (size_t)b * mm * R2 * A.nc;
+    cx* outb = out + (size_t)b * mm * R2 * A.nc;
+    const cx* Db = D + (size_t)b * A.d_stride;
+    for (int e = threadIdx.x; e < 4 * R2 * rt; e += blockDim.x) {
+        const int c = e / (R2 * rt), s = (e / rt) % R2, cl = e % rt;
+        const int64_t Cc = child2(A.Lq - l, j, c);
+        X[e] = cl < ncol ? inb[((ip * nC + Cc) * R2 + s) * A.nc + col0 + cl] : zc<cx>();
+    }
+    for (int e = threadIdx.x; e < 16 * R2; e += blockDim.x) {
+        const int a = e / (4 * R2), c = (e / R2) % 4, s = e % R2;
+        Ds[e] = Db[(child2(l - 1, ip, a) * nC + child2(A.Lq - l, j, c)) * R2 + s];
+    }
+    // this thread's task in pass 2 (fixed over c): (a1, t1, col)
+    const int my = threadIdx.x;
+    const bool mine = my < 2 * RP * rt;
+    const int mcl = my % rt, mt1 = (my / rt) % RP, ma1 = my / (RP * rt);
+    cx acc[2][RP];
+#pragma unroll
+    for (int a2 = 0; a2 < 2; ++a2)
+#pragma unroll
+        for (int t = 0; t < RP; ++t) acc[a2][t] = zc<cx>();
+    for (int c = 0; c < 4; ++c) {
+        __syncthreads();
+        // pass 1: task (s2, col): Z_{a1}[t1][s2] for a1 = 0, 1 from column s2 of X_c
+        for (int e = threadIdx.x; e < RP * rt; e += blockDim.x) {
+            const int cl = e % rt, s2 = e / rt;
+            const cx* xc = X + (c * R2) * rt + cl;
+            cx xe[HR], xo[HQ > 0 ? HQ : 1];
+#pragma unroll
+            for (int s1 = 0; s1 < HQ; ++s1) {
+                const cx lo = xc[(s1 * RP + s2) * rt], hi = xc[((RP - 1 - s1) * RP + s2) * rt];
+                xe[s1].x = lo.x + hi.x;
+                xe[s1].y = lo.y + hi.y;
+                xo[s1].x = lo.x - hi.x;
+                xo[s1].y = lo.y - hi.y;
+            }
+            if (RP & 1) xe[HQ] = xc[(HQ * RP + s2) * rt];
+#pragma unroll
+            for (int t1 = 0; t1 < RP; ++t1) {
+                cx ev = zc<cx>(), fv = zc<cx>();
+#pragma unroll
+                for (int s = 0; s < HR; ++s) {
+                    ev.x += W.E[t1][s] * xe[s].x;
+                    ev.y += W.E[t1][s] * xe[s].y;
+                }
+#pragma unroll
+                for (int s = 0; s < HQ; ++s) {
+                    fv.x += W.F[t1][s] * xo[s].x;
+                    fv.y += W.F[t1][s] * xo[s].y;
+                }
+                cx z0, z1;
+                z0.x = ev.x + fv.x;
+                z0.y = ev.y + fv.y;
+                z1.x = ev.x - fv.x;
+                z1.y = ev.y - fv.y;
+                Zs[((0 * RP + t1) * RP + s2) * rt + cl] = z0;
+                Zs[((1 * RP + (RP - 1 - t1)) * RP + s2) * rt + cl] = z1;
+            }
+        }
+        __syncthreads();
+        // pass 2: task (a1, t1, col): R_{a1,a2}[t1][t2] for a2 = 0, 1, times D_{a,c}
+        if (mine) {
+            const cx* zr = Zs + ((ma1 * RP + mt1) * RP) * rt + mcl;
+            cx xe[HR], xo[HQ > 0 ? HQ : 1];
+#pragma unroll
+            for (int s2 = 0; s2 < HQ; ++s2) {
+                const cx lo = zr[s2 * rt], hi = zr[(RP - 1 - s2) * rt];
+                xe[s2].x = lo.x + hi.x;
+                xe[s2].y = lo.y + hi.y;
+                xo[s2].x = lo.x - hi.x;
+                xo[s2].y = lo.y - hi.y;
+            }
+            if (RP & 1) xe[HQ] = zr[HQ * rt];
+            const cx* d0 = Ds + ((2 * ma1 + 0) * 4 + c) * R2 + mt1 * RP;
+            const cx* d1 = Ds + ((2 * ma1 + 1) * 4 + c) * R2 + mt1 * RP;
+#pragma unroll
+            for (int t2 = 0; t2 < RP; ++t2) {
+                cx ev = zc<cx>(), fv = zc<cx>();
+#pragma unroll
+                for (int s = 0; s < HR; ++s) {
+                    ev.x += W.E[t2][s] * xe[s].x;
+                    ev.y += W.E[t2][s] * xe[s].y;
+                }
+#pragma unroll
+                for (int s = 0; s < HQ; ++s) {
+                    fv.x += W.F[t2][s] * xo[s].x;
+                    fv.y += W.F[t2][s] * xo[s].y;
+                }
+                cx z0, z1;
+                z0.x = ev.x + fv.x;
+                z0.y = ev.y + fv.y;
+                z1.x = ev.x - fv.x;
+                z1.y = ev.y - fv.y;
+                addc(acc[0][t2], mulc(d0[t2], z0));
+                addc(acc[1][RP - 1 - t2], mulc(d1[RP - 1 - t2], z1));
+            }
+        }
+    }
+    if (mine && mcl < ncol) {
+#pragma unroll
+        for (int a2 = 0; a2 < 2; ++a2) {
+            const int64_t Aa = child2(l - 1, ip, 2 * ma1 + a2);
+            cx* od = outb + ((Aa * nj + j) * R2 + mt1 * RP) * A.nc + col0 + mcl;
+#pragma unroll
+            for (int t2 = 0; t2 < RP; ++t2) od[(int64_t)t2 * A.nc] = acc[a2][t2];
         }
     }
 }
@@ -290,18 +443,33 @@ static int apply_2d_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStrea
     typedef typename C2D<Real>::T cx;
     constexpr int R2 = RP * RP;
     Plan2D* P = (Plan2D*)p->p2d;
-    Tmat<Real, RP> Tm;
-    for (int c = 0; c < 2; ++c)
-        for (int t = 0; t < RP; ++t)
-            for (int s = 0; s < RP; ++s) Tm.T[c][t][s] = (Real)p->T[c][t][s];
+    EO2<Real, RP> W;
+    {
+        constexpr int HQ = EO2<Real, RP>::HQ;
+        const auto& T0 = p->T[0];
+        for (int t = 0; t < HQ; ++t)
+            for (int s = 0; s < RP; ++s) {
+                W.PmT[s][t] = (Real)((T0[t][s] + T0[RP - 1 - t][s]) / 2);
+                W.QmT[s][t] = (Real)((T0[t][s] - T0[RP - 1 - t][s]) / 2);
+            }
+        if (RP & 1)
+            for (int s = 0; s < RP; ++s) W.PmT[s][HQ] = (Real)T0[HQ][s];
+        for (int t = 0; t < RP; ++t) {
+            for (int s = 0; s < HQ; ++s) {
+                W.E[t][s] = (Real)((T0[s][t] + T0[RP - 1 - s][t]) / 2);
+                W.F[t][s] = (Real)((T0[s][t] - T0[RP - 1 - s][t]) / 2);
+            }
+            if (RP & 1) W.E[t][HQ] = (Real)T0[HQ][t];
+        }
+    }
     const int64_t N = (int64_t)P->n * P->n;
     static bool attr = false;
     if (!attr) {
         int dev = 0, optin = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        cudaFuncSetAttribute(k2_level<Real, RP, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-        cudaFuncSetAttribute(k2_level<Real, RP, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        cudaFuncSetAttribute(k2_level_h<Real, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        cudaFuncSetAttribute(k2_level_g<Real, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
         attr = true;
     }
     for (int c0 = 0; c0 < nrhs; c0 += p->max_nrhs) {
@@ -311,10 +479,14 @@ static int apply_2d_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStrea
         prof_start(p, st);
         k2_center<Real><<<nb(N * nc), 256, 0, st>>>((const cx*)P->KC, g, u, P->n, P->center, nc);
         prof_mark(p, st, IBF_K_2D);
-        // rhs tile: at most 32 columns and at most ~200 KB of shared memory
-        int rt = std::min(32, nc);
-        while (rt > 1 && (8 * (size_t)R2 * rt + 4 * R2) * sizeof(cx) > 200 * 1024) rt /= 2;
-        const size_t smem = (8 * (size_t)R2 * rt + 4 * R2) * sizeof(cx);
+        // rhs tile: at most 32 columns, 2 r rt G-level tasks within one CTA,
+        // at most ~200 KB of shared memory
+        int rt2 = std::min(nc, 32);
+        while (rt2 > 1 && 2 * RP * rt2 > k2g_threads<Real>()) rt2 /= 2;
+        while (rt2 > 1 && (6 * (size_t)R2 * rt2 + 16 * R2) * sizeof(cx) > 200 * 1024) rt2 /= 2;
+        const int gthreads = (2 * RP * rt2 + 31) / 32 * 32;
+        const size_t smem_h = (6 * (size_t)R2 * rt2 + 4 * R2) * sizeof(cx);
+        const size_t smem_g = (6 * (size_t)R2 * rt2 + 16 * R2) * sizeof(cx);
         for (const Ring2D& R : P->rings) {
             RingArgs A;
             memcpy(A.q1, R.q1, sizeof(A.q1));
@@ -332,13 +504,12 @@ static int apply_2d_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStrea
             cx* b = (cx*)P->ws[1];
             k2_init<Real><<<nb(12 * mm * R2 * nc), 256, 0, st>>>(A, R2, (const cx*)R.V, g, a);
             prof_mark(p, st, IBF_K_2D);
-            const int ntile = (nc + rt - 1) / rt;
-            const int64_t blocks = 12 * (mm / 4) * ntile;
+            const int64_t blocks2 = 12 * (mm / 4) * ((nc + rt2 - 1) / rt2);
             for (int l = 1; l <= R.Lq; ++l) {
                 if (l <= R.hq)
-                    k2_level<Real, RP, 0><<<(unsigned)blocks, 256, smem, st>>>(Tm, A, l, (const cx*)R.D[l], a, b, rt);
+                    k2_level_h<Real, RP><<<(unsigned)blocks2, 256, smem_h, st>>>(W, A, l, (const cx*)R.D[l], a, b, rt2);
                 else
-                    k2_level<Real, RP, 1><<<(unsigned)blocks, 256, smem, st>>>(Tm, A, l, (const cx*)R.D[l], a, b, rt);
+                    k2_level_g<Real, RP><<<(unsigned)blocks2, gthreads, smem_g, st>>>(W, A, l, (const cx*)R.D[l], a, b, rt2);
                 prof_mark(p, st, IBF_K_2D);
                 std::swap(a, b);
                 if (l == R.hq) {
