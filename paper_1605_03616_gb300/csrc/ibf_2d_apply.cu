@@ -60,24 +60,59 @@ __device__ __forceinline__ int64_t child2(int l, int64_t i, int c)
 }
 
 // u[pt + N col] = sum_k KC[pt][k] g[idx(k) + N col]  (the direct centre sum)
+// CTA = (128 points, rhs tile): the centre entries of g for the tile are
+// staged once, KC rows stream through shared memory in chunks of 32; thread
+// (point, column parity) keeps rt/2 outputs so stores run along the points.
 template <typename Real>
-__global__ void k2_center(const typename C2D<Real>::T* KC, const typename C2D<Real>::T* g,
-                          typename C2D<Real>::T* u, int n, int csd, int nc)
+__global__ void __launch_bounds__(256) k2_center(const typename C2D<Real>::T* __restrict__ KC,
+                                                 const typename C2D<Real>::T* __restrict__ g,
+                                                 typename C2D<Real>::T* __restrict__ u, int n, int csd, int nc, int rt)
 {
     typedef typename C2D<Real>::T cx;
-    const int64_t N = (int64_t)n * n;
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= N * nc) return;
-    const int col = (int)(e % nc);
-    const int64_t pt = e / nc;
+    constexpr int PT = 128, KCH = 32, CPT = 16;
+    extern __shared__ __align__(16) unsigned char sraw[];
     const int cc = csd * csd;
-    const cx* kr = KC + pt * cc;
-    cx acc = zc<cx>();
-    for (int k = 0; k < cc; ++k) {
+    cx* Gs = reinterpret_cast<cx*>(sraw);   // [cc][rt]
+    cx* Ks = Gs + (size_t)cc * rt;            // [PT][KCH + 1]
+    const int64_t N = (int64_t)n * n;
+    const int ntile = (nc + rt - 1) / rt;
+    const int tile = (int)(blockIdx.x % ntile);
+    const int64_t pt0 = (blockIdx.x / ntile) * PT;
+    const int col0 = tile * rt, ncol = min(rt, nc - col0);
+    for (int e = threadIdx.x; e < cc * rt; e += blockDim.x) {
+        const int cl = e / cc, k = e % cc;
         const int a1 = k / csd + n / 2 - csd / 2, a2 = k % csd + n / 2 - csd / 2;
-        addc(acc, mulc(kr[k], g[(int64_t)a1 * n + a2 + N * col]));
+        Gs[k * rt + cl] = cl < ncol ? g[(int64_t)a1 * n + a2 + N * (col0 + cl)] : zc<cx>();
     }
-    u[pt + N * col] = acc;
+    const int pl = threadIdx.x % PT, cg = threadIdx.x / PT;
+    cx acc[CPT];
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) acc[k] = zc<cx>();
+    for (int kc = 0; kc < cc; kc += KCH) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < PT * KCH; e += blockDim.x) {
+            const int pr = e / KCH, kk = e % KCH;
+            Ks[pr * (KCH + 1) + kk] = kc + kk < cc ? KC[(pt0 + pr) * cc + kc + kk] : zc<cx>();
+        }
+        __syncthreads();
+        const int kend = min(KCH, cc - kc);
+        for (int kk = 0; kk < kend; ++kk) {
+            const cx kv = Ks[pl * (KCH + 1) + kk];
+            const cx* gr = Gs + (kc + kk) * rt + cg;
+#pragma unroll
+            for (int k = 0; k < CPT; ++k)
+                if (cg + 2 * k < rt) {
+                    const cx x = gr[2 * k];
+                    acc[k].x += kv.x * x.x - kv.y * x.y;
+                    acc[k].y += kv.x * x.y + kv.y * x.x;
+                }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+        const int c = cg + 2 * k;
+        if (c < ncol) u[pt0 + pl + N * (col0 + c)] = acc[k];
+    }
 }
 
 // Lambda^0[box][j][t][col] = V'[box][j][t] g(q_box + j)
@@ -374,65 +409,157 @@ __global__ void __launch_bounds__(k2g_threads<Real>()) k2_level_g(const __grid_c
     }
 }
 
-// switch at level hq: out[p][t] = sum_s M[p][t][s] in[p][s]
-template <typename Real>
-__global__ void k2_switch(const RingArgs A, int r2, const typename C2D<Real>::T* M,
-                          const typename C2D<Real>::T* in, typename C2D<Real>::T* out)
+// Switch at level hq: out[p][t] = sum_s M[p][t][s] in[p][s].  CTA = (box,
+// pair p, rhs tile): M[p] (r^2 x r^2) and the pair's input tile are staged in
+// shared memory; thread (col, t group) keeps the outputs t = tg, tg + TG, ...
+// in registers, so every M entry read from HBM serves the whole tile.
+template <typename Real, int RP>
+__global__ void __launch_bounds__(256) k2_switch(const RingArgs A, const typename C2D<Real>::T* __restrict__ M,
+                                                 const typename C2D<Real>::T* __restrict__ in,
+                                                 typename C2D<Real>::T* __restrict__ out, int rt)
 {
     typedef typename C2D<Real>::T cx;
+    constexpr int R2 = RP * RP, KMAX = (R2 + 7) / 8;
+    extern __shared__ __align__(16) unsigned char sraw[];
+    cx* Ms = reinterpret_cast<cx*>(sraw);   // [R2][R2]
+    cx* Xs = Ms + R2 * R2;                    // [R2][rt]
+    const int ntile = (A.nc + rt - 1) / rt;
     const int64_t mm = (int64_t)A.m * A.m;
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= 12 * mm * r2 * A.nc) return;
-    const int col = (int)(e % A.nc);
-    const int t = (int)((e / A.nc) % r2);
-    const int64_t p = (e / ((int64_t)A.nc * r2)) % mm;
-    const int b = (int)(e / ((int64_t)A.nc * r2 * mm));
-    const cx* Mr = M + b * A.m_stride + (p * r2 + t) * r2;
-    const cx* v = in + ((size_t)(b * mm + p) * r2) * A.nc + col;
-    cx acc = zc<cx>();
-    for (int s = 0; s < r2; ++s) addc(acc, mulc(Mr[s], v[(int64_t)s * A.nc]));
-    out[e] = acc;
+    const int tile = (int)(blockIdx.x % ntile);
+    const int64_t bp = blockIdx.x / ntile;    // b * mm + p
+    const int b = (int)(bp / mm);
+    const int64_t p = bp % mm;
+    const int col0 = tile * rt, ncol = min(rt, A.nc - col0);
+    const cx* Mr = M + b * A.m_stride + p * R2 * R2;
+    for (int e = threadIdx.x; e < R2 * R2; e += blockDim.x) Ms[e] = Mr[e];
+    const cx* xin = in + (size_t)bp * R2 * A.nc + col0;
+    for (int e = threadIdx.x; e < R2 * rt; e += blockDim.x) {
+        const int sidx = e / rt, cl = e % rt;
+        Xs[e] = cl < ncol ? xin[(int64_t)sidx * A.nc + cl] : zc<cx>();
+    }
+    __syncthreads();
+    const int TG = blockDim.x / rt;           // rt divides the block
+    const int cl = threadIdx.x % rt, tg = threadIdx.x / rt;
+    cx acc[KMAX];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) acc[k] = zc<cx>();
+#pragma unroll 4
+    for (int sidx = 0; sidx < R2; ++sidx) {
+        const cx x = Xs[sidx * rt + cl];
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) {
+            const int t = tg + k * TG;
+            if (t < R2) {
+                const cx m = Ms[t * R2 + sidx];
+                acc[k].x += m.x * x.x - m.y * x.y;
+                acc[k].y += m.x * x.y + m.y * x.x;
+            }
+        }
+    }
+    if (cl < ncol) {
+        cx* o = out + (size_t)bp * R2 * A.nc + col0 + cl;
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) {
+            const int t = tg + k * TG;
+            if (t < R2) o[(int64_t)t * A.nc] = acc[k];
+        }
+    }
 }
 
 // u[pt + N col] += sum over the ring's boxes of
 //   uph[box][pt] sum_{t1,t2} lw[o1][t1] lw[o2][t2] Lambda^L[box][leaf(pt)][t][col]
-template <typename Real, int RP>
-__global__ void k2_term(const RingArgs A, const typename C2D<Real>::T* uph, const Real* lw,
-                        const typename C2D<Real>::T* lam, typename C2D<Real>::T* u)
+// CTA = (leaf, PB x PB block of its points, rhs tile).  Per box the leaf's
+// tile is staged, the o2 interpolation is applied once per (o2, t1, col)
+// and reused by every row o1 of the block (separable Lagrange weights).
+template <typename Real, int RP, int PB>
+__global__ void __launch_bounds__(256) k2_term(const RingArgs A, const typename C2D<Real>::T* __restrict__ uph,
+                                               const Real* __restrict__ lw,
+                                               const typename C2D<Real>::T* __restrict__ lam,
+                                               typename C2D<Real>::T* __restrict__ u, int rt)
 {
     typedef typename C2D<Real>::T cx;
-    constexpr int R2 = RP * RP;
+    constexpr int R2 = RP * RP, PAD = 16 / PB, KMAX = PB * PB * 32 / 256;
+    extern __shared__ __align__(16) unsigned char sraw[];
+    cx* Ls = reinterpret_cast<cx*>(sraw);      // [R2][rt]
+    const int SS = RP * rt + PAD;                // stride of one o2 in Ss
+    cx* Ss = Ls + R2 * rt;                       // [PB][RP][rt] (+ pad per o2)
+    cx* Us = Ss + PB * SS;                       // [PB * PB] uph of the block
+    Real* W1 = reinterpret_cast<Real*>(Us + PB * PB);   // [PB][RP]
+    Real* W2 = W1 + PB * RP;                            // [PB][RP]
     const int64_t N = (int64_t)A.n * A.n, mm = (int64_t)A.m * A.m;
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= N * A.nc) return;
-    const int col = (int)(e % A.nc);
-    const int64_t pt = e / A.nc;
-    const int K = A.n / A.m;
-    const int n1 = (int)(pt / A.n), n2 = (int)(pt % A.n);
-    const int64_t leaf = (int64_t)(n1 / K) * A.m + n2 / K;
-    const Real* w1 = lw + (n1 % K) * RP;
-    const Real* w2 = lw + (n2 % K) * RP;
-    cx tot = zc<cx>();
-    for (int b = 0; b < 12; ++b) {
-        const cx* v = lam + ((size_t)(b * mm + leaf) * R2) * A.nc + col;
-        cx acc = zc<cx>();
+    const int K = A.n / A.m, nb1 = K / PB;
+    const int ntile = (A.nc + rt - 1) / rt;
+    const int tile = (int)(blockIdx.x % ntile);
+    const int64_t rest = blockIdx.x / ntile;
+    const int pb = (int)(rest % (nb1 * nb1));
+    const int64_t leaf = rest / (nb1 * nb1);
+    const int o1b = (pb / nb1) * PB, o2b = (pb % nb1) * PB;
+    const int64_t n1b = (leaf / A.m) * K + o1b, n2b = (leaf % A.m) * K + o2b;
+    const int col0 = tile * rt, ncol = min(rt, A.nc - col0);
+    for (int e = threadIdx.x; e < PB * RP; e += blockDim.x) {
+        W1[e] = lw[(o1b + e / RP) * RP + e % RP];
+        W2[e] = lw[(o2b + e / RP) * RP + e % RP];
+    }
+    cx acc[KMAX];
 #pragma unroll
-        for (int t1 = 0; t1 < RP; ++t1) {
-            cx s = zc<cx>();
+    for (int k = 0; k < KMAX; ++k) acc[k] = zc<cx>();
+    for (int b = 0; b < 12; ++b) {
+        __syncthreads();
+        const cx* lb = lam + ((size_t)(b * mm + leaf) * R2) * A.nc + col0;
+        for (int e = threadIdx.x; e < R2 * rt; e += blockDim.x) {
+            const int t = e / rt, cl = e % rt;
+            Ls[e] = cl < ncol ? lb[(int64_t)t * A.nc + cl] : zc<cx>();
+        }
+        for (int e = threadIdx.x; e < PB * PB; e += blockDim.x)
+            Us[e] = uph[b * N + (n1b + e / PB) * A.n + n2b + e % PB];
+        __syncthreads();
+        // S[o2][t1][col] = sum_t2 w2[o2][t2] Lambda[t1 RP + t2][col]
+        for (int e = threadIdx.x; e < PB * RP * rt; e += blockDim.x) {
+            const int cl = e % rt, t1 = (e / rt) % RP, o2 = e / (rt * RP);
+            const cx* lr = Ls + t1 * RP * rt + cl;
+            cx sv = zc<cx>();
 #pragma unroll
             for (int t2 = 0; t2 < RP; ++t2) {
-                const cx x = v[(int64_t)(t1 * RP + t2) * A.nc];
-                s.x += w2[t2] * x.x;
-                s.y += w2[t2] * x.y;
+                const Real w = W2[o2 * RP + t2];
+                const cx x = lr[t2 * rt];
+                sv.x += w * x.x;
+                sv.y += w * x.y;
             }
-            acc.x += w1[t1] * s.x;
-            acc.y += w1[t1] * s.y;
+            Ss[o2 * SS + t1 * rt + cl] = sv;
         }
-        addc(tot, mulc(uph[b * N + pt], acc));
+        __syncthreads();
+        // acc(o1, o2, col) += uph * sum_t1 w1[o1][t1] S[o2][t1][col]
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) {
+            const int q = threadIdx.x + k * 256;
+            if (q < PB * PB * rt) {
+                const int o2 = q % PB, cl = (q / PB) % rt, o1 = q / (PB * rt);
+                const cx* sr = Ss + o2 * SS + cl;
+                cx v = zc<cx>();
+#pragma unroll
+                for (int t1 = 0; t1 < RP; ++t1) {
+                    const Real w = W1[o1 * RP + t1];
+                    const cx x = sr[t1 * rt];
+                    v.x += w * x.x;
+                    v.y += w * x.y;
+                }
+                addc(acc[k], mulc(Us[o1 * PB + o2], v));
+            }
+        }
     }
-    cx o = u[pt + N * col];
-    addc(o, tot);
-    u[pt + N * col] = o;
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        const int q = threadIdx.x + k * 256;
+        if (q < PB * PB * rt) {
+            const int o2 = q % PB, cl = (q / PB) % rt, o1 = q / (PB * rt);
+            if (cl < ncol) {
+                cx* up = u + (n1b + o1) * A.n + n2b + o2 + N * (col0 + cl);
+                cx o = *up;
+                addc(o, acc[k]);
+                *up = o;
+            }
+        }
+    }
 }
 
 static inline unsigned nb(int64_t n) { return (unsigned)((n + 255) / 256); }
@@ -470,6 +597,10 @@ static int apply_2d_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStrea
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         cudaFuncSetAttribute(k2_level_h<Real, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
         cudaFuncSetAttribute(k2_level_g<Real, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        cudaFuncSetAttribute(k2_switch<Real, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        cudaFuncSetAttribute(k2_center<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        cudaFuncSetAttribute(k2_term<Real, RP, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        cudaFuncSetAttribute(k2_term<Real, RP, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
         attr = true;
     }
     for (int c0 = 0; c0 < nrhs; c0 += p->max_nrhs) {
@@ -477,7 +608,13 @@ static int apply_2d_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStrea
         const cx* g = (const cx*)gv + N * c0;
         cx* u = (cx*)uv + N * c0;
         prof_start(p, st);
-        k2_center<Real><<<nb(N * nc), 256, 0, st>>>((const cx*)P->KC, g, u, P->n, P->center, nc);
+        {
+            int rtc = 1;
+            while (rtc < 32 && rtc < nc) rtc *= 2;
+            const size_t smem_c = ((size_t)P->center * P->center * rtc + 128 * 33) * sizeof(cx);
+            k2_center<Real><<<(unsigned)(N / 128 * ((nc + rtc - 1) / rtc)), 256, smem_c, st>>>(
+                (const cx*)P->KC, g, u, P->n, P->center, nc, rtc);
+        }
         prof_mark(p, st, IBF_K_2D);
         // rhs tile: at most 32 columns, 2 r rt G-level tasks within one CTA,
         // at most ~200 KB of shared memory
@@ -485,6 +622,15 @@ static int apply_2d_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStrea
         while (rt2 > 1 && 2 * RP * rt2 > k2g_threads<Real>()) rt2 /= 2;
         while (rt2 > 1 && (6 * (size_t)R2 * rt2 + 16 * R2) * sizeof(cx) > 200 * 1024) rt2 /= 2;
         const int gthreads = (2 * RP * rt2 + 31) / 32 * 32;
+        // switch and term: rhs tile a power of two up to 32 (it divides 256)
+        int rts = 1;
+        while (rts < 32 && rts < nc) rts *= 2;
+        const int ntile_s = (nc + rts - 1) / rts;
+        const size_t smem_s = ((size_t)R2 * R2 + (size_t)R2 * rts) * sizeof(cx);
+        auto term_smem = [&](int pbs) {
+            return ((size_t)R2 * rts + (size_t)pbs * (RP * rts + 16 / pbs) + pbs * pbs) * sizeof(cx) +
+                   2 * (size_t)pbs * RP * sizeof(Real);
+        };
         const size_t smem_h = (6 * (size_t)R2 * rt2 + 4 * R2) * sizeof(cx);
         const size_t smem_g = (6 * (size_t)R2 * rt2 + 16 * R2) * sizeof(cx);
         for (const Ring2D& R : P->rings) {
@@ -513,12 +659,18 @@ static int apply_2d_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStrea
                 prof_mark(p, st, IBF_K_2D);
                 std::swap(a, b);
                 if (l == R.hq) {
-                    k2_switch<Real><<<nb(12 * mm * R2 * nc), 256, 0, st>>>(A, R2, (const cx*)R.M, a, b);
+                    k2_switch<Real, RP><<<(unsigned)(12 * mm * ntile_s), 256, smem_s, st>>>(A, (const cx*)R.M, a, b,
+                                                                                            rts);
                     prof_mark(p, st, IBF_K_2D);
                     std::swap(a, b);
                 }
             }
-            k2_term<Real, RP><<<nb(N * nc), 256, 0, st>>>(A, (const cx*)R.uph, (const Real*)R.lw, a, u);
+            if (P->n / R.m >= 8)
+                k2_term<Real, RP, 8><<<(unsigned)(mm * (P->n / R.m / 8) * (P->n / R.m / 8) * ntile_s), 256,
+                                       term_smem(8), st>>>(A, (const cx*)R.uph, (const Real*)R.lw, a, u, rts);
+            else
+                k2_term<Real, RP, 4><<<(unsigned)(mm * (P->n / R.m / 4) * (P->n / R.m / 4) * ntile_s), 256,
+                                       term_smem(4), st>>>(A, (const cx*)R.uph, (const Real*)R.lw, a, u, rts);
             prof_mark(p, st, IBF_K_2D);
         }
     }

@@ -32,7 +32,7 @@ def _run(ibf, phase, n, r, dtype, g):
 
 @pytest.mark.parametrize("phase,n,r,nrhs", [(O.PHASE_SEPARABLE, 32, 5, 2), (O.PHASE_FIO2D, 32, 7, 3),
                                             (O.PHASE_FIO2D, 64, 5, 1), (O.PHASE_NUFFT, 64, 7, 2),
-                                            (O.PHASE_FIO2D, 64, 9, 2)])
+                                            (O.PHASE_FIO2D, 64, 9, 2), (O.PHASE_FIO2D, 64, 7, 37)])
 def test_2d_matches_oracle_mibf(ibf, phase, n, r, nrhs):
     x = W.grid_x_2d(n)
     g = W.complex_normal((n * n, nrhs), W.rng(601))
