@@ -149,51 +149,89 @@ struct EO2 {
     Real F[RP][HQ];
 };
 
+// Child of box i at quadtree level l (side 2^l boxes per axis), c = 2 c1 + c2.
+__device__ __forceinline__ int64_t child2s(int l, int64_t i, int c)
+{
+    return ((2 * (i >> l) + (c >> 1)) << (l + 1)) + 2 * (i & ((1LL << l) - 1)) + (c & 1);
+}
+
+// Shared prologue of both level kernels: the CTA's unit and rhs tile, its
+// four input blocks X[c][s][col] and all sixteen diagonals D[a][c][s].
+template <typename Real, int RP>
+struct LevelTile {
+    typedef typename C2D<Real>::T cx;
+    static constexpr int R2 = RP * RP;
+    int64_t ip, j, nj;
+    int col0, ncol;
+    cx* outb;
+    __device__ void stage(const RingArgs& A, int l, const cx* D, const cx* in, cx* out, int rt, int lrt, cx* X,
+                          cx* Ds)
+    {
+        const int ntile = (A.nc + rt - 1) >> lrt;
+        const int64_t units = (int64_t)A.m * A.m / 4;
+        const int tile = (int)(blockIdx.x % ntile);
+        const int64_t u = (blockIdx.x / ntile) % units;
+        const int b = (int)(blockIdx.x / (ntile * units));
+        col0 = tile << lrt;
+        ncol = min(rt, A.nc - col0);
+        const int ql = 2 * (A.Lq - l);
+        nj = 1LL << ql;
+        ip = u >> ql;
+        j = u & (nj - 1);
+        const int64_t nC = nj * 4, mm = (int64_t)A.m * A.m;
+        const cx* inb = in + (size_t)b * mm * R2 * A.nc + col0;
+        outb = out + (size_t)b * mm * R2 * A.nc + col0;
+        const cx* Db = D + (size_t)b * A.d_stride;
+        const int cl = threadIdx.x & (rt - 1), srow = threadIdx.x >> lrt, sstep = blockDim.x >> lrt;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const cx* src = inb + (ip * nC + child2s(A.Lq - l, j, c)) * R2 * A.nc;
+            for (int sidx = srow; sidx < R2; sidx += sstep)
+                X[(c * R2 + sidx) * rt + cl] = cl < ncol ? src[(int64_t)sidx * A.nc + cl] : zc<cx>();
+        }
+        for (int e = threadIdx.x; e < 16 * R2; e += blockDim.x) {
+            const int ac = e / R2, sidx = e - ac * R2;
+            Ds[e] = Db[(child2s(l - 1, ip, ac >> 2) * nC + child2s(A.Lq - l, j, ac & 3)) * R2 + sidx];
+        }
+    }
+};
+
+// Level kernels: 2 r rt threads with rt = 16 (FP32) or 8 (FP64) columns.
+template <typename Real, int RP>
+constexpr int k2_level_threads() { return (2 * RP * (sizeof(Real) == 8 ? 8 : 16) + 31) / 32 * 32; }
+template <typename Real, int RP>
+constexpr int k2_level_blocks() { return sizeof(Real) == 8 ? 1 : (RP > 7 ? 2 : 3); }
+
 // 2D H level, even/odd in both tensor directions.  For output a:
 //   W_{c1}[s1][.] = P T_0 (Y_{c1,0}[s1] + J Y_{c1,1}[s1]) + Q T_0 (Y_{c1,0}[s1] - J Y_{c1,1}[s1]),
-//   Y_c = D_{a,c} * X_c, then the same over s1 for c1 = 0, 1.
+//   Y_c = D_{a,c} * X_c, then the same over s1 for c1 = 0, 1.  Two outputs
+// per pass: 4 r rt tasks in pass 1, 2 r rt in pass 2, 2 r rt threads.
 template <typename Real, int RP>
-__global__ void __launch_bounds__(256) k2_level_h(const __grid_constant__ EO2<Real, RP> W, const RingArgs A, int l,
-                                                  const typename C2D<Real>::T* __restrict__ D,
-                                                  const typename C2D<Real>::T* __restrict__ in,
-                                                  typename C2D<Real>::T* __restrict__ out, int rt)
+__global__ void __launch_bounds__(k2_level_threads<Real, RP>(), k2_level_blocks<Real, RP>())
+    k2_level_h(const __grid_constant__ EO2<Real, RP> W, const RingArgs A, int l,
+               const typename C2D<Real>::T* __restrict__ D, const typename C2D<Real>::T* __restrict__ in,
+               typename C2D<Real>::T* __restrict__ out, int rt, int lrt)
 {
     typedef typename C2D<Real>::T cx;
     constexpr int R2 = RP * RP, HR = EO2<Real, RP>::HR, HQ = EO2<Real, RP>::HQ;
     extern __shared__ __align__(16) unsigned char sraw[];
-    cx* X = reinterpret_cast<cx*>(sraw);            // [4][R2][rt]
-    cx* Ws = X + 4 * R2 * rt;                         // [2][RP s1][RP t2][rt]
-    cx* Ds = Ws + 2 * R2 * rt;                        // [4][R2]
-    const int ntile = (A.nc + rt - 1) / rt;
-    const int64_t units = (int64_t)A.m * A.m / 4;
-    const int64_t blk = blockIdx.x;
-    const int tile = (int)(blk % ntile);
-    const int64_t u = (blk / ntile) % units;
-    const int b = (int)(blk / (ntile * units));
-    const int col0 = tile * rt, ncol = min(rt, A.nc - col0);
-    const int64_t nj = 1LL << (2 * (A.Lq - l)), nC = nj * 4;
-    const int64_t ip = u / nj, j = u % nj;
-    const int64_t mm = (int64_t)A.m * A.m;
-    const cx* inb = in + (size_t)b * mm * R2 * A.nc;
-    cx* outb = out + (size_t)b * mm * R2 * A.nc;
-    const cx* Db = D + (size_t)b * A.d_stride;
-    for (int e = threadIdx.x; e < 4 * R2 * rt; e += blockDim.x) {
-        const int c = e / (R2 * rt), s = (e / rt) % R2, cl = e % rt;
-        const int64_t Cc = child2(A.Lq - l, j, c);
-        X[e] = cl < ncol ? inb[((ip * nC + Cc) * R2 + s) * A.nc + col0 + cl] : zc<cx>();
-    }
-    for (int a = 0; a < 4; ++a) {
-        const int64_t Aa = child2(l - 1, ip, a);
+    cx* X = reinterpret_cast<cx*>(sraw);            // [4 c][R2][rt]
+    cx* Ws = X + 4 * R2 * rt;                         // [2 a][2 c1][RP s1][RP t2][rt]
+    cx* Ds = Ws + 4 * R2 * rt;                        // [4 a][4 c][R2]
+    LevelTile<Real, RP> T;
+    T.stage(A, l, D, in, out, rt, lrt, X, Ds);
+    const int msk = rt - 1;
+    for (int a0 = 0; a0 < 4; a0 += 2) {
         __syncthreads();
-        for (int e = threadIdx.x; e < 4 * R2; e += blockDim.x) {
-            const int c = e / R2, s = e % R2;
-            Ds[e] = Db[(Aa * nC + child2(A.Lq - l, j, c)) * R2 + s];
-        }
-        __syncthreads();
-        // pass 1: task (c1, s1, col) -> W_{c1}[s1][t2], t2 = 0..RP-1
-        for (int e = threadIdx.x; e < 2 * RP * rt; e += blockDim.x) {
-            const int cl = e % rt, s1 = (e / rt) % RP, c1 = e / (RP * rt);
+        // pass 1: task (ah, c1, s1, col) -> W_{a0+ah, c1}[s1][t2], t2 = 0..RP-1
+        for (int e = threadIdx.x; e < 4 * RP * rt; e += blockDim.x) {
+            const int cl = e & msk, q = e >> lrt;
+            const int s1 = q % RP, r4 = q / RP, c1 = r4 & 1, ah = r4 >> 1;
             const int c0 = 2 * c1, cc1 = 2 * c1 + 1;   // children (c1, 0) and (c1, 1)
+            const cx* d0 = Ds + ((a0 + ah) * 4 + c0) * R2 + s1 * RP;
+            const cx* d1 = Ds + ((a0 + ah) * 4 + cc1) * R2 + s1 * RP;
+            const cx* x0 = X + (c0 * R2 + s1 * RP) * rt + cl;
+            const cx* x1 = X + (cc1 * R2 + s1 * RP) * rt + cl;
             cx we[HR], wo[HQ > 0 ? HQ : 1];
 #pragma unroll
             for (int t = 0; t < HR; ++t) we[t] = zc<cx>();
@@ -201,9 +239,8 @@ __global__ void __launch_bounds__(256) k2_level_h(const __grid_constant__ EO2<Re
             for (int t = 0; t < HQ; ++t) wo[t] = zc<cx>();
 #pragma unroll
             for (int s2 = 0; s2 < RP; ++s2) {
-                const int i0 = s1 * RP + s2, i1 = s1 * RP + (RP - 1 - s2);
-                const cx y0 = mulc(Ds[c0 * R2 + i0], X[(c0 * R2 + i0) * rt + cl]);
-                const cx y1 = mulc(Ds[cc1 * R2 + i1], X[(cc1 * R2 + i1) * rt + cl]);
+                const cx y0 = mulc(d0[s2], x0[s2 * rt]);
+                const cx y1 = mulc(d1[RP - 1 - s2], x1[(RP - 1 - s2) * rt]);
                 const Real px = y0.x + y1.x, py = y0.y + y1.y, mx = y0.x - y1.x, my = y0.y - y1.y;
 #pragma unroll
                 for (int t = 0; t < HR; ++t) {
@@ -216,23 +253,26 @@ __global__ void __launch_bounds__(256) k2_level_h(const __grid_constant__ EO2<Re
                     wo[t].y += W.QmT[s2][t] * my;
                 }
             }
-            cx* wd = Ws + ((c1 * RP + s1) * RP) * rt + cl;
+            cx* wd = Ws + (((ah * 2 + c1) * RP + s1) * RP) * rt + cl;
 #pragma unroll
             for (int t = 0; t < HQ; ++t) {
-                cx p, q;
+                cx p, m;
                 p.x = we[t].x + wo[t].x;
                 p.y = we[t].y + wo[t].y;
-                q.x = we[t].x - wo[t].x;
-                q.y = we[t].y - wo[t].y;
+                m.x = we[t].x - wo[t].x;
+                m.y = we[t].y - wo[t].y;
                 wd[t * rt] = p;
-                wd[(RP - 1 - t) * rt] = q;
+                wd[(RP - 1 - t) * rt] = m;
             }
             if (RP & 1) wd[HQ * rt] = we[HQ];
         }
         __syncthreads();
-        // pass 2: task (t2, col) -> out_a[t1][t2], t1 = 0..RP-1
-        for (int e = threadIdx.x; e < RP * rt; e += blockDim.x) {
-            const int cl = e % rt, t2 = e / rt;
+        // pass 2: task (ah, t2, col) -> out_{a0+ah}[t1][t2], t1 = 0..RP-1
+        for (int e = threadIdx.x; e < 2 * RP * rt; e += blockDim.x) {
+            const int cl = e & msk, q = e >> lrt;
+            const int t2 = q % RP, ah = q / RP;
+            const cx* w0 = Ws + ((ah * 2 + 0) * R2 + t2) * rt + cl;
+            const cx* w1 = Ws + ((ah * 2 + 1) * R2 + t2) * rt + cl;
             cx we[HR], wo[HQ > 0 ? HQ : 1];
 #pragma unroll
             for (int t = 0; t < HR; ++t) we[t] = zc<cx>();
@@ -240,9 +280,9 @@ __global__ void __launch_bounds__(256) k2_level_h(const __grid_constant__ EO2<Re
             for (int t = 0; t < HQ; ++t) wo[t] = zc<cx>();
 #pragma unroll
             for (int s1 = 0; s1 < RP; ++s1) {
-                const cx w0 = Ws[((0 * RP + s1) * RP + t2) * rt + cl];
-                const cx w1 = Ws[((1 * RP + (RP - 1 - s1)) * RP + t2) * rt + cl];
-                const Real px = w0.x + w1.x, py = w0.y + w1.y, mx = w0.x - w1.x, my = w0.y - w1.y;
+                const cx v0 = w0[s1 * RP * rt];
+                const cx v1 = w1[(RP - 1 - s1) * RP * rt];
+                const Real px = v0.x + v1.x, py = v0.y + v1.y, mx = v0.x - v1.x, my = v0.y - v1.y;
 #pragma unroll
                 for (int t = 0; t < HR; ++t) {
                     we[t].x += W.PmT[s1][t] * px;
@@ -254,17 +294,18 @@ __global__ void __launch_bounds__(256) k2_level_h(const __grid_constant__ EO2<Re
                     wo[t].y += W.QmT[s1][t] * my;
                 }
             }
-            if (cl < ncol) {
-                cx* od = outb + ((Aa * nj + j) * R2 + t2) * A.nc + col0 + cl;
+            if (cl < T.ncol) {
+                const int64_t Aa = child2s(l - 1, T.ip, a0 + ah);
+                cx* od = T.outb + ((Aa * T.nj + T.j) * R2 + t2) * A.nc + cl;
 #pragma unroll
                 for (int t = 0; t < HQ; ++t) {
-                    cx p, q;
+                    cx p, m;
                     p.x = we[t].x + wo[t].x;
                     p.y = we[t].y + wo[t].y;
-                    q.x = we[t].x - wo[t].x;
-                    q.y = we[t].y - wo[t].y;
+                    m.x = we[t].x - wo[t].x;
+                    m.y = we[t].y - wo[t].y;
                     od[(int64_t)(t * RP) * A.nc] = p;
-                    od[(int64_t)((RP - 1 - t) * RP) * A.nc] = q;
+                    od[(int64_t)((RP - 1 - t) * RP) * A.nc] = m;
                 }
                 if (RP & 1) od[(int64_t)(HQ * RP) * A.nc] = we[HQ];
             }
@@ -272,137 +313,121 @@ __global__ void __launch_bounds__(256) k2_level_h(const __grid_constant__ EO2<Re
     }
 }
 
-// 2D G level: loop over the four inputs c; per input both tensor directions
-// use e/f (T_0^T x = e + f, T_1^T x = J(e - f)) so the four outputs share them.
-// Thread (a1, t1, col) keeps out_{(a1,a2)}[t1][t2] for a2 = 0, 1 in registers.
-template <typename Real>
-constexpr int k2g_threads() { return sizeof(Real) == 8 ? 256 : 512; }
-
+// 2D G level: both tensor directions use e/f (T_0^T x = e + f,
+// T_1^T x = J(e - f)) so the four outputs share one pass per input.  Two
+// inputs per pass 1 (2 r rt tasks); thread (a1, t1, col) keeps
+// out_{(a1,a2)}[t1][.] for a2 = 0, 1 in registers over all four inputs.
 template <typename Real, int RP>
-__global__ void __launch_bounds__(k2g_threads<Real>()) k2_level_g(const __grid_constant__ EO2<Real, RP> W, const RingArgs A, int l,
-                                                  const typename C2D<Real>::T* __restrict__ D,
-                                                  const typename C2D<Real>::T* __restrict__ in,
-                                                  typename C2D<Real>::T* __restrict__ out, int rt)
+__global__ void __launch_bounds__(k2_level_threads<Real, RP>(), k2_level_blocks<Real, RP>())
+    k2_level_g(const __grid_constant__ EO2<Real, RP> W, const RingArgs A, int l,
+               const typename C2D<Real>::T* __restrict__ D, const typename C2D<Real>::T* __restrict__ in,
+               typename C2D<Real>::T* __restrict__ out, int rt, int lrt)
 {
     typedef typename C2D<Real>::T cx;
     constexpr int R2 = RP * RP, HR = EO2<Real, RP>::HR, HQ = EO2<Real, RP>::HQ;
     extern __shared__ __align__(16) unsigned char sraw[];
-    cx* X = reinterpret_cast<cx*>(sraw);            // [4][R2][rt]
-    cx* Zs = X + 4 * R2 * rt;                         // [2 a1][RP t1][RP s2][rt]
-    cx* Ds = Zs + 2 * R2 * rt;                        // [4 a][4 c][R2]
-    const int ntile = (A.nc + rt - 1) / rt;
-    const int64_t units = (int64_t)A.m * A.m / 4;
-    const int64_t blk = blockIdx.x;
-    const int tile = (int)(blk % ntile);
-    const int64_t u = (blk / ntile) % units;
-    const int b = (int)(blk / (ntile * units));
-    const int col0 = tile * rt, ncol = min(rt, A.nc - col0);
-    const int64_t nj = 1LL << (2 * (A.Lq - l)), nC = nj * 4;
-    const int64_t ip = u / nj, j = u % nj;
-    const int64_t mm = (int64_t)A.m * A.m;
-    const cx* inb = in + (size_t)b * mm * R2 * A.nc;
-    cx* outb = out + (size_t)b * mm * R2 * A.nc;
-    const cx* Db = D + (size_t)b * A.d_stride;
-    for (int e = threadIdx.x; e < 4 * R2 * rt; e += blockDim.x) {
-        const int c = e / (R2 * rt), s = (e / rt) % R2, cl = e % rt;
-        const int64_t Cc = child2(A.Lq - l, j, c);
-        X[e] = cl < ncol ? inb[((ip * nC + Cc) * R2 + s) * A.nc + col0 + cl] : zc<cx>();
-    }
-    for (int e = threadIdx.x; e < 16 * R2; e += blockDim.x) {
-        const int a = e / (4 * R2), c = (e / R2) % 4, s = e % R2;
-        Ds[e] = Db[(child2(l - 1, ip, a) * nC + child2(A.Lq - l, j, c)) * R2 + s];
-    }
-    // this thread's task in pass 2 (fixed over c): (a1, t1, col)
-    const int my = threadIdx.x;
-    const bool mine = my < 2 * RP * rt;
-    const int mcl = my % rt, mt1 = (my / rt) % RP, ma1 = my / (RP * rt);
+    cx* X = reinterpret_cast<cx*>(sraw);            // [4 c][R2][rt]
+    cx* Zs = X + 4 * R2 * rt;                         // [2 ch][2 a1][RP t1][RP s2][rt]
+    cx* Ds = Zs + 4 * R2 * rt;                        // [4 a][4 c][R2]
+    LevelTile<Real, RP> T;
+    T.stage(A, l, D, in, out, rt, lrt, X, Ds);
+    const int msk = rt - 1;
+    const bool mine = threadIdx.x < 2 * RP * rt;
+    const int mcl = threadIdx.x & msk, mq = threadIdx.x >> lrt;
+    const int mt1 = mq % RP, ma1 = mq / RP;
     cx acc[2][RP];
 #pragma unroll
     for (int a2 = 0; a2 < 2; ++a2)
 #pragma unroll
         for (int t = 0; t < RP; ++t) acc[a2][t] = zc<cx>();
-    for (int c = 0; c < 4; ++c) {
+    for (int c0 = 0; c0 < 4; c0 += 2) {
         __syncthreads();
-        // pass 1: task (s2, col): Z_{a1}[t1][s2] for a1 = 0, 1 from column s2 of X_c
-        for (int e = threadIdx.x; e < RP * rt; e += blockDim.x) {
-            const int cl = e % rt, s2 = e / rt;
-            const cx* xc = X + (c * R2) * rt + cl;
+        // pass 1: task (ch, s2, col): Z_{ch, a1}[t1][s2] for a1 = 0, 1 from column s2 of X_{c0+ch}
+        for (int e = threadIdx.x; e < 2 * RP * rt; e += blockDim.x) {
+            const int cl = e & msk, q = e >> lrt;
+            const int s2 = q % RP, ch = q / RP;
+            const cx* xc = X + ((c0 + ch) * R2 + s2) * rt + cl;
             cx xe[HR], xo[HQ > 0 ? HQ : 1];
 #pragma unroll
             for (int s1 = 0; s1 < HQ; ++s1) {
-                const cx lo = xc[(s1 * RP + s2) * rt], hi = xc[((RP - 1 - s1) * RP + s2) * rt];
+                const cx lo = xc[s1 * RP * rt], hi = xc[(RP - 1 - s1) * RP * rt];
                 xe[s1].x = lo.x + hi.x;
                 xe[s1].y = lo.y + hi.y;
                 xo[s1].x = lo.x - hi.x;
                 xo[s1].y = lo.y - hi.y;
             }
-            if (RP & 1) xe[HQ] = xc[(HQ * RP + s2) * rt];
+            if (RP & 1) xe[HQ] = xc[HQ * RP * rt];
+            cx* z = Zs + (ch * 2 * R2 + s2) * rt + cl;
 #pragma unroll
             for (int t1 = 0; t1 < RP; ++t1) {
                 cx ev = zc<cx>(), fv = zc<cx>();
 #pragma unroll
-                for (int s = 0; s < HR; ++s) {
-                    ev.x += W.E[t1][s] * xe[s].x;
-                    ev.y += W.E[t1][s] * xe[s].y;
+                for (int sidx = 0; sidx < HR; ++sidx) {
+                    ev.x += W.E[t1][sidx] * xe[sidx].x;
+                    ev.y += W.E[t1][sidx] * xe[sidx].y;
                 }
 #pragma unroll
-                for (int s = 0; s < HQ; ++s) {
-                    fv.x += W.F[t1][s] * xo[s].x;
-                    fv.y += W.F[t1][s] * xo[s].y;
+                for (int sidx = 0; sidx < HQ; ++sidx) {
+                    fv.x += W.F[t1][sidx] * xo[sidx].x;
+                    fv.y += W.F[t1][sidx] * xo[sidx].y;
                 }
                 cx z0, z1;
                 z0.x = ev.x + fv.x;
                 z0.y = ev.y + fv.y;
                 z1.x = ev.x - fv.x;
                 z1.y = ev.y - fv.y;
-                Zs[((0 * RP + t1) * RP + s2) * rt + cl] = z0;
-                Zs[((1 * RP + (RP - 1 - t1)) * RP + s2) * rt + cl] = z1;
+                z[(t1 * RP) * rt] = z0;
+                z[(R2 + (RP - 1 - t1) * RP) * rt] = z1;
             }
         }
         __syncthreads();
-        // pass 2: task (a1, t1, col): R_{a1,a2}[t1][t2] for a2 = 0, 1, times D_{a,c}
+        // pass 2: task (a1, t1, col), both inputs of this pass
         if (mine) {
-            const cx* zr = Zs + ((ma1 * RP + mt1) * RP) * rt + mcl;
-            cx xe[HR], xo[HQ > 0 ? HQ : 1];
+#pragma unroll 1
+            for (int ch = 0; ch < 2; ++ch) {
+                const int c = c0 + ch;
+                const cx* zr = Zs + ((ch * 2 + ma1) * R2 + mt1 * RP) * rt + mcl;
+                cx xe[HR], xo[HQ > 0 ? HQ : 1];
 #pragma unroll
-            for (int s2 = 0; s2 < HQ; ++s2) {
-                const cx lo = zr[s2 * rt], hi = zr[(RP - 1 - s2) * rt];
-                xe[s2].x = lo.x + hi.x;
-                xe[s2].y = lo.y + hi.y;
-                xo[s2].x = lo.x - hi.x;
-                xo[s2].y = lo.y - hi.y;
-            }
-            if (RP & 1) xe[HQ] = zr[HQ * rt];
-            const cx* d0 = Ds + ((2 * ma1 + 0) * 4 + c) * R2 + mt1 * RP;
-            const cx* d1 = Ds + ((2 * ma1 + 1) * 4 + c) * R2 + mt1 * RP;
-#pragma unroll
-            for (int t2 = 0; t2 < RP; ++t2) {
-                cx ev = zc<cx>(), fv = zc<cx>();
-#pragma unroll
-                for (int s = 0; s < HR; ++s) {
-                    ev.x += W.E[t2][s] * xe[s].x;
-                    ev.y += W.E[t2][s] * xe[s].y;
+                for (int s2 = 0; s2 < HQ; ++s2) {
+                    const cx lo = zr[s2 * rt], hi = zr[(RP - 1 - s2) * rt];
+                    xe[s2].x = lo.x + hi.x;
+                    xe[s2].y = lo.y + hi.y;
+                    xo[s2].x = lo.x - hi.x;
+                    xo[s2].y = lo.y - hi.y;
                 }
+                if (RP & 1) xe[HQ] = zr[HQ * rt];
+                const cx* d0 = Ds + ((2 * ma1 + 0) * 4 + c) * R2 + mt1 * RP;
+                const cx* d1 = Ds + ((2 * ma1 + 1) * 4 + c) * R2 + mt1 * RP;
 #pragma unroll
-                for (int s = 0; s < HQ; ++s) {
-                    fv.x += W.F[t2][s] * xo[s].x;
-                    fv.y += W.F[t2][s] * xo[s].y;
+                for (int t2 = 0; t2 < RP; ++t2) {
+                    cx ev = zc<cx>(), fv = zc<cx>();
+#pragma unroll
+                    for (int sidx = 0; sidx < HR; ++sidx) {
+                        ev.x += W.E[t2][sidx] * xe[sidx].x;
+                        ev.y += W.E[t2][sidx] * xe[sidx].y;
+                    }
+#pragma unroll
+                    for (int sidx = 0; sidx < HQ; ++sidx) {
+                        fv.x += W.F[t2][sidx] * xo[sidx].x;
+                        fv.y += W.F[t2][sidx] * xo[sidx].y;
+                    }
+                    cx z0, z1;
+                    z0.x = ev.x + fv.x;
+                    z0.y = ev.y + fv.y;
+                    z1.x = ev.x - fv.x;
+                    z1.y = ev.y - fv.y;
+                    addc(acc[0][t2], mulc(d0[t2], z0));
+                    addc(acc[1][RP - 1 - t2], mulc(d1[RP - 1 - t2], z1));
                 }
-                cx z0, z1;
-                z0.x = ev.x + fv.x;
-                z0.y = ev.y + fv.y;
-                z1.x = ev.x - fv.x;
-                z1.y = ev.y - fv.y;
-                addc(acc[0][t2], mulc(d0[t2], z0));
-                addc(acc[1][RP - 1 - t2], mulc(d1[RP - 1 - t2], z1));
             }
         }
     }
-    if (mine && mcl < ncol) {
+    if (mine && mcl < T.ncol) {
 #pragma unroll
         for (int a2 = 0; a2 < 2; ++a2) {
-            const int64_t Aa = child2(l - 1, ip, 2 * ma1 + a2);
-            cx* od = outb + ((Aa * nj + j) * R2 + mt1 * RP) * A.nc + col0 + mcl;
+            const int64_t Aa = child2s(l - 1, T.ip, 2 * ma1 + a2);
+            cx* od = T.outb + ((Aa * T.nj + T.j) * R2 + mt1 * RP) * A.nc + mcl;
 #pragma unroll
             for (int t2 = 0; t2 < RP; ++t2) od[(int64_t)t2 * A.nc] = acc[a2][t2];
         }
@@ -616,12 +641,11 @@ static int apply_2d_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStrea
                 (const cx*)P->KC, g, u, P->n, P->center, nc, rtc);
         }
         prof_mark(p, st, IBF_K_2D);
-        // rhs tile: at most 32 columns, 2 r rt G-level tasks within one CTA,
-        // at most ~200 KB of shared memory
-        int rt2 = std::min(nc, 32);
-        while (rt2 > 1 && 2 * RP * rt2 > k2g_threads<Real>()) rt2 /= 2;
-        while (rt2 > 1 && (6 * (size_t)R2 * rt2 + 16 * R2) * sizeof(cx) > 200 * 1024) rt2 /= 2;
-        const int gthreads = (2 * RP * rt2 + 31) / 32 * 32;
+        // level kernels: rhs tile a power of two, 16 columns (8 in FP64)
+        int rt2 = 1, lrt2 = 0;
+        while (rt2 < (sizeof(Real) == 8 ? 8 : 16) && rt2 < nc) rt2 *= 2, ++lrt2;   // lthreads <= the bound
+        const int lthreads = (2 * RP * rt2 + 31) / 32 * 32;
+        const size_t smem_l = (8 * (size_t)R2 * rt2 + 16 * R2) * sizeof(cx);
         // switch and term: rhs tile a power of two up to 32 (it divides 256)
         int rts = 1;
         while (rts < 32 && rts < nc) rts *= 2;
@@ -653,9 +677,11 @@ static int apply_2d_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStrea
             const int64_t blocks2 = 12 * (mm / 4) * ((nc + rt2 - 1) / rt2);
             for (int l = 1; l <= R.Lq; ++l) {
                 if (l <= R.hq)
-                    k2_level_h<Real, RP><<<(unsigned)blocks2, 256, smem_h, st>>>(W, A, l, (const cx*)R.D[l], a, b, rt2);
+                    k2_level_h<Real, RP><<<(unsigned)blocks2, lthreads, smem_l, st>>>(W, A, l, (const cx*)R.D[l], a, b,
+                                                                                       rt2, lrt2);
                 else
-                    k2_level_g<Real, RP><<<(unsigned)blocks2, gthreads, smem_g, st>>>(W, A, l, (const cx*)R.D[l], a, b, rt2);
+                    k2_level_g<Real, RP><<<(unsigned)blocks2, lthreads, smem_l, st>>>(W, A, l, (const cx*)R.D[l], a, b,
+                                                                                       rt2, lrt2);
                 prof_mark(p, st, IBF_K_2D);
                 std::swap(a, b);
                 if (l == R.hq) {
