@@ -53,12 +53,6 @@ struct RingArgs {
     int n, m, Lq, hq, nc;
 };
 
-__device__ __forceinline__ int64_t child2(int l, int64_t i, int c)
-{
-    const int64_t n = 1LL << l;
-    return (2 * (i / n) + (c >> 1)) * (2 * n) + 2 * (i % n) + (c & 1);
-}
-
 // u[pt + N col] = sum_k KC[pt][k] g[idx(k) + N col]  (the direct centre sum)
 // CTA = (128 points, rhs tile): the centre entries of g for the tile are
 // staged once, KC rows stream through shared memory in chunks of 32; thread
@@ -115,23 +109,6 @@ __global__ void __launch_bounds__(256) k2_center(const typename C2D<Real>::T* __
     }
 }
 
-// Lambda^0[box][j][t][col] = V'[box][j][t] g(q_box + j)
-template <typename Real>
-__global__ void k2_init(const RingArgs A, int r2, const typename C2D<Real>::T* V, const typename C2D<Real>::T* g,
-                        typename C2D<Real>::T* lam)
-{
-    const int64_t mm = (int64_t)A.m * A.m, N = (int64_t)A.n * A.n;
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= 12 * mm * r2 * A.nc) return;
-    const int col = (int)(e % A.nc);
-    const int t = (int)((e / A.nc) % r2);
-    const int64_t j = (e / ((int64_t)A.nc * r2)) % mm;
-    const int b = (int)(e / ((int64_t)A.nc * r2 * mm));
-    const int64_t a1 = (int64_t)(A.q1[b] + 0.5 * A.n) + (j >> A.Lq);
-    const int64_t a2 = (int64_t)(A.q2[b] + 0.5 * A.n) + (j & (A.m - 1));
-    lam[e] = mulc(V[b * A.v_stride + j * r2 + t], g[a1 * A.n + a2 + N * col]);
-}
-
 // One 2D butterfly level l for all 12 boxes.  CTA = (box, unit, rhs tile),
 // unit = (X parent ip at level l-1, Omega box j at level Lq-l); inputs
 // (ip, child c of j), outputs (child a of ip, j), a, c = 2 c1 + c2.
@@ -155,6 +132,18 @@ __device__ __forceinline__ int64_t child2s(int l, int64_t i, int c)
     return ((2 * (i >> l) + (c >> 1)) << (l + 1)) + 2 * (i & ((1LL << l) - 1)) + (c & 1);
 }
 
+// Asynchronous 8- or 16-byte global -> shared copy; !valid writes zeros.
+__device__ __forceinline__ void cp_async_cx(float2* dst, const float2* src, bool valid)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_cx(double2* dst, const double2* src, bool valid)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
+
 // Shared prologue of both level kernels: the CTA's unit and rhs tile, its
 // four input blocks X[c][s][col] and all sixteen diagonals D[a][c][s].
 template <typename Real, int RP>
@@ -164,8 +153,10 @@ struct LevelTile {
     int64_t ip, j, nj;
     int col0, ncol;
     cx* outb;
+    // With g0 != nullptr (level 1) the inputs are Lambda^0 = V' g formed here
+    // from the box's V table and g, instead of read from the workspace.
     __device__ void stage(const RingArgs& A, int l, const cx* D, const cx* in, cx* out, int rt, int lrt, cx* X,
-                          cx* Ds)
+                          cx* Ds, const cx* g0 = nullptr, const cx* V0 = nullptr)
     {
         const int ntile = (A.nc + rt - 1) >> lrt;
         const int64_t units = (int64_t)A.m * A.m / 4;
@@ -183,15 +174,45 @@ struct LevelTile {
         outb = out + (size_t)b * mm * R2 * A.nc + col0;
         const cx* Db = D + (size_t)b * A.d_stride;
         const int cl = threadIdx.x & (rt - 1), srow = threadIdx.x >> lrt, sstep = blockDim.x >> lrt;
+        // asynchronous copies: every load of the tile is in flight at once;
+        // columns past the tile's end are zero-filled (source size 0)
+        cx* Vs = Ds + 16 * R2;   // level 1 only: [4 c][R2] V rows, [4 c][rt] g values
+        cx* Gs = Vs + 4 * R2;
+        if (g0) {
+            const int64_t N = (int64_t)A.n * A.n;
+            const int64_t o1 = (int64_t)(A.q1[b] + 0.5 * A.n), o2 = (int64_t)(A.q2[b] + 0.5 * A.n);
+            for (int e = threadIdx.x; e < 4 * R2; e += blockDim.x) {
+                const int c = e / R2, sidx = e - c * R2;
+                cp_async_cx(Vs + e, V0 + b * A.v_stride + child2s(A.Lq - 1, j, c) * R2 + sidx, true);
+            }
+            for (int e = threadIdx.x; e < 4 * rt; e += blockDim.x) {
+                const int c = e >> lrt, k = e & (rt - 1);
+                const int64_t leaf = child2s(A.Lq - 1, j, c);
+                const cx* gp = g0 + (o1 + (leaf >> A.Lq)) * A.n + o2 + (leaf & (A.m - 1)) + N * col0;
+                cp_async_cx(Gs + e, k < ncol ? gp + N * k : gp, k < ncol);
+            }
+        } else {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const cx* src = inb + (ip * nC + child2s(A.Lq - l, j, c)) * R2 * A.nc;
-            for (int sidx = srow; sidx < R2; sidx += sstep)
-                X[(c * R2 + sidx) * rt + cl] = cl < ncol ? src[(int64_t)sidx * A.nc + cl] : zc<cx>();
+            for (int c = 0; c < 4; ++c) {
+                const cx* src = inb + (ip * nC + child2s(A.Lq - l, j, c)) * R2 * A.nc;
+                for (int sidx = srow; sidx < R2; sidx += sstep)
+                    cp_async_cx(X + (c * R2 + sidx) * rt + cl, cl < ncol ? src + (int64_t)sidx * A.nc + cl : src,
+                                cl < ncol);
+            }
         }
         for (int e = threadIdx.x; e < 16 * R2; e += blockDim.x) {
             const int ac = e / R2, sidx = e - ac * R2;
-            Ds[e] = Db[(child2s(l - 1, ip, ac >> 2) * nC + child2s(A.Lq - l, j, ac & 3)) * R2 + sidx];
+            cp_async_cx(Ds + e, Db + (child2s(l - 1, ip, ac >> 2) * nC + child2s(A.Lq - l, j, ac & 3)) * R2 + sidx,
+                        true);
+        }
+        asm volatile("cp.async.commit_group;\n" ::);
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        if (g0) {
+            __syncthreads();
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                for (int sidx = srow; sidx < R2; sidx += sstep)
+                    X[(c * R2 + sidx) * rt + cl] = mulc(Vs[c * R2 + sidx], Gs[c * rt + cl]);
         }
     }
 };
@@ -210,16 +231,17 @@ template <typename Real, int RP>
 __global__ void __launch_bounds__(k2_level_threads<Real, RP>(), k2_level_blocks<Real, RP>())
     k2_level_h(const __grid_constant__ EO2<Real, RP> W, const RingArgs A, int l,
                const typename C2D<Real>::T* __restrict__ D, const typename C2D<Real>::T* __restrict__ in,
-               typename C2D<Real>::T* __restrict__ out, int rt, int lrt)
+               typename C2D<Real>::T* __restrict__ out, int rt, int lrt, const typename C2D<Real>::T* __restrict__ g0,
+               const typename C2D<Real>::T* __restrict__ V0)
 {
     typedef typename C2D<Real>::T cx;
     constexpr int R2 = RP * RP, HR = EO2<Real, RP>::HR, HQ = EO2<Real, RP>::HQ;
     extern __shared__ __align__(16) unsigned char sraw[];
     cx* X = reinterpret_cast<cx*>(sraw);            // [4 c][R2][rt]
     cx* Ws = X + 4 * R2 * rt;                         // [2 a][2 c1][RP s1][RP t2][rt]
-    cx* Ds = Ws + 4 * R2 * rt;                        // [4 a][4 c][R2]
+    cx* Ds = Ws + 4 * R2 * rt;                        // [4 a][4 c][R2] (+ level-1 V rows and g)
     LevelTile<Real, RP> T;
-    T.stage(A, l, D, in, out, rt, lrt, X, Ds);
+    T.stage(A, l, D, in, out, rt, lrt, X, Ds, g0, V0);
     const int msk = rt - 1;
     for (int a0 = 0; a0 < 4; a0 += 2) {
         __syncthreads();
@@ -435,67 +457,78 @@ __global__ void __launch_bounds__(k2_level_threads<Real, RP>(), k2_level_blocks<
 }
 
 // Switch at level hq: out[p][t] = sum_s M[p][t][s] in[p][s].  CTA = (box,
-// pair p, rhs tile): M[p] (r^2 x r^2) and the pair's input tile are staged in
-// shared memory; thread (col, t group) keeps the outputs t = tg, tg + TG, ...
-// in registers, so every M entry read from HBM serves the whole tile.
+// pair p, 32-column tile): M[p] (r^2 x r^2) and the pair's input tile are
+// staged by asynchronous copies; thread (column group cg, row group tg)
+// keeps outputs t = tg + 16k for the columns cg + 8q (q < 4) in registers,
+// so one shared load of M serves four columns and one of x four rows.
 template <typename Real, int RP>
-__global__ void __launch_bounds__(256) k2_switch(const RingArgs A, const typename C2D<Real>::T* __restrict__ M,
+__global__ void __launch_bounds__(128) k2_switch(const RingArgs A, const typename C2D<Real>::T* __restrict__ M,
                                                  const typename C2D<Real>::T* __restrict__ in,
-                                                 typename C2D<Real>::T* __restrict__ out, int rt)
+                                                 typename C2D<Real>::T* __restrict__ out)
 {
     typedef typename C2D<Real>::T cx;
-    constexpr int R2 = RP * RP, KMAX = (R2 + 7) / 8;
+    constexpr int R2 = RP * RP, CW = 32, TG = 16, KT = (R2 + TG - 1) / TG;
     extern __shared__ __align__(16) unsigned char sraw[];
     cx* Ms = reinterpret_cast<cx*>(sraw);   // [R2][R2]
-    cx* Xs = Ms + R2 * R2;                    // [R2][rt]
-    const int ntile = (A.nc + rt - 1) / rt;
+    cx* Xs = Ms + R2 * R2;                    // [R2][CW]
+    const int ntile = (A.nc + CW - 1) / CW;
     const int64_t mm = (int64_t)A.m * A.m;
     const int tile = (int)(blockIdx.x % ntile);
     const int64_t bp = blockIdx.x / ntile;    // b * mm + p
     const int b = (int)(bp / mm);
     const int64_t p = bp % mm;
-    const int col0 = tile * rt, ncol = min(rt, A.nc - col0);
+    const int col0 = tile * CW, ncol = min(CW, A.nc - col0);
     const cx* Mr = M + b * A.m_stride + p * R2 * R2;
-    for (int e = threadIdx.x; e < R2 * R2; e += blockDim.x) Ms[e] = Mr[e];
+    for (int e = threadIdx.x; e < R2 * R2; e += blockDim.x) cp_async_cx(Ms + e, Mr + e, true);
     const cx* xin = in + (size_t)bp * R2 * A.nc + col0;
-    for (int e = threadIdx.x; e < R2 * rt; e += blockDim.x) {
-        const int sidx = e / rt, cl = e % rt;
-        Xs[e] = cl < ncol ? xin[(int64_t)sidx * A.nc + cl] : zc<cx>();
+    for (int e = threadIdx.x; e < R2 * CW; e += blockDim.x) {
+        const int sidx = e >> 5, cl = e & 31;
+        cp_async_cx(Xs + e, cl < ncol ? xin + (int64_t)sidx * A.nc + cl : xin, cl < ncol);
     }
+    asm volatile("cp.async.commit_group;\n" ::);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
-    const int TG = blockDim.x / rt;           // rt divides the block
-    const int cl = threadIdx.x % rt, tg = threadIdx.x / rt;
-    cx acc[KMAX];
+    const int cg = threadIdx.x & 7, tg = threadIdx.x >> 3;
+    cx acc[KT][4];
 #pragma unroll
-    for (int k = 0; k < KMAX; ++k) acc[k] = zc<cx>();
-#pragma unroll 4
+    for (int k = 0; k < KT; ++k)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[k][q] = zc<cx>();
+#pragma unroll 7
     for (int sidx = 0; sidx < R2; ++sidx) {
-        const cx x = Xs[sidx * rt + cl];
+        cx x[4];
 #pragma unroll
-        for (int k = 0; k < KMAX; ++k) {
+        for (int q = 0; q < 4; ++q) x[q] = Xs[sidx * CW + cg + 8 * q];
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
             const int t = tg + k * TG;
             if (t < R2) {
                 const cx m = Ms[t * R2 + sidx];
-                acc[k].x += m.x * x.x - m.y * x.y;
-                acc[k].y += m.x * x.y + m.y * x.x;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    acc[k][q].x += m.x * x[q].x - m.y * x[q].y;
+                    acc[k][q].y += m.x * x[q].y + m.y * x[q].x;
+                }
             }
         }
     }
-    if (cl < ncol) {
-        cx* o = out + (size_t)bp * R2 * A.nc + col0 + cl;
+    cx* o = out + (size_t)bp * R2 * A.nc + col0;
 #pragma unroll
-        for (int k = 0; k < KMAX; ++k) {
-            const int t = tg + k * TG;
-            if (t < R2) o[(int64_t)t * A.nc] = acc[k];
-        }
+    for (int k = 0; k < KT; ++k) {
+        const int t = tg + k * TG;
+        if (t < R2)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (cg + 8 * q < ncol) o[(int64_t)t * A.nc + cg + 8 * q] = acc[k][q];
     }
 }
 
 // u[pt + N col] += sum over the ring's boxes of
 //   uph[box][pt] sum_{t1,t2} lw[o1][t1] lw[o2][t2] Lambda^L[box][leaf(pt)][t][col]
-// CTA = (leaf, PB x PB block of its points, rhs tile).  Per box the leaf's
-// tile is staged, the o2 interpolation is applied once per (o2, t1, col)
-// and reused by every row o1 of the block (separable Lagrange weights).
+// CTA = (leaf, PB x PB block of its points, rhs tile).  The twelve boxes'
+// leaf tiles stream through a double buffer of asynchronous copies; per box
+// the o2 interpolation is applied once per (o2, t1, col) and reused by every
+// row o1 of the block (separable Lagrange weights).
 template <typename Real, int RP, int PB>
 __global__ void __launch_bounds__(256) k2_term(const RingArgs A, const typename C2D<Real>::T* __restrict__ uph,
                                                const Real* __restrict__ lw,
@@ -505,12 +538,12 @@ __global__ void __launch_bounds__(256) k2_term(const RingArgs A, const typename 
     typedef typename C2D<Real>::T cx;
     constexpr int R2 = RP * RP, PAD = 16 / PB, KMAX = PB * PB * 32 / 256;
     extern __shared__ __align__(16) unsigned char sraw[];
-    cx* Ls = reinterpret_cast<cx*>(sraw);      // [R2][rt]
+    cx* Ls = reinterpret_cast<cx*>(sraw);      // [2][R2][rt]
     const int SS = RP * rt + PAD;                // stride of one o2 in Ss
-    cx* Ss = Ls + R2 * rt;                       // [PB][RP][rt] (+ pad per o2)
-    cx* Us = Ss + PB * SS;                       // [PB * PB] uph of the block
-    Real* W1 = reinterpret_cast<Real*>(Us + PB * PB);   // [PB][RP]
-    Real* W2 = W1 + PB * RP;                            // [PB][RP]
+    cx* Ss = Ls + 2 * R2 * rt;                   // [PB][RP][rt] (+ pad per o2)
+    cx* Us = Ss + PB * SS;                       // [2][PB * PB] uph of the block
+    Real* W1 = reinterpret_cast<Real*>(Us + 2 * PB * PB);   // [PB][RP]
+    Real* W2 = W1 + PB * RP;                                // [PB][RP]
     const int64_t N = (int64_t)A.n * A.n, mm = (int64_t)A.m * A.m;
     const int K = A.n / A.m, nb1 = K / PB;
     const int ntile = (A.nc + rt - 1) / rt;
@@ -525,23 +558,35 @@ __global__ void __launch_bounds__(256) k2_term(const RingArgs A, const typename 
         W1[e] = lw[(o1b + e / RP) * RP + e % RP];
         W2[e] = lw[(o2b + e / RP) * RP + e % RP];
     }
+    auto issue = [&](int b) {
+        const cx* lb = lam + ((size_t)(b * mm + leaf) * R2) * A.nc + col0;
+        cx* ld = Ls + (b & 1) * R2 * rt;
+        for (int e = threadIdx.x; e < R2 * rt; e += blockDim.x) {
+            const int t = e / rt, cl = e % rt;
+            cp_async_cx(ld + e, cl < ncol ? lb + (int64_t)t * A.nc + cl : lb, cl < ncol);
+        }
+        for (int e = threadIdx.x; e < PB * PB; e += blockDim.x)
+            cp_async_cx(Us + (b & 1) * PB * PB + e, uph + b * N + (n1b + e / PB) * A.n + n2b + e % PB, true);
+        asm volatile("cp.async.commit_group;\n" ::);
+    };
     cx acc[KMAX];
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) acc[k] = zc<cx>();
+    issue(0);
     for (int b = 0; b < 12; ++b) {
-        __syncthreads();
-        const cx* lb = lam + ((size_t)(b * mm + leaf) * R2) * A.nc + col0;
-        for (int e = threadIdx.x; e < R2 * rt; e += blockDim.x) {
-            const int t = e / rt, cl = e % rt;
-            Ls[e] = cl < ncol ? lb[(int64_t)t * A.nc + cl] : zc<cx>();
+        if (b + 1 < 12) {
+            issue(b + 1);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         }
-        for (int e = threadIdx.x; e < PB * PB; e += blockDim.x)
-            Us[e] = uph[b * N + (n1b + e / PB) * A.n + n2b + e % PB];
         __syncthreads();
+        const cx* Lb = Ls + (b & 1) * R2 * rt;
+        const cx* Ub = Us + (b & 1) * PB * PB;
         // S[o2][t1][col] = sum_t2 w2[o2][t2] Lambda[t1 RP + t2][col]
         for (int e = threadIdx.x; e < PB * RP * rt; e += blockDim.x) {
             const int cl = e % rt, t1 = (e / rt) % RP, o2 = e / (rt * RP);
-            const cx* lr = Ls + t1 * RP * rt + cl;
+            const cx* lr = Lb + t1 * RP * rt + cl;
             cx sv = zc<cx>();
 #pragma unroll
             for (int t2 = 0; t2 < RP; ++t2) {
@@ -568,9 +613,10 @@ __global__ void __launch_bounds__(256) k2_term(const RingArgs A, const typename 
                     v.x += w * x.x;
                     v.y += w * x.y;
                 }
-                addc(acc[k], mulc(Us[o1 * PB + o2], v));
+                addc(acc[k], mulc(Ub[o1 * PB + o2], v));
             }
         }
+        __syncthreads();   // buffers of box b and Ss are free again
     }
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
@@ -586,8 +632,6 @@ __global__ void __launch_bounds__(256) k2_term(const RingArgs A, const typename 
         }
     }
 }
-
-static inline unsigned nb(int64_t n) { return (unsigned)((n + 255) / 256); }
 
 template <typename Real, int RP>
 static int apply_2d_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStream_t st)
@@ -645,14 +689,14 @@ static int apply_2d_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStrea
         int rt2 = 1, lrt2 = 0;
         while (rt2 < (sizeof(Real) == 8 ? 8 : 16) && rt2 < nc) rt2 *= 2, ++lrt2;   // lthreads <= the bound
         const int lthreads = (2 * RP * rt2 + 31) / 32 * 32;
-        const size_t smem_l = (8 * (size_t)R2 * rt2 + 16 * R2) * sizeof(cx);
+        const size_t smem_l = (8 * (size_t)R2 * rt2 + 20 * R2 + 4 * rt2) * sizeof(cx);
         // switch and term: rhs tile a power of two up to 32 (it divides 256)
         int rts = 1;
         while (rts < 32 && rts < nc) rts *= 2;
         const int ntile_s = (nc + rts - 1) / rts;
-        const size_t smem_s = ((size_t)R2 * R2 + (size_t)R2 * rts) * sizeof(cx);
+        const size_t smem_s = ((size_t)R2 * R2 + (size_t)R2 * 32) * sizeof(cx);
         auto term_smem = [&](int pbs) {
-            return ((size_t)R2 * rts + (size_t)pbs * (RP * rts + 16 / pbs) + pbs * pbs) * sizeof(cx) +
+            return (2 * (size_t)R2 * rts + (size_t)pbs * (RP * rts + 16 / pbs) + 2 * pbs * pbs) * sizeof(cx) +
                    2 * (size_t)pbs * RP * sizeof(Real);
         };
         const size_t smem_h = (6 * (size_t)R2 * rt2 + 4 * R2) * sizeof(cx);
@@ -672,21 +716,19 @@ static int apply_2d_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStrea
             const int64_t mm = (int64_t)R.m * R.m;
             cx* a = (cx*)P->ws[0];
             cx* b = (cx*)P->ws[1];
-            k2_init<Real><<<nb(12 * mm * R2 * nc), 256, 0, st>>>(A, R2, (const cx*)R.V, g, a);
-            prof_mark(p, st, IBF_K_2D);
             const int64_t blocks2 = 12 * (mm / 4) * ((nc + rt2 - 1) / rt2);
             for (int l = 1; l <= R.Lq; ++l) {
                 if (l <= R.hq)
-                    k2_level_h<Real, RP><<<(unsigned)blocks2, lthreads, smem_l, st>>>(W, A, l, (const cx*)R.D[l], a, b,
-                                                                                       rt2, lrt2);
+                    k2_level_h<Real, RP><<<(unsigned)blocks2, lthreads, smem_l, st>>>(
+                        W, A, l, (const cx*)R.D[l], a, b, rt2, lrt2, l == 1 ? g : nullptr, (const cx*)R.V);
                 else
                     k2_level_g<Real, RP><<<(unsigned)blocks2, lthreads, smem_l, st>>>(W, A, l, (const cx*)R.D[l], a, b,
                                                                                        rt2, lrt2);
                 prof_mark(p, st, IBF_K_2D);
                 std::swap(a, b);
                 if (l == R.hq) {
-                    k2_switch<Real, RP><<<(unsigned)(12 * mm * ntile_s), 256, smem_s, st>>>(A, (const cx*)R.M, a, b,
-                                                                                            rts);
+                    k2_switch<Real, RP><<<(unsigned)(12 * mm * ((nc + 31) / 32)), 128, smem_s, st>>>(
+                        A, (const cx*)R.M, a, b);
                     prof_mark(p, st, IBF_K_2D);
                     std::swap(a, b);
                 }
@@ -719,7 +761,7 @@ int launches_2d(const ibf_plan* p)
 {
     const Plan2D* P = (const Plan2D*)p->p2d;
     int n = 1;
-    for (const Ring2D& R : P->rings) n += R.Lq + 3;
+    for (const Ring2D& R : P->rings) n += R.Lq + 2;
     return n;
 }
 
