@@ -118,9 +118,9 @@ template <typename Real, int RP>
 static int persist_launch(const ibf_batch* b, cudaStream_t st)
 {
     static bool attr = false;
-    static int grid = 0;
+    static int nsm = 0;
     if (!attr) {
-        int dev = 0, optin = 0, nsm = 0;
+        int dev = 0, optin = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -133,13 +133,17 @@ static int persist_launch(const ibf_batch* b, cudaStream_t st)
         cudaFuncGetAttributes(&fa, k_fused_persist<Real, RP, true>);
         cudaFuncSetAttribute(k_fused_persist<Real, RP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              optin - (int)fa.sharedSizeBytes);
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_persist<Real, RP, false>,
-                                                      FusedTraits<Real>::kThreads, 100 * 1024);
-        grid = nsm * std::max(1, per_sm);
         attr = true;
-        cudaGetLastError();   // the occupancy query is advisory
     }
+    // every CTA must be resident at once (items wait on other CTAs' items)
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_persist<Real, RP, false>,
+                                                      PersistTraits<Real>::kThreads, b->p_smem) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        return set_error(IBF_ERR_CUDA, "persistent batch: the CTA shape does not fit an SM");
+    }
+    const int grid = nsm * per_sm;
     PersistArgs A;
     A.descs = b->p_descs;
     A.start = b->p_start;
@@ -156,9 +160,9 @@ static int persist_launch(const ibf_batch* b, cudaStream_t st)
     cudaMemsetAsync(b->p_status, 0, sizeof(int), st);
     const unsigned g = (unsigned)std::min<int64_t>(grid, b->p_total);
     if (b->adjoint)
-        k_fused_persist<Real, RP, true><<<g, FusedTraits<Real>::kThreads, b->p_smem, st>>>(A);
+        k_fused_persist<Real, RP, true><<<g, PersistTraits<Real>::kThreads, b->p_smem, st>>>(A);
     else
-        k_fused_persist<Real, RP, false><<<g, FusedTraits<Real>::kThreads, b->p_smem, st>>>(A);
+        k_fused_persist<Real, RP, false><<<g, PersistTraits<Real>::kThreads, b->p_smem, st>>>(A);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? IBF_OK : cuda_error(e, "persistent batch launch");
 }
@@ -319,13 +323,15 @@ extern "C" int ibf_batch_create(ibf_plan* const* plans, int count, const int* nr
         std::vector<int64_t> last_blocks(count, 0);
         int64_t total = 0;
         size_t smem = 0;
-        // one CTA shape for the whole launch: 32-column tiles and the fusion
-        // depth that fits them
+        // one CTA shape for the whole launch: 32-column tiles and a fusion
+        // depth whose butterfly steps fill the CTA (2^(k-1) x 32 <= threads)
         std::vector<std::vector<Chunk>> psched(count);
         int pphase = 0;
+        const int kcta = 4;   // 2^(4-1) x 32 = 256 threads, the persistent CTA
         for (int b = 0; b < count; ++b) {
             const ibf_plan* p = plans[b];
-            const int kmax = p->user_kfuse ? std::min(p->kfuse, fused_kmax(32, p->r, esz)) : fused_kmax(32, p->r, esz);
+            const int kfit = std::min(kcta, fused_kmax(32, p->r, esz));
+            const int kmax = p->user_kfuse ? std::min(p->kfuse, kfit) : kfit;
             psched[b] = fused_schedule(p->L, p->h, std::max(1, kmax));
             pphase = std::max(pphase, (int)psched[b].size());
         }
