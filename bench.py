@@ -42,14 +42,14 @@ FP32_LANES_PER_SM = 128
 # this benchmark at N = 2^20, r = 9, nrhs = 64, 4 levels per launch, tile 32
 # (profiles/k_fused_f32_fio1d_n2e20_nrhs64.md).  Keyed by the launch's level
 # range; valid only while the kernel sources hash to KERNEL_SRC_SHA.
-KERNEL_SRC_SHA = "58f3ab0e6f78eb5e"
+KERNEL_SRC_SHA = "4331e57baf5851a0"
 TRAFFIC_N20_R9_NRHS64_K4 = {
-    (0, 4, "H"): 1216650752 + 4772077824,
-    (4, 7, "H"): 5284976640 + 4779201280,
-    (7, 10, "H"): 5964457728 + 4783379200,
-    (10, 14, "G"): 5436062720 + 4780604160,
-    (14, 17, "G"): 5285076992 + 4780598528,
-    (17, 20, "G"): 5368861696 + 527849984,
+    (0, 4, "H"): 1218297344 + 4771960320,
+    (4, 7, "H"): 5285875968 + 4778969856,
+    (7, 10, "H"): 5964549888 + 4783535104,
+    (10, 14, "G"): 5436256000 + 4780984320,
+    (14, 17, "G"): 5284909312 + 4780577536,
+    (17, 20, "G"): 5368868352 + 527558400,
 }
 
 
@@ -536,11 +536,21 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--levels-per-launch", type=int, default=0, help="force the fused depth (skips autotuning)")
     ap.add_argument("--rhs-tile", type=int, default=0, help="force the rhs tile (skips autotuning)")
+    ap.add_argument("--only-2d", type=int, default=0, metavar="n",
+                    help="profiling aid: time only the 2D apply on the n x n grid and print its record")
+    ap.add_argument("--only-batch", action="store_true",
+                    help="profiling aid: time only the 256-transform batch and print its record")
     a = ap.parse_args()
     if a.warmup < 3 and a.impl == "ibf":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if a.impl == "reference":
         return run_reference(a)
+    if a.only_2d or a.only_batch:
+        import torch
+        import paper_1605_03616_gb300 as ibf
+        rec = run_2d(ibf, torch, n=a.only_2d) if a.only_2d else run_batch(ibf, torch)
+        print(json.dumps({"profile_only": "fio2d" if a.only_2d else "batch256", **rec}), flush=True)
+        return 0
     return run_gpu(a)
 
 

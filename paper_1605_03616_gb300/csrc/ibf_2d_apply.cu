@@ -689,7 +689,8 @@ static int apply_2d_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStrea
         int rt2 = 1, lrt2 = 0;
         while (rt2 < (sizeof(Real) == 8 ? 8 : 16) && rt2 < nc) rt2 *= 2, ++lrt2;   // lthreads <= the bound
         const int lthreads = (2 * RP * rt2 + 31) / 32 * 32;
-        const size_t smem_l = (8 * (size_t)R2 * rt2 + 20 * R2 + 4 * rt2) * sizeof(cx);
+        const size_t smem_l = (8 * (size_t)R2 * rt2 + 16 * R2) * sizeof(cx);
+        const size_t smem_l1 = smem_l + (4 * (size_t)R2 + 4 * rt2) * sizeof(cx);   // + V rows and g of level 1
         // switch and term: rhs tile a power of two up to 32 (it divides 256)
         int rts = 1;
         while (rts < 32 && rts < nc) rts *= 2;
@@ -719,7 +720,7 @@ static int apply_2d_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStrea
             const int64_t blocks2 = 12 * (mm / 4) * ((nc + rt2 - 1) / rt2);
             for (int l = 1; l <= R.Lq; ++l) {
                 if (l <= R.hq)
-                    k2_level_h<Real, RP><<<(unsigned)blocks2, lthreads, smem_l, st>>>(
+                    k2_level_h<Real, RP><<<(unsigned)blocks2, lthreads, l == 1 ? smem_l1 : smem_l, st>>>(
                         W, A, l, (const cx*)R.D[l], a, b, rt2, lrt2, l == 1 ? g : nullptr, (const cx*)R.V);
                 else
                     k2_level_g<Real, RP><<<(unsigned)blocks2, lthreads, smem_l, st>>>(W, A, l, (const cx*)R.D[l], a, b,
