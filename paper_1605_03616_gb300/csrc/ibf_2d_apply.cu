@@ -700,8 +700,6 @@ static int apply_2d_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStrea
             return (2 * (size_t)R2 * rts + (size_t)pbs * (RP * rts + 16 / pbs) + 2 * pbs * pbs) * sizeof(cx) +
                    2 * (size_t)pbs * RP * sizeof(Real);
         };
-        const size_t smem_h = (6 * (size_t)R2 * rt2 + 4 * R2) * sizeof(cx);
-        const size_t smem_g = (6 * (size_t)R2 * rt2 + 16 * R2) * sizeof(cx);
         for (const Ring2D& R : P->rings) {
             RingArgs A;
             memcpy(A.q1, R.q1, sizeof(A.q1));
