@@ -80,6 +80,12 @@ struct FusedConsts {
     Real Qm[RP][EO<RP>::HQ > 0 ? EO<RP>::HQ : 1];
     Real E[RP][EO<RP>::HR];
     Real F[RP][EO<RP>::HQ > 0 ? EO<RP>::HQ : 1];
+    // the same weights as (w, w) pairs: one packed two-lane multiply-add
+    // applies a weight to the real and imaginary part at once
+    typename CT<Real>::T Pm2[RP][EO<RP>::HR];
+    typename CT<Real>::T Qm2[RP][EO<RP>::HQ > 0 ? EO<RP>::HQ : 1];
+    typename CT<Real>::T E2[RP][EO<RP>::HR];
+    typename CT<Real>::T F2[RP][EO<RP>::HQ > 0 ? EO<RP>::HQ : 1];
 };
 
 // The weights depend only on r, so every translation unit that launches the
@@ -156,6 +162,20 @@ __device__ __forceinline__ void cacc(C& a, C b)
 {
     a.x += b.x;
     a.y += b.y;
+}
+
+// Two-lane arithmetic on (re, im) pairs: Blackwell's packed FP32 instructions
+// (one issue slot for both lanes) in single precision, per-component double
+// operations otherwise.  Rounding is that of the per-component operations:
+// a - b is b * (-1) + a rounded once, w * x + acc is one fused multiply-add.
+__device__ __forceinline__ float2 p2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p2sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 p2fma(float2 w, float2 x, float2 acc) { return __ffma2_rn(w, x, acc); }
+__device__ __forceinline__ double2 p2add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 p2sub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 p2fma(double2 w, double2 x, double2 acc)
+{
+    return make_double2(fma(w.x, x.x, acc.x), fma(w.y, x.y, acc.y));
 }
 
 // KIND: 0 = H levels (1..h), 1 = G levels (h+1..L).  RT: the rhs tile width
@@ -326,44 +346,29 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
                             const cx y01 = ADJ ? cmulc(d01[RP - 1 - s2], xb) : cmul(d01[RP - 1 - s2], xb);
                             const cx y10 = ADJ ? cmulc(d10[s2], xa) : cmul(d10[s2], xa);
                             const cx y11 = ADJ ? cmulc(d11[RP - 1 - s2], xb) : cmul(d11[RP - 1 - s2], xb);
-                            const Real p0x = y00.x + y01.x, p0y = y00.y + y01.y;
-                            const Real m0x = y00.x - y01.x, m0y = y00.y - y01.y;
-                            const Real p1x = y10.x + y11.x, p1y = y10.y + y11.y;
-                            const Real m1x = y10.x - y11.x, m1y = y10.y - y11.y;
+                            const cx pv0 = p2add(y00, y01), mv0 = p2sub(y00, y01);
+                            const cx pv1 = p2add(y10, y11), mv1 = p2sub(y10, y11);
 #pragma unroll
                             for (int t = 0; t < HR; ++t) {
-                                const Real pm = C.Pm[s2][t];
-                                we0[t].x += pm * p0x;
-                                we0[t].y += pm * p0y;
-                                we1[t].x += pm * p1x;
-                                we1[t].y += pm * p1y;
+                                const cx pm = C.Pm2[s2][t];
+                                we0[t] = p2fma(pm, pv0, we0[t]);
+                                we1[t] = p2fma(pm, pv1, we1[t]);
                             }
 #pragma unroll
                             for (int t = 0; t < HQ; ++t) {
-                                const Real qm = C.Qm[s2][t];
-                                wo0[t].x += qm * m0x;
-                                wo0[t].y += qm * m0y;
-                                wo1[t].x += qm * m1x;
-                                wo1[t].y += qm * m1y;
+                                const cx qm = C.Qm2[s2][t];
+                                wo0[t] = p2fma(qm, mv0, wo0[t]);
+                                wo1[t] = p2fma(qm, mv1, wo1[t]);
                             }
                         }
                         cx* o0 = sm + (size_t)p0 * PS + c;
                         cx* o1 = sm + (size_t)p1 * PS + c;
 #pragma unroll
                         for (int t = 0; t < HQ; ++t) {
-                            cx a, b;
-                            a.x = we0[t].x + wo0[t].x;
-                            a.y = we0[t].y + wo0[t].y;
-                            b.x = we0[t].x - wo0[t].x;
-                            b.y = we0[t].y - wo0[t].y;
-                            o0[t * rt] = a;
-                            o0[(RP - 1 - t) * rt] = b;
-                            a.x = we1[t].x + wo1[t].x;
-                            a.y = we1[t].y + wo1[t].y;
-                            b.x = we1[t].x - wo1[t].x;
-                            b.y = we1[t].y - wo1[t].y;
-                            o1[t * rt] = a;
-                            o1[(RP - 1 - t) * rt] = b;
+                            o0[t * rt] = p2add(we0[t], wo0[t]);
+                            o0[(RP - 1 - t) * rt] = p2sub(we0[t], wo0[t]);
+                            o1[t * rt] = p2add(we1[t], wo1[t]);
+                            o1[(RP - 1 - t) * rt] = p2sub(we1[t], wo1[t]);
                         }
                         if (ODD) {
                             o0[HQ * rt] = we0[HQ];
@@ -386,10 +391,8 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
 #pragma unroll
                             for (int s2 = 0; s2 < HQ; ++s2) {
                                 const cx lo = xp[s2 * rt], hi = xp[(RP - 1 - s2) * rt];
-                                xe[q][s2].x = lo.x + hi.x;
-                                xe[q][s2].y = lo.y + hi.y;
-                                xo[q][s2].x = lo.x - hi.x;
-                                xo[q][s2].y = lo.y - hi.y;
+                                xe[q][s2] = p2add(lo, hi);
+                                xo[q][s2] = p2sub(lo, hi);
                             }
                             if (ODD) xe[q][HQ] = xp[HQ * rt];
                         }
@@ -402,20 +405,11 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
                             for (int q = 0; q < 2; ++q) {
                                 cx e = cz<cx>(), f = cz<cx>();
 #pragma unroll
-                                for (int s2 = 0; s2 < HR; ++s2) {
-                                    e.x += C.E[t][s2] * xe[q][s2].x;
-                                    e.y += C.E[t][s2] * xe[q][s2].y;
-                                }
+                                for (int s2 = 0; s2 < HR; ++s2) e = p2fma(C.E2[t][s2], xe[q][s2], e);
 #pragma unroll
-                                for (int s2 = 0; s2 < HQ; ++s2) {
-                                    f.x += C.F[t][s2] * xo[q][s2].x;
-                                    f.y += C.F[t][s2] * xo[q][s2].y;
-                                }
-                                cx z0, z1;   // (T_0^T x_q)[t] and (T_1^T x_q)[RP-1-t]
-                                z0.x = e.x + f.x;
-                                z0.y = e.y + f.y;
-                                z1.x = e.x - f.x;
-                                z1.y = e.y - f.y;
+                                for (int s2 = 0; s2 < HQ; ++s2) f = p2fma(C.F2[t][s2], xo[q][s2], f);
+                                // (T_0^T x_q)[t] and (T_1^T x_q)[RP-1-t]
+                                const cx z0 = p2add(e, f), z1 = p2sub(e, f);
                                 // forward G: output a uses D_{a,q}; adjoint H: output c uses conj(D_{q,c})
                                 const cx* dA = du + (ADJ ? (q * 2 + 0) : (0 * 2 + q)) * RP;
                                 const cx* dB = du + (ADJ ? (q * 2 + 1) : (1 * 2 + q)) * RP;
@@ -778,6 +772,16 @@ inline void fill_even_odd(const ibf_plan* p, FusedConsts<Real, RP>& C)
             C.F[t][s] = (Real)((T0[s][t] - T0[RP - 1 - s][t]) / 2);
         }
         if (RP & 1) C.E[t][HQ] = (Real)T0[HQ][t];
+    }
+    for (int s = 0; s < RP; ++s) {
+        for (int t = 0; t < EO<RP>::HR; ++t) {
+            C.Pm2[s][t].x = C.Pm2[s][t].y = C.Pm[s][t];
+            C.E2[s][t].x = C.E2[s][t].y = C.E[s][t];
+        }
+        for (int t = 0; t < HQ; ++t) {
+            C.Qm2[s][t].x = C.Qm2[s][t].y = C.Qm[s][t];
+            C.F2[s][t].x = C.F2[s][t].y = C.F[s][t];
+        }
     }
 }
 
