@@ -163,6 +163,32 @@ __device__ __forceinline__ void cacc(C& a, C b)
     a.x += b.x;
     a.y += b.y;
 }
+// acc += a b and acc += conj(a) b as chains of fused multiply-adds (four
+// instructions instead of a product and a sum)
+template <typename C>
+__device__ __forceinline__ void cmac(C& acc, C a, C b)
+{
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+template <typename C>
+__device__ __forceinline__ void cmacc(C& acc, C a, C b)
+{
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(-a.y, b.x, acc.y);
+}
+template <bool CONJ, typename C>
+__device__ __forceinline__ void cmacx(C& acc, C a, C b)
+{
+    if (CONJ)
+        cmacc(acc, a, b);
+    else
+        cmac(acc, a, b);
+}
 
 // Two-lane arithmetic on (re, im) pairs: Blackwell's packed FP32 instructions
 // (one issue slot for both lanes) in single precision, per-component double
@@ -235,7 +261,7 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
                 for (int32_t n = P.off[leaf]; n < n1; ++n) {
                     const cx yv = y[P.perm[n] + N * (col0 + c)];
 #pragma unroll
-                    for (int t = 0; t < RP; ++t) cacc(acc[t], cmulc(U[(int64_t)n * RP + t], yv));
+                    for (int t = 0; t < RP; ++t) cmacc(acc[t], U[(int64_t)n * RP + t], yv);
                 }
             }
 #pragma unroll
@@ -413,8 +439,8 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
                                 // forward G: output a uses D_{a,q}; adjoint H: output c uses conj(D_{q,c})
                                 const cx* dA = du + (ADJ ? (q * 2 + 0) : (0 * 2 + q)) * RP;
                                 const cx* dB = du + (ADJ ? (q * 2 + 1) : (1 * 2 + q)) * RP;
-                                cacc(a0, ADJ ? cmulc(dA[t], z0) : cmul(dA[t], z0));
-                                cacc(a1, ADJ ? cmulc(dB[RP - 1 - t], z1) : cmul(dB[RP - 1 - t], z1));
+                                cmacx<ADJ>(a0, dA[t], z0);
+                                cmacx<ADJ>(a1, dB[RP - 1 - t], z1);
                             }
                             o0[t * rt] = a0;
                             o1[(RP - 1 - t) * rt] = a1;
@@ -504,8 +530,8 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
 #pragma unroll
                     for (int s2 = 0; s2 < RP; ++s2) {
                         const cx mv = ADJ ? Mp[s2 * RP + t] : Mp[t * RP + s2];
-                        cacc(aa, ADJ ? cmulc(mv, xa[s2]) : cmul(mv, xa[s2]));
-                        cacc(ab, ADJ ? cmulc(mv, xb[s2]) : cmul(mv, xb[s2]));
+                        cmacx<ADJ>(aa, mv, xa[s2]);
+                        cmacx<ADJ>(ab, mv, xb[s2]);
                     }
                     if (c < ncol) oa[(int64_t)t * P.nc] = aa;
                     if (c + 16 < ncol) oa[(int64_t)t * P.nc + 16] = ab;
@@ -529,10 +555,10 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
                 cx acc = cz<cx>();
                 if (!ADJ) {
 #pragma unroll
-                    for (int s2 = 0; s2 < RP; ++s2) cacc(acc, cmul(Mp[t * RP + s2], x[s2]));
+                    for (int s2 = 0; s2 < RP; ++s2) cmac(acc, Mp[t * RP + s2], x[s2]);
                 } else {
 #pragma unroll
-                    for (int s2 = 0; s2 < RP; ++s2) cacc(acc, cmulc(Mp[s2 * RP + t], x[s2]));
+                    for (int s2 = 0; s2 < RP; ++s2) cmacc(acc, Mp[s2 * RP + t], x[s2]);
                 }
                 out[(pair * RP + t) * P.nc + col0 + c] = acc;
             }
@@ -563,7 +589,7 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
             for (int32_t n = P.off[leaf]; n < n1; ++n) {
                 cx acc = cz<cx>();
 #pragma unroll
-                for (int t = 0; t < RP; ++t) cacc(acc, cmul(U[(int64_t)n * RP + t], x[t]));
+                for (int t = 0; t < RP; ++t) cmac(acc, U[(int64_t)n * RP + t], x[t]);
                 u[P.perm[n] + N * (col0 + c)] = acc;
             }
         }
@@ -577,7 +603,7 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
             const int64_t kx = (jb << k) + pos;
             cx acc = cz<cx>();
 #pragma unroll
-            for (int t = 0; t < RP; ++t) cacc(acc, cmulc(V[kx * RP + t], sm[pos * PS + t * rt + c]));
+            for (int t = 0; t < RP; ++t) cmacc(acc, V[kx * RP + t], sm[pos * PS + t * rt + c]);
             g[kx + N * (col0 + c)] = acc;
         }
     }
