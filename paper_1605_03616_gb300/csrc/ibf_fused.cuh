@@ -190,6 +190,21 @@ __device__ __forceinline__ void cmacx(C& acc, C a, C b)
         cmac(acc, a, b);
 }
 
+// Asynchronous global -> shared copy of one complex element (no register
+// round trip); !valid writes zeros.  Completed by cp_async_wait() before the
+// barrier that publishes the shared memory.
+__device__ __forceinline__ void cp_async_elem(float2* dst, const float2* src, bool valid)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(double2* dst, const double2* src, bool valid)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Two-lane arithmetic on (re, im) pairs: Blackwell's packed FP32 instructions
 // (one issue slot for both lanes) in single precision, per-component double
 // operations otherwise.  Rounding is that of the per-component operations:
@@ -270,22 +285,28 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
     } else {
         const cx* in = (const cx*)P.in;
         if (RT == 32) {
-            // one warp per position: its r rows of 32 columns are loaded
-            // together (r loads in flight per lane), then stored
+            // one warp per position: its r rows of 32 columns are copied
+            // together (r copies in flight per lane); data written by other
+            // CTAs of the same launch (COH) is read past L1 through registers
             const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
             const bool on = lane < ncol;
             for (int pos = threadIdx.x >> 5; pos < G; pos += nw) {
                 const int64_t pair = !ADJ ? (i0 << (L - l0)) + (jb << k) + pos
                                           : (((i0 << k) + brevk(pos, k)) << nbj) + jb;
                 const cx* src = in + pair * RP * P.nc + col0 + lane;
-                cx v[RP];
-#pragma unroll
-                for (int t = 0; t < RP; ++t)
-                    v[t] = on ? (COH ? __ldcg(src + (int64_t)t * P.nc) : src[(int64_t)t * P.nc]) : cz<cx>();
                 cx* dst = sm + pos * PS + lane;
+                if (!COH) {
 #pragma unroll
-                for (int t = 0; t < RP; ++t) dst[t * 32] = v[t];
+                    for (int t = 0; t < RP; ++t) cp_async_elem(dst + t * 32, on ? src + (int64_t)t * P.nc : src, on);
+                } else {
+                    cx v[RP];
+#pragma unroll
+                    for (int t = 0; t < RP; ++t) v[t] = on ? __ldcg(src + (int64_t)t * P.nc) : cz<cx>();
+#pragma unroll
+                    for (int t = 0; t < RP; ++t) dst[t * 32] = v[t];
+                }
             }
+            cp_async_wait();
         } else {
             for (int e = threadIdx.x; e < G * RP * rt; e += blockDim.x) {
                 const int c = e % rt, t = (e / rt) % RP, pos = e / (rt * RP);
@@ -321,13 +342,11 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
             const int64_t C = (((jb << (k - s)) + (p0 >> s)) << 1) + (ac & 1);
             const int64_t ldC = 1LL << (L - l0 - s + 1);
             const cx* src = (const cx*)P.D[st1] + (ia * ldC + C) * RP;
-            cx v[RP];
-#pragma unroll
-            for (int t = 0; t < RP; ++t) v[t] = __ldg(src + t);
             cx* dst = dsm + (st1 * nunit + u) * DS + ac * RP;
 #pragma unroll
-            for (int t = 0; t < RP; ++t) dst[t] = v[t];
+            for (int t = 0; t < RP; ++t) cp_async_elem(dst + t, src + t, true);
         }
+        cp_async_wait();
     }
     __syncthreads();
 
