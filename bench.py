@@ -437,9 +437,8 @@ def run_gpu(a):
     uh = torch.empty_like(gh).pin_memory()
 
     def e2e_step():
-        g.copy_(gh, non_blocking=True)
-        plan.apply_raw(g.data_ptr(), u.data_ptr(), nrhs, stream.cuda_stream)
-        uh.copy_(u, non_blocking=True)
+        # ibf_apply_host: chunked copies in and out overlap the apply
+        plan.apply_host(gh, uh, stream=stream)
 
     for _ in range(max(1, a.warmup)):
         e2e_step()
@@ -452,7 +451,8 @@ def run_gpu(a):
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dist if world > 1 else None, dev)
     e2e = {"value": job_throughput(nrhs, a.steps, world, e2e_ms), "unit": "vectors/s",
-           "h2d_bytes_per_step": int(g.numel() * 8), "d2h_bytes_per_step": int(u.numel() * 8)}
+           "h2d_bytes_per_step": int(gh.numel() * 8), "d2h_bytes_per_step": int(uh.numel() * 8),
+           "api": "ibf_apply_host (page-locked host buffers, copies overlapped with the apply)"}
 
     # ---- plain FP64 explicit single-vector form on the same GPU, and accuracy
     fp64 = None

@@ -164,6 +164,28 @@ int ibf_apply(ibf_plan* plan, const void* g, void* u, int nrhs, ibf_stream_t str
 int ibf_apply_adjoint(ibf_plan* plan, const void* y, void* g, int nrhs, ibf_stream_t stream);
 
 /*
+ * ibf_apply_host -- u = K g (adjoint = 0) or g = K^* y (adjoint = 1) with
+ * both vectors in host memory (same column-major layouts as ibf_apply and
+ * ibf_apply_adjoint).  The paper applies the factors to resident vectors; this
+ * is the transfer-overlapped form of the same apply for data that lives on
+ * the host.  The columns are processed in chunks of the plan's rhs tile
+ * (16 for 2D and explicit plans): while chunk j is applied on `stream`,
+ * chunk j+1 is copied in and chunk j-1 copied out on two copy streams owned
+ * by the plan, ordered by events.
+ *   in_host, out_host : host arrays N x nrhs; page-locked memory
+ *          (cudaHostAlloc / cudaHostRegister) lets the copies run
+ *          asynchronously and overlap, pageable memory works but serialises.
+ *          Must stay valid and untouched until `stream` has completed.
+ * The first call on a plan creates its staging buffers (4 N chunk elements on
+ * the device), copy streams and events: make it outside stream capture.
+ * Returns once the work is queued; out_host is complete when `stream` is.
+ * Calls on one plan must be ordered on `stream`.  Errors as ibf_apply;
+ * IBF_ERR_OOM if the staging buffers cannot be allocated.
+ */
+int ibf_apply_host(ibf_plan* plan, const void* in_host, void* out_host, int nrhs, int adjoint,
+                   ibf_stream_t stream);
+
+/*
  * ibf_apply_static_scratch -- u = K g like ibf_apply, for callers that may
  * not allocate device memory once their plans exist (for example a plug-in
  * whose host application owns the device heap and forbids further cudaMalloc

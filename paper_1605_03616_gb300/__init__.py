@@ -41,7 +41,7 @@ EXPORTS = ("ibf_plan_create", "ibf_plan_create_ex", "ibf_apply", "ibf_apply_adjo
            "ibf_plan_query", "ibf_get_last_error", "ibf_plan_profile_begin", "ibf_plan_profile_end",
            "ibf_apply_static_scratch", "ibf_batch_create", "ibf_batch_apply", "ibf_batch_query",
            "ibf_batch_destroy", "ibf_plan_autotune", "ibf_batch_apply_persistent", "ibf_batch_status",
-           "ibf_batch_set_wait_limit", "ibf_batch_test_withhold")
+           "ibf_batch_set_wait_limit", "ibf_batch_test_withhold", "ibf_apply_host")
 
 BQ_LAUNCHES, BQ_WORKSPACE_BYTES, BQ_COUNT, BQ_PERSIST_ITEMS = range(4)
 
@@ -235,6 +235,22 @@ class Plan:
     def adjoint_raw(self, y_ptr: int, g_ptr: int, nrhs: int, stream_ptr: int = 0) -> None:
         _check(self._lib.ibf_apply_adjoint(self._p, ctypes.c_void_p(y_ptr), ctypes.c_void_p(g_ptr), nrhs,
                                            ctypes.c_void_p(stream_ptr)))
+
+    def apply_host(self, src, dst, adjoint: bool = False, stream=None) -> None:
+        """ibf_apply_host: `src` and `dst` are CPU tensors (or numpy arrays) of
+        shape (nrhs, N), complex64 or complex128 to match the plan; page-locked
+        tensors (`pin_memory()`) overlap the copies with the apply.  Queued on
+        `stream` (default: the current CUDA stream); synchronise it before
+        reading `dst`."""
+        torch = _torch()
+
+        def ptr(a):
+            return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+
+        nrhs = int(src.shape[0]) if len(src.shape) == 2 else 1
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        _check(self._lib.ibf_apply_host(self._p, ctypes.c_void_p(ptr(src)), ctypes.c_void_p(ptr(dst)), nrhs,
+                                        1 if adjoint else 0, ctypes.c_void_p(s)))
 
 
 class Batch:

@@ -62,6 +62,13 @@ struct ibf_plan {
     void* p2d = nullptr;
 
     void* ws[2] = {nullptr, nullptr};   // apply workspace (ping-pong Lambda buffers)
+
+    // host-buffer apply (ibf_apply_host), set up by its first call: device
+    // staging slots [2][in|out][N x chunk], two copy streams and their events
+    void* hst_buf = nullptr;
+    int hst_chunk = 0;
+    cudaStream_t hst_in = nullptr, hst_out = nullptr;
+    cudaEvent_t hst_ev[7] = {};   // start, h2d[2], apply[2], d2h[2]
     size_t factor_bytes = 0, ws_bytes = 0;
     int64_t nnz = 0;
     std::vector<void*> allocations;

@@ -379,6 +379,10 @@ static void free_plan(ibf_plan* p)
     if (!p) return;
     delete (Plan2D*)p->p2d;
     for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : p->hst_ev)
+        if (e) cudaEventDestroy(e);
+    if (p->hst_in) cudaStreamDestroy(p->hst_in);
+    if (p->hst_out) cudaStreamDestroy(p->hst_out);
     for (void* a : p->allocations) cudaFree(a);
     delete p;
 }
@@ -605,6 +609,83 @@ extern "C" int ibf_apply_adjoint(ibf_plan* p, const void* y, void* g, int nrhs, 
     if (p->d == 2) return set_error(IBF_ERR_UNSUPPORTED, "2D plans have no adjoint apply");
     if (p->form == IBF_FORM_EXPLICIT) return explicit_adjoint(p, y, g, nrhs, (cudaStream_t)stream);
     return fused_apply(p, y, g, nrhs, true, (cudaStream_t)stream);
+}
+
+// Host-buffer apply: chunks of `hst_chunk` columns go through two device
+// staging slots.  Chunk j (slot s = j % 2): copy-in stream waits until the
+// apply of chunk j-2 has read slot s, copies the chunk in; `stream` waits for
+// that copy and for the copy-out of chunk j-2 from slot s, applies; copy-out
+// stream waits for the apply and copies the result out.  So the copies of
+// neighbouring chunks overlap the apply of the current one.
+static int host_setup(ibf_plan* p)
+{
+    if (p->hst_buf) return IBF_OK;
+    const size_t esz = p->dtype == IBF_C128 ? 16 : 8;
+    const int tile = (p->d == 1 && p->form == IBF_FORM_STRUCTURED && p->rtile > 0) ? p->rtile : 16;
+    p->hst_chunk = std::max(1, std::min(p->max_nrhs, tile));
+    cudaError_t e;
+    for (cudaEvent_t& ev : p->hst_ev)
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_error(e, "host apply: cudaEventCreate");
+    if ((e = cudaStreamCreateWithFlags(&p->hst_in, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&p->hst_out, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_error(e, "host apply: cudaStreamCreate");
+    void* buf = nullptr;
+    if ((e = cudaMalloc(&buf, 4 * esz * (size_t)p->N * p->hst_chunk)) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(IBF_ERR_OOM, "host apply: staging buffers");
+    }
+    p->allocations.push_back(buf);
+    p->hst_buf = buf;
+    return IBF_OK;
+}
+
+extern "C" int ibf_apply_host(ibf_plan* p, const void* hin, void* hout, int nrhs, int adjoint, ibf_stream_t stream)
+{
+    if (!p) return set_error(IBF_ERR_INVALID, "plan is NULL");
+    if (!hin || !hout) return set_error(IBF_ERR_INVALID, "NULL vector pointer");
+    if (nrhs < 1) return set_error(IBF_ERR_INVALID, "nrhs must be >= 1");
+    const size_t esz = p->dtype == IBF_C128 ? 16 : 8;
+    if (((uintptr_t)hin % esz) || ((uintptr_t)hout % esz)) return set_error(IBF_ERR_INVALID, "misaligned vector pointer");
+    if (adjoint && p->d == 2) return set_error(IBF_ERR_UNSUPPORTED, "2D plans have no adjoint apply");
+    int rc = host_setup(p);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t col = esz * (size_t)p->N;
+    const int ch = p->hst_chunk;
+    char* slot_in[2] = {(char*)p->hst_buf, (char*)p->hst_buf + col * ch};
+    char* slot_out[2] = {(char*)p->hst_buf + 2 * col * ch, (char*)p->hst_buf + 3 * col * ch};
+    cudaEvent_t ev0 = p->hst_ev[0], *h2d = p->hst_ev + 1, *app = p->hst_ev + 3, *d2h = p->hst_ev + 5;
+    cudaError_t e;
+    // earlier work on `stream` (a previous call's applies) comes first
+    if ((e = cudaEventRecord(ev0, st)) != cudaSuccess) return cuda_error(e, "host apply: event");
+    cudaStreamWaitEvent(p->hst_in, ev0, 0);
+    cudaStreamWaitEvent(p->hst_out, ev0, 0);
+    const int nch = (nrhs + ch - 1) / ch;
+    for (int j = 0; j < nch; ++j) {
+        const int s = j & 1, c0 = j * ch, nc = std::min(ch, nrhs - c0);
+        if (j >= 2) cudaStreamWaitEvent(p->hst_in, app[s], 0);
+        if ((e = cudaMemcpyAsync(slot_in[s], (const char*)hin + col * c0, col * nc, cudaMemcpyHostToDevice,
+                                 p->hst_in)) != cudaSuccess)
+            return cuda_error(e, "host apply: copy in");
+        cudaEventRecord(h2d[s], p->hst_in);
+        cudaStreamWaitEvent(st, h2d[s], 0);
+        if (j >= 2) cudaStreamWaitEvent(st, d2h[s], 0);
+        rc = adjoint ? ibf_apply_adjoint(p, slot_in[s], slot_out[s], nc, stream)
+                     : ibf_apply(p, slot_in[s], slot_out[s], nc, stream);
+        if (rc) return rc;
+        cudaEventRecord(app[s], st);
+        cudaStreamWaitEvent(p->hst_out, app[s], 0);
+        if ((e = cudaMemcpyAsync((char*)hout + col * c0, slot_out[s], col * nc, cudaMemcpyDeviceToHost,
+                                 p->hst_out)) != cudaSuccess)
+            return cuda_error(e, "host apply: copy out");
+        cudaEventRecord(d2h[s], p->hst_out);
+    }
+    // `stream` completes only after every copy-out
+    cudaStreamWaitEvent(st, d2h[0], 0);
+    if (nch > 1) cudaStreamWaitEvent(st, d2h[1], 0);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? IBF_OK : cuda_error(e, "host apply");
 }
 
 extern "C" int ibf_plan_profile_begin(ibf_plan* p, int cap)
