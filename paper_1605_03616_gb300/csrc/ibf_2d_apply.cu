@@ -46,6 +46,27 @@ __device__ __forceinline__ void addc(C& a, C b)
     a.x += b.x;
     a.y += b.y;
 }
+// acc += a b as a chain of four fused multiply-adds
+template <typename C>
+__device__ __forceinline__ void cmac(C& acc, C a, C b)
+{
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+// Two-lane arithmetic on (re, im) pairs: packed FP32 instructions in single
+// precision (one issue slot for both lanes), per-component operations in
+// double; a - b is b * (-1) + a rounded once.
+__device__ __forceinline__ float2 p2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p2sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 p2fma(float2 w, float2 x, float2 acc) { return __ffma2_rn(w, x, acc); }
+__device__ __forceinline__ double2 p2add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 p2sub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 p2fma(double2 w, double2 x, double2 acc)
+{
+    return make_double2(fma(w.x, x.x, acc.x), fma(w.y, x.y, acc.y));
+}
 
 struct RingArgs {
     double q1[12], q2[12];
@@ -95,11 +116,7 @@ __global__ void __launch_bounds__(256) k2_center(const typename C2D<Real>::T* __
             const cx* gr = Gs + (kc + kk) * rt + cg;
 #pragma unroll
             for (int k = 0; k < CPT; ++k)
-                if (cg + 2 * k < rt) {
-                    const cx x = gr[2 * k];
-                    acc[k].x += kv.x * x.x - kv.y * x.y;
-                    acc[k].y += kv.x * x.y + kv.y * x.x;
-                }
+                if (cg + 2 * k < rt) cmac(acc[k], kv, gr[2 * k]);
         }
     }
 #pragma unroll
@@ -117,13 +134,16 @@ __global__ void __launch_bounds__(256) k2_center(const typename C2D<Real>::T* __
 
 // Even/odd weights of T_0 (T_1 = J T_0 J, as in 1D): H form rows by input
 // index (PmT[s][t], QmT[s][t]), G form rows by output index (E[t][s], F[t][s]).
+// Each weight is stored as a (w, w) pair, so one two-lane multiply-add
+// applies it to a complex value.
 template <typename Real, int RP>
 struct EO2 {
     static constexpr int HR = (RP + 1) / 2, HQ = RP / 2;
-    Real PmT[RP][HR];
-    Real QmT[RP][HQ];
-    Real E[RP][HR];
-    Real F[RP][HQ];
+    typedef typename C2D<Real>::T P;
+    P PmT[RP][HR];
+    P QmT[RP][HQ];
+    P E[RP][HR];
+    P F[RP][HQ];
 };
 
 // Child of box i at quadtree level l (side 2^l boxes per axis), c = 2 c1 + c2.
@@ -263,28 +283,17 @@ __global__ void __launch_bounds__(k2_level_threads<Real, RP>(), k2_level_blocks<
             for (int s2 = 0; s2 < RP; ++s2) {
                 const cx y0 = mulc(d0[s2], x0[s2 * rt]);
                 const cx y1 = mulc(d1[RP - 1 - s2], x1[(RP - 1 - s2) * rt]);
-                const Real px = y0.x + y1.x, py = y0.y + y1.y, mx = y0.x - y1.x, my = y0.y - y1.y;
+                const cx pv = p2add(y0, y1), mv = p2sub(y0, y1);
 #pragma unroll
-                for (int t = 0; t < HR; ++t) {
-                    we[t].x += W.PmT[s2][t] * px;
-                    we[t].y += W.PmT[s2][t] * py;
-                }
+                for (int t = 0; t < HR; ++t) we[t] = p2fma(W.PmT[s2][t], pv, we[t]);
 #pragma unroll
-                for (int t = 0; t < HQ; ++t) {
-                    wo[t].x += W.QmT[s2][t] * mx;
-                    wo[t].y += W.QmT[s2][t] * my;
-                }
+                for (int t = 0; t < HQ; ++t) wo[t] = p2fma(W.QmT[s2][t], mv, wo[t]);
             }
             cx* wd = Ws + (((ah * 2 + c1) * RP + s1) * RP) * rt + cl;
 #pragma unroll
             for (int t = 0; t < HQ; ++t) {
-                cx p, m;
-                p.x = we[t].x + wo[t].x;
-                p.y = we[t].y + wo[t].y;
-                m.x = we[t].x - wo[t].x;
-                m.y = we[t].y - wo[t].y;
-                wd[t * rt] = p;
-                wd[(RP - 1 - t) * rt] = m;
+                wd[t * rt] = p2add(we[t], wo[t]);
+                wd[(RP - 1 - t) * rt] = p2sub(we[t], wo[t]);
             }
             if (RP & 1) wd[HQ * rt] = we[HQ];
         }
@@ -304,30 +313,19 @@ __global__ void __launch_bounds__(k2_level_threads<Real, RP>(), k2_level_blocks<
             for (int s1 = 0; s1 < RP; ++s1) {
                 const cx v0 = w0[s1 * RP * rt];
                 const cx v1 = w1[(RP - 1 - s1) * RP * rt];
-                const Real px = v0.x + v1.x, py = v0.y + v1.y, mx = v0.x - v1.x, my = v0.y - v1.y;
+                const cx pv = p2add(v0, v1), mv = p2sub(v0, v1);
 #pragma unroll
-                for (int t = 0; t < HR; ++t) {
-                    we[t].x += W.PmT[s1][t] * px;
-                    we[t].y += W.PmT[s1][t] * py;
-                }
+                for (int t = 0; t < HR; ++t) we[t] = p2fma(W.PmT[s1][t], pv, we[t]);
 #pragma unroll
-                for (int t = 0; t < HQ; ++t) {
-                    wo[t].x += W.QmT[s1][t] * mx;
-                    wo[t].y += W.QmT[s1][t] * my;
-                }
+                for (int t = 0; t < HQ; ++t) wo[t] = p2fma(W.QmT[s1][t], mv, wo[t]);
             }
             if (cl < T.ncol) {
                 const int64_t Aa = child2s(l - 1, T.ip, a0 + ah);
                 cx* od = T.outb + ((Aa * T.nj + T.j) * R2 + t2) * A.nc + cl;
 #pragma unroll
                 for (int t = 0; t < HQ; ++t) {
-                    cx p, m;
-                    p.x = we[t].x + wo[t].x;
-                    p.y = we[t].y + wo[t].y;
-                    m.x = we[t].x - wo[t].x;
-                    m.y = we[t].y - wo[t].y;
-                    od[(int64_t)(t * RP) * A.nc] = p;
-                    od[(int64_t)((RP - 1 - t) * RP) * A.nc] = m;
+                    od[(int64_t)(t * RP) * A.nc] = p2add(we[t], wo[t]);
+                    od[(int64_t)((RP - 1 - t) * RP) * A.nc] = p2sub(we[t], wo[t]);
                 }
                 if (RP & 1) od[(int64_t)(HQ * RP) * A.nc] = we[HQ];
             }
@@ -373,10 +371,8 @@ __global__ void __launch_bounds__(k2_level_threads<Real, RP>(), k2_level_blocks<
 #pragma unroll
             for (int s1 = 0; s1 < HQ; ++s1) {
                 const cx lo = xc[s1 * RP * rt], hi = xc[(RP - 1 - s1) * RP * rt];
-                xe[s1].x = lo.x + hi.x;
-                xe[s1].y = lo.y + hi.y;
-                xo[s1].x = lo.x - hi.x;
-                xo[s1].y = lo.y - hi.y;
+                xe[s1] = p2add(lo, hi);
+                xo[s1] = p2sub(lo, hi);
             }
             if (RP & 1) xe[HQ] = xc[HQ * RP * rt];
             cx* z = Zs + (ch * 2 * R2 + s2) * rt + cl;
@@ -384,22 +380,11 @@ __global__ void __launch_bounds__(k2_level_threads<Real, RP>(), k2_level_blocks<
             for (int t1 = 0; t1 < RP; ++t1) {
                 cx ev = zc<cx>(), fv = zc<cx>();
 #pragma unroll
-                for (int sidx = 0; sidx < HR; ++sidx) {
-                    ev.x += W.E[t1][sidx] * xe[sidx].x;
-                    ev.y += W.E[t1][sidx] * xe[sidx].y;
-                }
+                for (int sidx = 0; sidx < HR; ++sidx) ev = p2fma(W.E[t1][sidx], xe[sidx], ev);
 #pragma unroll
-                for (int sidx = 0; sidx < HQ; ++sidx) {
-                    fv.x += W.F[t1][sidx] * xo[sidx].x;
-                    fv.y += W.F[t1][sidx] * xo[sidx].y;
-                }
-                cx z0, z1;
-                z0.x = ev.x + fv.x;
-                z0.y = ev.y + fv.y;
-                z1.x = ev.x - fv.x;
-                z1.y = ev.y - fv.y;
-                z[(t1 * RP) * rt] = z0;
-                z[(R2 + (RP - 1 - t1) * RP) * rt] = z1;
+                for (int sidx = 0; sidx < HQ; ++sidx) fv = p2fma(W.F[t1][sidx], xo[sidx], fv);
+                z[(t1 * RP) * rt] = p2add(ev, fv);
+                z[(R2 + (RP - 1 - t1) * RP) * rt] = p2sub(ev, fv);
             }
         }
         __syncthreads();
@@ -413,10 +398,8 @@ __global__ void __launch_bounds__(k2_level_threads<Real, RP>(), k2_level_blocks<
 #pragma unroll
                 for (int s2 = 0; s2 < HQ; ++s2) {
                     const cx lo = zr[s2 * rt], hi = zr[(RP - 1 - s2) * rt];
-                    xe[s2].x = lo.x + hi.x;
-                    xe[s2].y = lo.y + hi.y;
-                    xo[s2].x = lo.x - hi.x;
-                    xo[s2].y = lo.y - hi.y;
+                    xe[s2] = p2add(lo, hi);
+                    xo[s2] = p2sub(lo, hi);
                 }
                 if (RP & 1) xe[HQ] = zr[HQ * rt];
                 const cx* d0 = Ds + ((2 * ma1 + 0) * 4 + c) * R2 + mt1 * RP;
@@ -425,22 +408,11 @@ __global__ void __launch_bounds__(k2_level_threads<Real, RP>(), k2_level_blocks<
                 for (int t2 = 0; t2 < RP; ++t2) {
                     cx ev = zc<cx>(), fv = zc<cx>();
 #pragma unroll
-                    for (int sidx = 0; sidx < HR; ++sidx) {
-                        ev.x += W.E[t2][sidx] * xe[sidx].x;
-                        ev.y += W.E[t2][sidx] * xe[sidx].y;
-                    }
+                    for (int sidx = 0; sidx < HR; ++sidx) ev = p2fma(W.E[t2][sidx], xe[sidx], ev);
 #pragma unroll
-                    for (int sidx = 0; sidx < HQ; ++sidx) {
-                        fv.x += W.F[t2][sidx] * xo[sidx].x;
-                        fv.y += W.F[t2][sidx] * xo[sidx].y;
-                    }
-                    cx z0, z1;
-                    z0.x = ev.x + fv.x;
-                    z0.y = ev.y + fv.y;
-                    z1.x = ev.x - fv.x;
-                    z1.y = ev.y - fv.y;
-                    addc(acc[0][t2], mulc(d0[t2], z0));
-                    addc(acc[1][RP - 1 - t2], mulc(d1[RP - 1 - t2], z1));
+                    for (int sidx = 0; sidx < HQ; ++sidx) fv = p2fma(W.F[t2][sidx], xo[sidx], fv);
+                    cmac(acc[0][t2], d0[t2], p2add(ev, fv));
+                    cmac(acc[1][RP - 1 - t2], d1[RP - 1 - t2], p2sub(ev, fv));
                 }
             }
         }
@@ -505,10 +477,7 @@ __global__ void __launch_bounds__(128) k2_switch(const RingArgs A, const typenam
             if (t < R2) {
                 const cx m = Ms[t * R2 + sidx];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    acc[k][q].x += m.x * x[q].x - m.y * x[q].y;
-                    acc[k][q].y += m.x * x[q].y + m.y * x[q].x;
-                }
+                for (int q = 0; q < 4; ++q) cmac(acc[k][q], m, x[q]);
             }
         }
     }
@@ -542,8 +511,8 @@ __global__ void __launch_bounds__(256) k2_term(const RingArgs A, const typename 
     const int SS = RP * rt + PAD;                // stride of one o2 in Ss
     cx* Ss = Ls + 2 * R2 * rt;                   // [PB][RP][rt] (+ pad per o2)
     cx* Us = Ss + PB * SS;                       // [2][PB * PB] uph of the block
-    Real* W1 = reinterpret_cast<Real*>(Us + 2 * PB * PB);   // [PB][RP]
-    Real* W2 = W1 + PB * RP;                                // [PB][RP]
+    cx* W1 = Us + 2 * PB * PB;   // [PB][RP] Lagrange weights of the block's rows, as (w, w) pairs
+    cx* W2 = W1 + PB * RP;       // [PB][RP] the same for its columns
     const int64_t N = (int64_t)A.n * A.n, mm = (int64_t)A.m * A.m;
     const int K = A.n / A.m, nb1 = K / PB;
     const int ntile = (A.nc + rt - 1) / rt;
@@ -555,8 +524,9 @@ __global__ void __launch_bounds__(256) k2_term(const RingArgs A, const typename 
     const int64_t n1b = (leaf / A.m) * K + o1b, n2b = (leaf % A.m) * K + o2b;
     const int col0 = tile * rt, ncol = min(rt, A.nc - col0);
     for (int e = threadIdx.x; e < PB * RP; e += blockDim.x) {
-        W1[e] = lw[(o1b + e / RP) * RP + e % RP];
-        W2[e] = lw[(o2b + e / RP) * RP + e % RP];
+        const Real w1 = lw[(o1b + e / RP) * RP + e % RP], w2 = lw[(o2b + e / RP) * RP + e % RP];
+        W1[e].x = W1[e].y = w1;
+        W2[e].x = W2[e].y = w2;
     }
     auto issue = [&](int b) {
         const cx* lb = lam + ((size_t)(b * mm + leaf) * R2) * A.nc + col0;
@@ -589,12 +559,7 @@ __global__ void __launch_bounds__(256) k2_term(const RingArgs A, const typename 
             const cx* lr = Lb + t1 * RP * rt + cl;
             cx sv = zc<cx>();
 #pragma unroll
-            for (int t2 = 0; t2 < RP; ++t2) {
-                const Real w = W2[o2 * RP + t2];
-                const cx x = lr[t2 * rt];
-                sv.x += w * x.x;
-                sv.y += w * x.y;
-            }
+            for (int t2 = 0; t2 < RP; ++t2) sv = p2fma(W2[o2 * RP + t2], lr[t2 * rt], sv);
             Ss[o2 * SS + t1 * rt + cl] = sv;
         }
         __syncthreads();
@@ -607,13 +572,8 @@ __global__ void __launch_bounds__(256) k2_term(const RingArgs A, const typename 
                 const cx* sr = Ss + o2 * SS + cl;
                 cx v = zc<cx>();
 #pragma unroll
-                for (int t1 = 0; t1 < RP; ++t1) {
-                    const Real w = W1[o1 * RP + t1];
-                    const cx x = sr[t1 * rt];
-                    v.x += w * x.x;
-                    v.y += w * x.y;
-                }
-                addc(acc[k], mulc(Ub[o1 * PB + o2], v));
+                for (int t1 = 0; t1 < RP; ++t1) v = p2fma(W1[o1 * RP + t1], sr[t1 * rt], v);
+                cmac(acc[k], Ub[o1 * PB + o2], v);
             }
         }
         __syncthreads();   // buffers of box b and Ss are free again
@@ -643,19 +603,24 @@ static int apply_2d_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStrea
     {
         constexpr int HQ = EO2<Real, RP>::HQ;
         const auto& T0 = p->T[0];
+        auto pr = [](double v) {
+            typename C2D<Real>::T q;
+            q.x = q.y = (Real)v;
+            return q;
+        };
         for (int t = 0; t < HQ; ++t)
             for (int s = 0; s < RP; ++s) {
-                W.PmT[s][t] = (Real)((T0[t][s] + T0[RP - 1 - t][s]) / 2);
-                W.QmT[s][t] = (Real)((T0[t][s] - T0[RP - 1 - t][s]) / 2);
+                W.PmT[s][t] = pr((T0[t][s] + T0[RP - 1 - t][s]) / 2);
+                W.QmT[s][t] = pr((T0[t][s] - T0[RP - 1 - t][s]) / 2);
             }
         if (RP & 1)
-            for (int s = 0; s < RP; ++s) W.PmT[s][HQ] = (Real)T0[HQ][s];
+            for (int s = 0; s < RP; ++s) W.PmT[s][HQ] = pr(T0[HQ][s]);
         for (int t = 0; t < RP; ++t) {
             for (int s = 0; s < HQ; ++s) {
-                W.E[t][s] = (Real)((T0[s][t] + T0[RP - 1 - s][t]) / 2);
-                W.F[t][s] = (Real)((T0[s][t] - T0[RP - 1 - s][t]) / 2);
+                W.E[t][s] = pr((T0[s][t] + T0[RP - 1 - s][t]) / 2);
+                W.F[t][s] = pr((T0[s][t] - T0[RP - 1 - s][t]) / 2);
             }
-            if (RP & 1) W.E[t][HQ] = (Real)T0[HQ][t];
+            if (RP & 1) W.E[t][HQ] = pr(T0[HQ][t]);
         }
     }
     const int64_t N = (int64_t)P->n * P->n;
@@ -697,8 +662,8 @@ static int apply_2d_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStrea
         const int ntile_s = (nc + rts - 1) / rts;
         const size_t smem_s = ((size_t)R2 * R2 + (size_t)R2 * 32) * sizeof(cx);
         auto term_smem = [&](int pbs) {
-            return (2 * (size_t)R2 * rts + (size_t)pbs * (RP * rts + 16 / pbs) + 2 * pbs * pbs) * sizeof(cx) +
-                   2 * (size_t)pbs * RP * sizeof(Real);
+            return (2 * (size_t)R2 * rts + (size_t)pbs * (RP * rts + 16 / pbs) + 2 * pbs * pbs + 2 * pbs * RP) *
+                   sizeof(cx);
         };
         for (const Ring2D& R : P->rings) {
             RingArgs A;
