@@ -329,7 +329,10 @@ def run_gpu(a):
             dist.barrier()
 
     N, r, nrhs = a.N, a.r, a.nrhs
-    plan = ibf.Plan(ibf.PHASE_FIO1D, N, r, ibf.C64_FP32, max_nrhs=nrhs)
+    torch.cuda.synchronize()
+    t_c0 = time.perf_counter()
+    plan = ibf.Plan(ibf.PHASE_FIO1D, N, r, ibf.C64_FP32, max_nrhs=nrhs)   # returns after construction
+    t_struct = (time.perf_counter() - t_c0) * 1e3
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     g_host = W.complex_normal((nrhs, N), W.rng(workload=2 + 1000 * rank), dtype=np.complex64)  # row = column
@@ -457,7 +460,9 @@ def run_gpu(a):
     # ---- plain FP64 explicit single-vector form on the same GPU, and accuracy
     fp64 = None
     if not a.skip_fp64 and rank == 0:
+        t_c0 = time.perf_counter()
         p64 = ibf.Plan(ibf.PHASE_FIO1D, N, r, ibf.C128, max_nrhs=1)
+        t_expl = (time.perf_counter() - t_c0) * 1e3
         g64 = g[0:1].to(torch.complex128).contiguous()
         u64 = torch.empty_like(g64)
         for _ in range(2):
@@ -489,6 +494,17 @@ def run_gpu(a):
     if rank == 0 and not a.skip_batch:
         batch = run_batch(ibf, torch)
 
+    # ---- construction (SURVEY-style count of phase evaluations of the
+    # explicit factors, (3 r L + r^2 + 2 r) N, FP64 on the GPU)
+    L = int(round(np.log2(N)))
+    n_phase = (3 * r * L + r * r + 2 * r) * N
+    construction = {"structured_fp32_plan_ms": t_struct,
+                    "phase_evaluations": n_phase,
+                    "phase_evaluations_per_s_structured": n_phase / (t_struct / 1e3),
+                    "note": "wall clock of plan creation (host set-up, FP64 phase kernels, uploads), one run"}
+    if fp64 is not None:
+        construction["explicit_fp64_plan_ms"] = t_expl
+
     fio2d = None
     if rank == 0 and not a.skip_2d:
         fio2d = run_2d(ibf, torch)
@@ -512,7 +528,8 @@ def run_gpu(a):
                            "l2": "inputs and workspace larger than L2 (no flush)",
                            "parallelism": "independent rhs batches per GPU (dp%d)" % world},
                 "clocks": clk, "e2e": e2e, "gpu_launches": a.steps * launches, "roofline": roof,
-                "fp64_plain": fp64, "batch256": batch, "fio2d": fio2d, "cpu_baseline": cpu}
+                "fp64_plain": fp64, "construction": construction, "batch256": batch, "fio2d": fio2d,
+                "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:

@@ -1,0 +1,49 @@
+"""Parity at the benchmark's full size: 1D FIO (Sec. 6.2 form), N = 2^20,
+r = 9, 64 right-hand sides, FP32 structured apply in the launch shape the
+autotuner picks (the configuration bench.py times).  The oracle computes two
+sampled columns in full (matrix-free preliminary IBF, FP64); the GPU result
+must match them within 1e-5 relative L2, and the IBF must be within its
+interpolation error (2.5e-5 class at r = 9) of the direct sum on sampled rows."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ibf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1605_03616_gb300 as m
+    return m
+
+
+def test_full_size_fio1d_sampled_columns(ibf):
+    N, r, nrhs = 1 << 20, 9, 64
+    plan = ibf.Plan(ibf.PHASE_FIO1D, N, r, ibf.C64_FP32, max_nrhs=nrhs)
+    k, rt, _ = plan.autotune(nrhs)
+    g = W.complex_normal((nrhs, N), W.rng(workload=2), dtype=np.complex64)   # rows = columns of g
+    gd = torch.from_numpy(g).cuda()
+    u = torch.empty_like(gd)
+    plan.apply_raw(gd.data_ptr(), u.data_ptr(), nrhs, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    u = u.cpu().numpy()
+    cols = [0, nrhs - 1]
+    x = W.uniform_x(N)
+    g2 = g[cols].T.astype(np.complex128)                                      # N x 2
+    ref = O.ibf_apply_1d(O.PHASE_FIO1D, N, r, x, g2)
+    err = O.rel_l2(u[cols].T, ref)
+    rows = W.rng(900).choice(N, 32, replace=False)
+    ed = O.rel_l2(ref[rows], O.direct_1d(O.PHASE_FIO1D, x[rows], W.omega_1d(N), g2))
+    print("\nfull size N=2^20 nrhs=64 (k=%d, tile %d): fp32 vs oracle %.3e; oracle IBF vs direct (32 rows) %.3e"
+          % (k, rt, err, ed))
+    assert err < 1e-5
+    assert ed < 1e-4
+    plan.close()
