@@ -226,10 +226,11 @@ int ibf_apply_static_scratch(const ibf_plan* plan, const void* g, void* u, int n
  * buffers must outlive it.  Synchronizes the device before returning.
  *
  * ibf_batch_apply runs the whole batch on `stream`: one launch runs fused
- * chunk p of every plan with the same level kind and rhs tile width (1, 2,
- * ..., 32), so the number of launches (IBF_BQ_LAUNCHES) is at most 12 times
- * the largest number of chunks of any plan, independent of the number of
- * plans.  It copies nothing from the host and
+ * chunk p of every plan with the same level kind, rhs tile width (1, 2, ...,
+ * 32) and fusion depth, so the number of launches (IBF_BQ_LAUNCHES) is
+ * bounded by the number of distinct (kind, tile, depth) shapes per chunk
+ * index times the largest number of chunks of any plan, independent of the
+ * number of plans.  It copies nothing from the host and
  * allocates nothing, so it may be captured in a CUDA graph.  Calls on one
  * batch must be ordered.
  */

@@ -4,10 +4,10 @@
 // A batch binds, once, a list of plans with their input/output buffers and
 // right-hand-side counts.  Each plan's apply is a short sequence of fused
 // chunks (levels fused per launch); the batch runs chunk p of every plan in
-// one launch of k_fused_batch per (level kind, tile width) (CTA ranges map to
-// plans through a prefix sum), so a batch of B plans costs at most
-// 12 max_b(chunks_b) launches, whatever B, instead of sum_b(chunks_b), and ibf_batch_apply issues nothing but
-// those launches: it can be captured in a CUDA graph.
+// one launch of k_fused_batch per (level kind, tile width, fusion depth) (CTA
+// ranges map to plans through a prefix sum), so the launch count depends on
+// the shapes present, not on the number of plans, and ibf_batch_apply issues
+// nothing but those launches: it can be captured in a CUDA graph.
 #include <algorithm>
 #include <vector>
 
@@ -244,12 +244,14 @@ extern "C" int ibf_batch_create(ibf_plan* const* plans, int count, const int* nr
     }
     B->ws_bytes = ws;
 
-    // one launch per (chunk index, tile width): plans whose tiles differ get
-    // CTAs sized for their tile, (2^k / 2) * rt threads
+    // one launch per (chunk index, level kind, tile width, fusion depth): every
+    // CTA of a launch has exactly the shape its chunk needs, (2^k / 2) * rt
+    // threads and the shared memory of depth k
     const int cap = p0->dtype == IBF_C128 ? FusedTraits<double>::kThreads : FusedTraits<float>::kThreads;
     for (int ph = 0; ph < nphase; ++ph) {
         for (int kc = 0; kc < 2; ++kc)
-        for (int rtc = 1; rtc <= 32; rtc *= 2) {
+        for (int rtc = 1; rtc <= 32; rtc *= 2)
+        for (int kq = 1; kq <= kMaxFuse; ++kq) {
             std::vector<FusedDesc> descs;
             std::vector<int64_t> start;
             int64_t blocks = 0;
@@ -260,7 +262,7 @@ extern "C" int ibf_batch_create(ibf_plan* const* plans, int count, const int* nr
                 if (ph >= nch || rt[b] != rtc) continue;
                 const ibf_plan* p = plans[b];
                 const Chunk ch = B->adjoint ? sched[b][nch - 1 - ph] : sched[b][ph];
-                if (ch.kind != kc) continue;
+                if (ch.kind != kc || ch.hi - ch.lo != kq) continue;
                 FusedDesc d;
                 memset(&d, 0, sizeof(d));
                 d.k = ch.hi - ch.lo;
