@@ -83,10 +83,17 @@ enum ibf_form {
     IBF_FORM_AUTO = 0,       /* EXPLICIT for IBF_C128, STRUCTURED otherwise             */
     IBF_FORM_EXPLICIT = 1,   /* every r x r block of V^0, H^l, M^h, G^l, U^L stored
                                 as in Sec. 3; one kernel per level (the plain form)   */
-    IBF_FORM_STRUCTURED = 2  /* each butterfly block stored as diag * T_c * diag with
+    IBF_FORM_STRUCTURED = 2, /* each butterfly block stored as diag * T_c * diag with
                                 the two universal real Lagrange transfer matrices T_c
                                 and the diagonal phases of adjacent levels merged;
                                 several levels fused per kernel                       */
+    IBF_FORM_OPTIMAL = 3     /* the optimal IBF after the sweep-out stage of Sec. 4.2:
+                                the explicit factors compressed from the middle level
+                                outward (eqs. KeqUCMRV, GC, HR) to blocks of rank
+                                ibf_options.rank by truncated SVDs, applied like the
+                                explicit form.  FP64 (IBF_C128), d = 1, r <= 12.
+                                The sweep-in stage (Sec. 4.3, for nonuniform points)
+                                is not part of it.                                    */
 };
 
 /* Optional plan parameters; zero-initialise and set what you need. */
@@ -100,6 +107,8 @@ typedef struct ibf_options {
                               (1..10); <= 0 lets the autotuner choose              */
     int rhs_tile;          /* structured form: right-hand sides per CTA (1..64,
                               power of two); <= 0 lets the autotuner choose        */
+    int rank;              /* optimal form: rank r0 of every compressed block,
+                              1..r (the paper's r0); ignored by the other forms    */
 } ibf_options;
 
 /*
@@ -297,7 +306,9 @@ enum ibf_query {
     IBF_Q_NNZ = 9,             /* entries of the explicit factors (complex)       */
     IBF_Q_LAUNCHES = 10,       /* kernels one apply of one slice launches         */
     IBF_Q_LEVELS_PER_LAUNCH = 11,
-    IBF_Q_RHS_TILE = 12
+    IBF_Q_RHS_TILE = 12,
+    IBF_Q_RANK = 13            /* block rank the apply uses: r0 for the optimal
+                                  form, r otherwise                               */
 };
 int ibf_plan_query(const ibf_plan* plan, int what, int64_t* value);
 

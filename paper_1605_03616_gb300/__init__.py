@@ -29,9 +29,10 @@ C64_BF16X3 = 2
 FORM_AUTO = 0
 FORM_EXPLICIT = 1
 FORM_STRUCTURED = 2
+FORM_OPTIMAL = 3
 
 Q_N, Q_L, Q_H, Q_R, Q_DTYPE, Q_FORM, Q_FACTOR_BYTES, Q_WORKSPACE_BYTES, Q_MAX_NRHS, Q_NNZ, Q_LAUNCHES, \
-    Q_LEVELS_PER_LAUNCH, Q_RHS_TILE = range(13)
+    Q_LEVELS_PER_LAUNCH, Q_RHS_TILE, Q_RANK = range(14)
 
 STATUS = {0: "IBF_OK", 1: "IBF_ERR_INVALID", 2: "IBF_ERR_OOM", 3: "IBF_ERR_CUDA", 4: "IBF_ERR_UNSUPPORTED",
           5: "IBF_ERR_TIMEOUT"}
@@ -56,7 +57,7 @@ class IBFError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int), ("h", ctypes.c_int), ("max_nrhs", ctypes.c_int),
-                ("levels_per_launch", ctypes.c_int), ("rhs_tile", ctypes.c_int)]
+                ("levels_per_launch", ctypes.c_int), ("rhs_tile", ctypes.c_int), ("rank", ctypes.c_int)]
 
 
 _lib = None
@@ -125,14 +126,14 @@ class Plan:
 
     def __init__(self, phase: int, N: int, r: int = 9, dtype: int = C64_FP32, x=None, d: int = 1,
                  form: int = FORM_AUTO, h: int = 0, max_nrhs: int = 0, levels_per_launch: int = 0,
-                 rhs_tile: int = 0):
+                 rhs_tile: int = 0, rank: int = 0):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("the IBF library runs on a CUDA GPU only; none is available")
         torch.cuda.init()
         self._lib = load_library()
         self.N, self.r, self.dtype, self.phase = int(N), int(r), int(dtype), int(phase)
-        opt = Options(form, h, max_nrhs, levels_per_launch, rhs_tile)
+        opt = Options(form, h, max_nrhs, levels_per_launch, rhs_tile, rank)
         xa = None
         if x is not None:
             xa = np.ascontiguousarray(x, dtype=np.float64)

@@ -30,6 +30,7 @@ UNITS = {
     "ibf_batch.cu": [],
     "ibf_2d_build.cu": ["-fmad=false"],
     "ibf_2d_apply.cu": [],
+    "ibf_optimal.cu": [],
 }
 
 

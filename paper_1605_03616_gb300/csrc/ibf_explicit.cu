@@ -139,7 +139,7 @@ int explicit_launches(const ibf_plan* p) { return p->L + 3; }
 
 int explicit_apply(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStream_t st)
 {
-    const int r = p->r, L = p->L;
+    const int r = p->ra > 0 ? p->ra : p->r, L = p->L;   // r0 for the optimal form
     const int64_t N = p->N;
     for (int c0 = 0; c0 < nrhs; c0 += p->max_nrhs) {
         int nc = std::min(p->max_nrhs, nrhs - c0);
@@ -170,7 +170,7 @@ int explicit_apply(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStream_t
 
 int explicit_adjoint(ibf_plan* p, const void* yv, void* gv, int nrhs, cudaStream_t st)
 {
-    const int r = p->r, L = p->L;
+    const int r = p->ra > 0 ? p->ra : p->r, L = p->L;   // r0 for the optimal form
     const int64_t N = p->N;
     for (int c0 = 0; c0 < nrhs; c0 += p->max_nrhs) {
         int nc = std::min(p->max_nrhs, nrhs - c0);

@@ -27,6 +27,7 @@ struct ibf_plan {
     int64_t N = 0, nx = 0;
     int max_nrhs = 0;
     int kfuse = 0, rtile = 0;   // structured form launch shape
+    int ra = 0;                 // optimal form: rank r0 of the compressed blocks (0: r)
     bool user_kfuse = false, user_rtile = false;
 
     // Chebyshev grid on [-1/2,1/2] and the two child-to-parent Lagrange
@@ -89,6 +90,11 @@ void prof_mark(ibf_plan* p, cudaStream_t s, int kind);
 // construction (ibf_plan.cu)
 int build_explicit(ibf_plan* p);
 int build_structured(ibf_plan* p);
+
+// optimal form (ibf_optimal.cu): compress the explicit factors to rank r0;
+// alloc returns device memory owned by the plan (nullptr on failure), release
+// frees one such block
+int compress_optimal(ibf_plan* p, int r0, void* (*alloc)(ibf_plan*, size_t), void (*release)(ibf_plan*, void*));
 
 // explicit-form apply (ibf_explicit.cu), FP64
 int explicit_apply(ibf_plan* p, const void* g, void* u, int nrhs, cudaStream_t s);

@@ -278,6 +278,20 @@ static int dalloc(ibf_plan* p, void** ptr, size_t bytes, bool factor)
 
 static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
+static void* opt_alloc(ibf_plan* p, size_t bytes)
+{
+    void* q = nullptr;
+    return dalloc(p, &q, bytes, true) ? nullptr : q;
+}
+
+static void opt_release(ibf_plan* p, void* q)
+{
+    auto it = std::find(p->allocations.begin(), p->allocations.end(), q);
+    if (it == p->allocations.end()) return;
+    cudaFree(q);
+    p->allocations.erase(it);
+}
+
 int build_explicit(ibf_plan* p)
 {
     const Geo G = make_geo(p);
@@ -418,7 +432,8 @@ static int create_2d(int phase_id, int64_t N, int r, int dtype, const double* x,
     ibf_options o;
     memset(&o, 0, sizeof(o));
     if (opt) o = *opt;
-    if (o.form == IBF_FORM_EXPLICIT) return set_error(IBF_ERR_UNSUPPORTED, "2D: structured form only");
+    if (o.form == IBF_FORM_EXPLICIT || o.form == IBF_FORM_OPTIMAL)
+        return set_error(IBF_ERR_UNSUPPORTED, "2D: structured form only");
     ibf_plan* p = new ibf_plan();
     p->phase_id = phase_id;
     p->d = 2;
@@ -475,7 +490,13 @@ extern "C" int ibf_plan_create_ex(int phase_id, int d, int64_t N, int r, int dty
     memset(&o, 0, sizeof(o));
     if (opt) o = *opt;
     int form = o.form == IBF_FORM_AUTO ? (dtype == IBF_C128 ? IBF_FORM_EXPLICIT : IBF_FORM_STRUCTURED) : o.form;
-    if (form != IBF_FORM_EXPLICIT && form != IBF_FORM_STRUCTURED) return set_error(IBF_ERR_INVALID, "unknown form");
+    if (form != IBF_FORM_EXPLICIT && form != IBF_FORM_STRUCTURED && form != IBF_FORM_OPTIMAL)
+        return set_error(IBF_ERR_INVALID, "unknown form");
+    if (form == IBF_FORM_OPTIMAL) {
+        if (dtype != IBF_C128) return set_error(IBF_ERR_UNSUPPORTED, "the optimal form is FP64 (IBF_C128) only");
+        if (r > 12) return set_error(IBF_ERR_UNSUPPORTED, "the optimal form supports r <= 12");
+        if (o.rank < 1 || o.rank > r) return set_error(IBF_ERR_INVALID, "optimal form: rank must be in [1, r]");
+    }
     if (form == IBF_FORM_EXPLICIT && dtype != IBF_C128)
         return set_error(IBF_ERR_UNSUPPORTED, "the explicit form is FP64 (IBF_C128) only");
     if (dtype == IBF_C64_BF16X3)
@@ -522,7 +543,7 @@ extern "C" int ibf_plan_create_ex(int phase_id, int d, int64_t N, int r, int dty
     p->h = h;
     p->N = N;
     p->nx = N;
-    p->max_nrhs = o.max_nrhs > 0 ? o.max_nrhs : (form == IBF_FORM_EXPLICIT ? 8 : 64);
+    p->max_nrhs = o.max_nrhs > 0 ? o.max_nrhs : (form == IBF_FORM_STRUCTURED ? 64 : 8);
     p->kfuse = o.levels_per_launch;
     p->rtile = o.rhs_tile;
     p->user_kfuse = o.levels_per_launch > 0;
@@ -547,7 +568,11 @@ extern "C" int ibf_plan_create_ex(int phase_id, int d, int64_t N, int r, int dty
     cudaMemcpy(p->d_off, off.data(), sizeof(int32_t) * (N + 1), cudaMemcpyHostToDevice);
     cudaMemcpy(p->d_leaf, leaf.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice);
 
-    rc = form == IBF_FORM_EXPLICIT ? build_explicit(p) : build_structured(p);
+    rc = form == IBF_FORM_STRUCTURED ? build_structured(p) : build_explicit(p);
+    if (!rc && form == IBF_FORM_OPTIMAL) {
+        rc = compress_optimal(p, o.rank, opt_alloc, opt_release);
+        if (!rc) p->factor_bytes = sizeof(double2) * (size_t)p->nnz;
+    }
     if (rc) {
         free_plan(p);
         return rc;
@@ -598,7 +623,7 @@ extern "C" int ibf_apply(ibf_plan* p, const void* g, void* u, int nrhs, ibf_stre
     int rc = check_apply(p, g, u, nrhs);
     if (rc) return rc;
     if (p->d == 2) return apply_2d(p, g, u, nrhs, (cudaStream_t)stream);
-    if (p->form == IBF_FORM_EXPLICIT) return explicit_apply(p, g, u, nrhs, (cudaStream_t)stream);
+    if (p->form != IBF_FORM_STRUCTURED) return explicit_apply(p, g, u, nrhs, (cudaStream_t)stream);
     return fused_apply(p, g, u, nrhs, false, (cudaStream_t)stream);
 }
 
@@ -607,7 +632,7 @@ extern "C" int ibf_apply_adjoint(ibf_plan* p, const void* y, void* g, int nrhs, 
     int rc = check_apply(p, y, g, nrhs);
     if (rc) return rc;
     if (p->d == 2) return set_error(IBF_ERR_UNSUPPORTED, "2D plans have no adjoint apply");
-    if (p->form == IBF_FORM_EXPLICIT) return explicit_adjoint(p, y, g, nrhs, (cudaStream_t)stream);
+    if (p->form != IBF_FORM_STRUCTURED) return explicit_adjoint(p, y, g, nrhs, (cudaStream_t)stream);
     return fused_apply(p, y, g, nrhs, true, (cudaStream_t)stream);
 }
 
@@ -750,10 +775,11 @@ extern "C" int ibf_plan_query(const ibf_plan* p, int what, int64_t* v)
     case IBF_Q_MAX_NRHS: *v = p->max_nrhs; break;
     case IBF_Q_NNZ: *v = p->nnz; break;
     case IBF_Q_LAUNCHES:
-        *v = p->d == 2 ? launches_2d(p) : (p->form == IBF_FORM_EXPLICIT ? explicit_launches(p) : fused_launches(p));
+        *v = p->d == 2 ? launches_2d(p) : (p->form != IBF_FORM_STRUCTURED ? explicit_launches(p) : fused_launches(p));
         break;
     case IBF_Q_LEVELS_PER_LAUNCH: *v = p->kfuse; break;
     case IBF_Q_RHS_TILE: *v = p->rtile; break;
+    case IBF_Q_RANK: *v = p->ra > 0 ? p->ra : p->r; break;
     default: return set_error(IBF_ERR_INVALID, "unknown query");
     }
     return IBF_OK;

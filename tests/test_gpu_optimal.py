@@ -1,0 +1,79 @@
+"""GPU optimal IBF (sweep-out stage of Sec. 4.2, FP64): the compression on
+the GPU (one-sided Jacobi SVDs) against the oracle's compression (LAPACK
+SVDs) on the same preliminary factors.  A rank-r0 truncation is unique when
+the r0-th and (r0+1)-th singular values differ, so both must give the same
+operator to rounding; at full rank both equal the preliminary IBF, and for a
+separable phase rank one is exact.
+
+Tolerance: 1e-10, or 1e-3 of the compression's own effect (optimal vs
+preliminary) when that is larger.  All cuts here have a gap of at least 2
+between the r0-th and (r0+1)-th singular values, but at r = 12 the cut lies
+near rounding level (sigma_{r0+1} / sigma_1 ~ 1e-13), where any normwise
+stable SVD fixes the smallest kept directions only to about
+eps sigma_1 / sigma_r0: two LAPACK drivers then differ by 3e-11 and the
+Jacobi SVD by 3e-9, against a compression effect of 1.7e-5."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from oracle.optimal import OptimalIBF
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ibf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1605_03616_gb300 as m
+    return m
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a).astype(np.complex128)).cuda()
+
+
+@pytest.mark.parametrize("phase,N,r,r0,nrhs", [
+    (O.PHASE_FIO1D, 256, 9, 9, 2),        # full rank: the preliminary IBF itself
+    (O.PHASE_FIO1D, 1024, 9, 6, 2),
+    (O.PHASE_NUFFT, 1024, 9, 5, 3),       # random points: leaves with 0, 1, several points
+    (O.PHASE_FIO1D, 2048, 12, 9, 1),      # odd L
+    (O.PHASE_SEPARABLE, 512, 7, 1, 2),    # rank one is exact
+])
+def test_optimal_matches_oracle(ibf, phase, N, r, r0, nrhs):
+    x = W.random_sorted_x(N, W.rng(960)) if phase == O.PHASE_NUFFT else W.uniform_x(N)
+    g = W.complex_normal((N, nrhs), W.rng(961))
+    y = W.complex_normal((N, nrhs), W.rng(962))
+    plan = ibf.Plan(phase, N, r, ibf.C128, x=x if phase == O.PHASE_NUFFT else None, form=ibf.FORM_OPTIMAL, rank=r0)
+    assert plan.query(ibf.Q_RANK) == r0 and plan.query(ibf.Q_FORM) == ibf.FORM_OPTIMAL
+    u = plan.apply(_dev(g)).cpu().numpy()
+    ga = plan.adjoint(_dev(y)).cpu().numpy()
+    ref = OptimalIBF(phase, N, r, x, r0)
+    uo, go = ref.apply(g), ref.adjoint(y)
+    ef, ea = O.rel_l2(u, uo), O.rel_l2(ga, go)
+    ud = O.direct_1d(phase, x, W.omega_1d(N), g)
+    trunc = O.rel_l2(uo, O.ExplicitIBF(phase, N, r, x).apply(g))
+    tol = max(1e-10, 1e-3 * trunc)
+    print("\noptimal phase=%d N=%d r=%d r0=%d: gpu vs oracle fwd %.2e adj %.2e (tol %.1e); oracle vs direct %.2e"
+          % (phase, N, r, r0, ef, ea, tol, O.rel_l2(uo, ud)))
+    assert ef < tol
+    assert ea < tol
+    if phase == O.PHASE_SEPARABLE:
+        assert O.rel_l2(u, ud) < 1e-12
+    plan.close()
+
+
+def test_optimal_rejects_bad_options(ibf):
+    for kw, code in [(dict(dtype=ibf.C128, rank=0), 1), (dict(dtype=ibf.C128, rank=10), 1),
+                     (dict(dtype=ibf.C64_FP32, rank=4), 4)]:
+        with pytest.raises(ibf.IBFError) as e:
+            ibf.Plan(ibf.PHASE_FIO1D, 256, 9, form=ibf.FORM_OPTIMAL, **kw)
+        assert e.value.code == code
+    with pytest.raises(ibf.IBFError) as e:
+        ibf.Plan(ibf.PHASE_FIO1D, 256, 13, ibf.C128, form=ibf.FORM_OPTIMAL, rank=6)
+    assert e.value.code == 4
