@@ -187,6 +187,75 @@ def run_reference(a):
 
 
 # ------------------------------------------------------- batched workload
+def run_optimal(ibf, torch, N=1 << 16, nrhs=8, reps=3):
+    """Optimal IBF (sweep-out stage, Sec. 4.2) against the preliminary IBF,
+    FP64 explicit factors, 1D FIO N = 2^16, 8 columns: construction time,
+    apply vectors/s, stored entries, and the relative L2 difference from the
+    r = 12 preliminary IBF (itself ~7e-8 from the direct sum)."""
+    gen = W.rng(workload=6)
+    g = torch.from_numpy(W.complex_normal((N, nrhs), gen)).cuda()
+    out, ref = [], None
+    for r, form, r0 in [(12, ibf.FORM_EXPLICIT, 0), (9, ibf.FORM_EXPLICIT, 0), (12, ibf.FORM_OPTIMAL, 9),
+                        (12, ibf.FORM_OPTIMAL, 7), (9, ibf.FORM_OPTIMAL, 7)]:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p = ibf.Plan(ibf.PHASE_FIO1D, N, r, ibf.C128, form=form, rank=r0, max_nrhs=nrhs)
+        torch.cuda.synchronize()
+        tc = (time.perf_counter() - t0) * 1e3
+        u = p.apply(g)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            p.apply(g)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        if ref is None:
+            ref = u.clone()
+        rec = {"form": "optimal" if form == ibf.FORM_OPTIMAL else "preliminary", "r": r,
+               "r0": r0 or r, "construct_ms": tc, "apply_ms": ms, "vectors_per_s": nrhs / (ms / 1e3),
+               "nnz": p.query(ibf.Q_NNZ),
+               "rel_diff_vs_r12_preliminary": float(torch.linalg.vector_norm(u - ref) / torch.linalg.vector_norm(ref))}
+        out.append(rec)
+        p.close()
+    return {"workload": "1D FIO N=2^16, 8 columns complex128, explicit FP64 factors", "variants": out}
+
+
+def run_autograd(ibf, torch, N=1 << 18, nrhs=32, reps=5):
+    """Config 5: loss ||K g - y||^2 at N = 2^18, 32 columns, complex64; one
+    step = forward apply + backward (the hand-written adjoint) through
+    torch.autograd, CUDA events."""
+    from paper_1605_03616_gb300.autograd import ibf_apply
+    plan = ibf.Plan(ibf.PHASE_FIO1D, N, 9, ibf.C64_FP32, max_nrhs=nrhs)
+    gen = W.rng(workload=5)
+    g0 = torch.from_numpy(W.complex_normal((N, nrhs), gen, dtype=np.complex64)).cuda()
+    y = torch.from_numpy(W.complex_normal((N, nrhs), gen, dtype=np.complex64)).cuda()
+
+    def step():
+        g = g0.clone().requires_grad_(True)
+        loss = (ibf_apply(plan, g) - y).abs().pow(2).sum()
+        loss.backward()
+        return g.grad
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    rec = {"workload": "loss ||K g - y||^2, 1D FIO N=2^18 r=9, 32 columns complex64, forward + adjoint via autograd",
+           "ms_per_step": ms, "vectors_per_s": nrhs / (ms / 1e3)}
+    plan.close()
+    return rec
+
+
 def run_batch(ibf, torch, reps=5, count=256, seed=4):
     """256 independent 1D FIO transforms, N = 2^e with e uniform in 10..16,
     nrhs uniform in 1..64, complex64, r = 9: the batched launch captured in a
@@ -505,6 +574,13 @@ def run_gpu(a):
     if fp64 is not None:
         construction["explicit_fp64_plan_ms"] = t_expl
 
+    grad5 = None
+    if rank == 0 and not a.skip_batch:
+        grad5 = run_autograd(ibf, torch)
+    optimal = None
+    if rank == 0 and not a.skip_fp64:
+        optimal = run_optimal(ibf, torch)
+
     fio2d = None
     if rank == 0 and not a.skip_2d:
         fio2d = run_2d(ibf, torch)
@@ -517,6 +593,11 @@ def run_gpu(a):
         cpu = {"value": v, "unit": "vectors/s", "cores": cores, "kind": "oracle",
                "sample": "1 of the %d vectors (full N=2^%d, matrix-free FP64 oracle, %.1f s)" % (
                    nrhs, int(np.log2(N)), dt)}
+        # one core, on a 2^16 vector (the full size would take minutes)
+        small = argparse.Namespace(**{**vars(a), "N": 1 << 16})
+        v1, dt1 = oracle_vectors_per_s(small, 1)
+        cpu["single_core"] = {"vectors_per_s_at_N_2e16": v1, "seconds": dt1, "cores": 1}
+        oracle_vectors_per_s(small, cores)   # leave the thread count at all cores
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "vectors/s", "n_gpus": world, "steps": a.steps,
@@ -528,8 +609,8 @@ def run_gpu(a):
                            "l2": "inputs and workspace larger than L2 (no flush)",
                            "parallelism": "independent rhs batches per GPU (dp%d)" % world},
                 "clocks": clk, "e2e": e2e, "gpu_launches": a.steps * launches, "roofline": roof,
-                "fp64_plain": fp64, "construction": construction, "batch256": batch, "fio2d": fio2d,
-                "cpu_baseline": cpu}
+                "fp64_plain": fp64, "construction": construction, "batch256": batch, "autograd": grad5, "optimal_ibf": optimal,
+                "fio2d": fio2d, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:
