@@ -16,6 +16,8 @@ paper); this module compiles it with gcc and wraps it with ctypes/numpy:
 * ``ibf_apply_2d_box`` / ``mibf_apply_2d`` -- the 2D butterfly on one square
   frequency box (Sec. 5.1) and the multiscale sum over a corona
   decomposition with a directly summed centre (Sec. 5.2).
+* ``optimal.OptimalIBF`` (numpy, module ``oracle.optimal``) -- the optimal
+  IBF's sweep-out compression of the explicit factors (Sec. 4.2).
 """
 from __future__ import annotations
 
