@@ -187,6 +187,48 @@ def run_reference(a):
 
 
 # ------------------------------------------------------- batched workload
+def run_nufft_latency(ibf, torch, N=1024, reps=200):
+    """Config 1: NUFFT-type phase x xi with N = 1024 sorted iid uniform
+    points, one vector: apply latency in microseconds, FP64 explicit and FP32
+    structured, as a sequence of launches and replayed from a CUDA graph."""
+    gen = W.rng(workload=1)
+    x = W.random_sorted_x(N, gen)
+    g64 = torch.from_numpy(W.complex_normal(N, gen)).cuda()
+    out = {"workload": "NUFFT phase x*xi, N=1024 random sorted x, r=9, one vector"}
+    stream = torch.cuda.Stream()
+    for name, dtype, gv in [("fp64_explicit", ibf.C128, g64), ("fp32_structured", ibf.C64_FP32,
+                                                               g64.to(torch.complex64))]:
+        p = ibf.Plan(ibf.PHASE_NUFFT, N, 9, dtype, x=x, max_nrhs=1)
+        u = torch.empty_like(gv)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            for _ in range(10):
+                p.apply_raw(gv.data_ptr(), u.data_ptr(), 1, stream.cuda_stream)
+            e0.record(stream)
+            for _ in range(reps):
+                p.apply_raw(gv.data_ptr(), u.data_ptr(), 1, stream.cuda_stream)
+            e1.record(stream)
+        stream.synchronize()
+        t_launch = e0.elapsed_time(e1) / reps * 1e3
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            p.apply_raw(gv.data_ptr(), u.data_ptr(), 1, stream.cuda_stream)
+        for _ in range(10):
+            graph.replay()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = {"us_per_apply": t_launch, "us_per_apply_graph": e0.elapsed_time(e1) / reps * 1e3,
+                     "launches": p.query(ibf.Q_LAUNCHES)}
+        del graph
+        p.close()
+    return out
+
+
 def run_optimal(ibf, torch, N=1 << 16, nrhs=8, reps=3):
     """Optimal IBF (sweep-out stage, Sec. 4.2) against the preliminary IBF,
     FP64 explicit factors, 1D FIO N = 2^16, 8 columns: construction time,
@@ -577,9 +619,10 @@ def run_gpu(a):
     grad5 = None
     if rank == 0 and not a.skip_batch:
         grad5 = run_autograd(ibf, torch)
-    optimal = None
+    optimal = nufft = None
     if rank == 0 and not a.skip_fp64:
         optimal = run_optimal(ibf, torch)
+        nufft = run_nufft_latency(ibf, torch)
 
     fio2d = None
     if rank == 0 and not a.skip_2d:
@@ -609,7 +652,7 @@ def run_gpu(a):
                            "l2": "inputs and workspace larger than L2 (no flush)",
                            "parallelism": "independent rhs batches per GPU (dp%d)" % world},
                 "clocks": clk, "e2e": e2e, "gpu_launches": a.steps * launches, "roofline": roof,
-                "fp64_plain": fp64, "construction": construction, "batch256": batch, "autograd": grad5, "optimal_ibf": optimal,
+                "fp64_plain": fp64, "construction": construction, "batch256": batch, "autograd": grad5, "optimal_ibf": optimal, "nufft1024_latency": nufft,
                 "fio2d": fio2d, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     plan.close()
