@@ -15,7 +15,8 @@ paper); this module compiles it with gcc and wraps it with ctypes/numpy:
   M^h, G^l, U^L (Sec. 3, eqs. PIBF1-PIBF3, switchlocM, PIBFbf3).
 * ``ibf_apply_2d_box`` / ``mibf_apply_2d`` -- the 2D butterfly on one square
   frequency box (Sec. 5.1) and the multiscale sum over a corona
-  decomposition with a directly summed centre (Sec. 5.2).
+  decomposition with a directly summed centre (Sec. 5.2); with
+  ``ibf_adjoint_2d_box`` / ``mibf_adjoint_2d``, their conjugate transposes.
 * ``optimal.OptimalIBF`` (numpy, module ``oracle.optimal``) -- the optimal
   IBF's sweep-out compression of the explicit factors (Sec. 4.2).
 """
@@ -78,6 +79,8 @@ def _load():
         D = ctypes.c_double
         lib.orc_ibf_apply_2d.argtypes = [Ci, I64, Ci, Ci, I64, P, D, D, P, Ci, P]
         lib.orc_mibf_apply_2d.argtypes = [Ci, I64, Ci, Ci, I64, P, P, Ci, P]
+        lib.orc_ibf_adjoint_2d.argtypes = [Ci, I64, Ci, Ci, I64, P, D, D, P, Ci, P]
+        lib.orc_mibf_adjoint_2d.argtypes = [Ci, I64, Ci, Ci, I64, P, P, Ci, P]
         _lib = lib
     return _lib
 
@@ -215,6 +218,31 @@ def mibf_apply_2d(phase_id: int, n: int, r: int, x, g, center_side: int = 16):
     if rc:
         raise ValueError("orc_mibf_apply_2d failed (%d)" % rc)
     return _uncols(u, x.shape[0], nrhs, vec)
+
+
+def ibf_adjoint_2d_box(phase_id: int, m: int, r: int, x, q1: float, q2: float, y, h: int | None = None):
+    """Adjoint of ibf_apply_2d_box: g = K_Q^* y, y of shape (nx,) or (nx, nrhs)."""
+    L = int(m).bit_length() - 1
+    h = L // 2 if h is None else h
+    x = _f64(x).reshape(-1, 2)
+    yb, nrhs, vec = _cols(y, x.shape[0])
+    g = np.zeros(m * m * nrhs, np.complex128)
+    rc = _load().orc_ibf_adjoint_2d(phase_id, m, r, h, x.shape[0], _ptr(x), float(q1), float(q2), _ptr(yb), nrhs,
+                                    _ptr(g))
+    if rc:
+        raise ValueError("orc_ibf_adjoint_2d failed (%d)" % rc)
+    return _uncols(g, m * m, nrhs, vec)
+
+
+def mibf_adjoint_2d(phase_id: int, n: int, r: int, x, y, center_side: int = 16):
+    """Adjoint of mibf_apply_2d: g = K^* y on the n x n frequency grid."""
+    x = _f64(x).reshape(-1, 2)
+    yb, nrhs, vec = _cols(y, x.shape[0])
+    g = np.zeros(n * n * nrhs, np.complex128)
+    rc = _load().orc_mibf_adjoint_2d(phase_id, n, r, center_side, x.shape[0], _ptr(x), _ptr(yb), nrhs, _ptr(g))
+    if rc:
+        raise ValueError("orc_mibf_adjoint_2d failed (%d)" % rc)
+    return _uncols(g, n * n, nrhs, vec)
 
 
 class ExplicitIBF:

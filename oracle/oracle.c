@@ -931,6 +931,156 @@ int orc_ibf_apply_2d(int phase_id, int64_t m, int r, int h, int64_t nx, const do
     return 0;
 }
 
+/* Adjoint of orc_ibf_apply_2d: g = K_Q^* y, the conjugate transpose of each
+   step of the 2D butterfly in reverse order (termination, recursion in x,
+   switch, recursion in xi, initialization).  Each level's adjoint gathers,
+   for input pair (ip, C) of level l-1, from the four output pairs
+   (child a of ip, parent of C) of level l that read it. */
+int orc_ibf_adjoint_2d(int phase_id, int64_t m, int r, int h, int64_t nx, const double* x, double q1, double q2,
+                       const cplx* y, int nrhs, cplx* g)
+{
+    int L = ilog2(m);
+    if (((int64_t)1 << L) != m || r < 2 || r > 16 || h < 0 || h > L) return 1;
+    double z[64];
+    orc_cheb_grid(r, z);
+    bf2 B = {phase_id, r, L, q1, q2, (double)m, z};
+    const int r2 = r * r;
+    const int64_t npair = (int64_t)1 << (2 * L);
+    cplx* a = (cplx*)malloc(sizeof(cplx) * npair * r2);
+    cplx* b = (cplx*)malloc(sizeof(cplx) * npair * r2);
+    if (!a || !b) { free(a); free(b); return 2; }
+    for (int col = 0; col < nrhs; ++col) {
+        const cplx* yc = y + nx * col;
+        /* termination^*: a[i][t] = sum over points n of leaf i */
+        {
+            double cQ1 = q1 + 0.5 * (double)m, cQ2 = q2 + 0.5 * (double)m;
+            int64_t nl = (int64_t)1 << L;
+            memset(a, 0, sizeof(cplx) * npair * r2);
+            for (int64_t n = 0; n < nx; ++n) {
+                double x1 = x[2 * n], x2 = x[2 * n + 1];
+                int64_t i1 = (int64_t)floor(x1 * (double)nl), i2 = (int64_t)floor(x2 * (double)nl);
+                if (i1 >= nl) i1 = nl - 1;
+                if (i2 >= nl) i2 = nl - 1;
+                if (i1 < 0) i1 = 0;
+                if (i2 < 0) i2 = 0;
+                int64_t i = i1 * nl + i2;
+                double cA1, cA2, wA;
+                xbox2(L, i, &cA1, &cA2, &wA);
+                cplx v = conj(e2pi(phi2(&B, x1, x2, cQ1, cQ2))) * yc[n];
+                for (int t = 0; t < r2; ++t) {
+                    double gA1 = cA1 + wA * z[t / r], gA2 = cA2 + wA * z[t % r];
+                    a[i * r2 + t] += lag2(&B, t, (x1 - cA1) / wA, (x2 - cA2) / wA) *
+                                     conj(e2pi(-phi2(&B, gA1, gA2, cQ1, cQ2))) * v;
+                }
+            }
+        }
+        /* recursion in x^*, l = L..h+1 */
+        for (int l = L; l >= h + 1; --l) {
+            int64_t np = (int64_t)1 << (2 * (l - 1)), nC = (int64_t)1 << (2 * (L - l + 1)), nj = nC / 4;
+#pragma omp parallel for collapse(2) schedule(static)
+            for (int64_t ip = 0; ip < np; ++ip)
+                for (int64_t C = 0; C < nC; ++C) {
+                    int64_t j = parent2(L - l + 1, C);
+                    double cC1, cC2, wC, cP1, cP2, wP;
+                    wbox2(&B, L - l + 1, C, &cC1, &cC2, &wC);
+                    xbox2(l - 1, ip, &cP1, &cP2, &wP);
+                    for (int s = 0; s < r2; ++s) {
+                        double gP1 = cP1 + wP * z[s / r], gP2 = cP2 + wP * z[s % r];
+                        cplx acc = 0;
+                        for (int aa = 0; aa < 4; ++aa) {
+                            int64_t i = child2(l - 1, ip, aa);
+                            double cA1, cA2, wA;
+                            xbox2(l, i, &cA1, &cA2, &wA);
+                            const cplx* bp = a + (i * nj + j) * r2;
+                            for (int t = 0; t < r2; ++t) {
+                                double gA1 = cA1 + wA * z[t / r], gA2 = cA2 + wA * z[t % r];
+                                cplx coef = e2pi(phi2(&B, gA1, gA2, cC1, cC2)) *
+                                            lag2(&B, s, (gA1 - cP1) / wP, (gA2 - cP2) / wP) *
+                                            e2pi(-phi2(&B, gP1, gP2, cC1, cC2));
+                                acc += conj(coef) * bp[t];
+                            }
+                        }
+                        b[(ip * nC + C) * r2 + s] = acc;
+                    }
+                }
+            cplx* tmp = a; a = b; b = tmp;
+        }
+        /* switch^* */
+        {
+            int64_t ni = (int64_t)1 << (2 * h), nj = (int64_t)1 << (2 * (L - h));
+#pragma omp parallel for collapse(2) schedule(static)
+            for (int64_t i = 0; i < ni; ++i)
+                for (int64_t j = 0; j < nj; ++j) {
+                    double cA1, cA2, wA, cB1, cB2, wB;
+                    xbox2(h, i, &cA1, &cA2, &wA);
+                    wbox2(&B, L - h, j, &cB1, &cB2, &wB);
+                    for (int s = 0; s < r2; ++s) {
+                        double gB1 = cB1 + wB * z[s / r], gB2 = cB2 + wB * z[s % r];
+                        cplx acc = 0;
+                        for (int t = 0; t < r2; ++t)
+                            acc += conj(e2pi(phi2(&B, cA1 + wA * z[t / r], cA2 + wA * z[t % r], gB1, gB2))) *
+                                   a[(i * nj + j) * r2 + t];
+                        b[(i * nj + j) * r2 + s] = acc;
+                    }
+                }
+            cplx* tmp = a; a = b; b = tmp;
+        }
+        /* recursion in xi^*, l = h..1 */
+        for (int l = h; l >= 1; --l) {
+            int64_t np = (int64_t)1 << (2 * (l - 1)), nC = (int64_t)1 << (2 * (L - l + 1)), nj = nC / 4;
+#pragma omp parallel for collapse(2) schedule(static)
+            for (int64_t ip = 0; ip < np; ++ip)
+                for (int64_t C = 0; C < nC; ++C) {
+                    int64_t j = parent2(L - l + 1, C);
+                    double cC1, cC2, wC, cB1, cB2, wB;
+                    wbox2(&B, L - l + 1, C, &cC1, &cC2, &wC);
+                    wbox2(&B, L - l, j, &cB1, &cB2, &wB);
+                    for (int s = 0; s < r2; ++s) {
+                        double gC1 = cC1 + wC * z[s / r], gC2 = cC2 + wC * z[s % r];
+                        cplx acc = 0;
+                        for (int aa = 0; aa < 4; ++aa) {
+                            int64_t i = child2(l - 1, ip, aa);
+                            double cA1, cA2, wA;
+                            xbox2(l, i, &cA1, &cA2, &wA);
+                            const cplx* bp = a + (i * nj + j) * r2;
+                            for (int t = 0; t < r2; ++t) {
+                                double gB1 = cB1 + wB * z[t / r], gB2 = cB2 + wB * z[t % r];
+                                cplx coef = e2pi(-phi2(&B, cA1, cA2, gB1, gB2)) *
+                                            lag2(&B, t, (gC1 - cB1) / wB, (gC2 - cB2) / wB) *
+                                            e2pi(phi2(&B, cA1, cA2, gC1, gC2));
+                                acc += conj(coef) * bp[t];
+                            }
+                        }
+                        b[(ip * nC + C) * r2 + s] = acc;
+                    }
+                }
+            cplx* tmp = a; a = b; b = tmp;
+        }
+        /* initialization^* */
+        {
+            double cA1, cA2, wA;
+            xbox2(0, 0, &cA1, &cA2, &wA);
+            for (int64_t j = 0; j < npair; ++j) {
+                double cB1, cB2, wB;
+                wbox2(&B, L, j, &cB1, &cB2, &wB);
+                int64_t j1 = j >> L, j2 = j & (((int64_t)1 << L) - 1);
+                double k1 = q1 + (double)j1, k2 = q2 + (double)j2;
+                cplx acc = 0;
+                for (int t = 0; t < r2; ++t) {
+                    double gB1 = cB1 + wB * z[t / r], gB2 = cB2 + wB * z[t % r];
+                    cplx coef = e2pi(-phi2(&B, cA1, cA2, gB1, gB2)) * lag2(&B, t, (k1 - cB1) / wB, (k2 - cB2) / wB) *
+                                e2pi(phi2(&B, cA1, cA2, k1, k2));
+                    acc += conj(coef) * a[j * r2 + t];
+                }
+                g[j1 * m + j2 + m * m * col] = acc;
+            }
+        }
+    }
+    free(a);
+    free(b);
+    return 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* Multiscale IBF (Sec. 5.2, eqs. domaindecomp, mba, f1) on the n x n    */
 /* frequency grid xi = (k1 - n/2, k2 - n/2).  Corona decomposition with  */
@@ -993,5 +1143,58 @@ int orc_mibf_apply_2d(int phase_id, int64_t n, int r, int center_side, int64_t n
             }
     }
     free(tmp);
+    return 0;
+}
+
+/* Adjoint of orc_mibf_apply_2d: g = K^* y.  The corona boxes and the centre
+   partition the frequency grid, so each writes its own part of g: the box
+   adjoints (orc_ibf_adjoint_2d) and the direct adjoint sum on the centre. */
+int orc_mibf_adjoint_2d(int phase_id, int64_t n, int r, int center_side, int64_t nx, const double* x, const cplx* y,
+                        int nrhs, cplx* g)
+{
+    if (n < 4 || (n & (n - 1)) || center_side < 1 || center_side > n || (center_side & (center_side - 1)))
+        return 1;
+    int64_t nn = n * n;
+    memset(g, 0, sizeof(cplx) * nn * nrhs);
+    int64_t side = n;
+    while (side > center_side) {
+        int64_t m = side / 4;
+        if (m < 1) break;
+        double s0 = -0.5 * (double)side;
+        int L = ilog2(m);
+        cplx* gq = (cplx*)malloc(sizeof(cplx) * m * m);
+        for (int b1 = 0; b1 < 4; ++b1)
+            for (int b2 = 0; b2 < 4; ++b2) {
+                if (b1 >= 1 && b1 <= 2 && b2 >= 1 && b2 <= 2) continue;
+                double q1 = s0 + (double)(b1 * m), q2 = s0 + (double)(b2 * m);
+                for (int col = 0; col < nrhs; ++col) {
+                    int rc = orc_ibf_adjoint_2d(phase_id, m, r, (L + 1) / 2, nx, x, q1, q2, y + nx * col, 1, gq);
+                    if (rc) { free(gq); return rc; }
+                    for (int64_t k1 = 0; k1 < m; ++k1)
+                        for (int64_t k2 = 0; k2 < m; ++k2) {
+                            int64_t a1 = (int64_t)(q1 + (double)k1 + 0.5 * (double)n);
+                            int64_t a2 = (int64_t)(q2 + (double)k2 + 0.5 * (double)n);
+                            g[(a1 * n + a2) + nn * col] = gq[k1 * m + k2];
+                        }
+                }
+            }
+        free(gq);
+        side /= 2;
+    }
+    {
+        double s0 = -0.5 * (double)side;
+#pragma omp parallel for collapse(2) schedule(static)
+        for (int64_t k1 = 0; k1 < side; ++k1)
+            for (int64_t k2 = 0; k2 < side; ++k2) {
+                double xi1 = s0 + (double)k1, xi2 = s0 + (double)k2;
+                int64_t a1 = (int64_t)(xi1 + 0.5 * (double)n), a2 = (int64_t)(xi2 + 0.5 * (double)n);
+                for (int col = 0; col < nrhs; ++col) {
+                    cplx acc = 0;
+                    for (int64_t p = 0; p < nx; ++p)
+                        acc += conj(e2pi(orc_phi_2d(phase_id, x[2 * p], x[2 * p + 1], xi1, xi2))) * y[p + nx * col];
+                    g[a1 * n + a2 + nn * col] = acc;
+                }
+            }
+    }
     return 0;
 }
