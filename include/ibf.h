@@ -165,7 +165,10 @@ int ibf_apply(ibf_plan* plan, const void* g, void* u, int nrhs, ibf_stream_t str
 /*
  * ibf_apply_adjoint -- g = K^* y, the conjugate-transposed factors in reverse
  * order: V^0 H^1 ... H^h (M^h)^* (G^h)^* ... (G^{L-1})^* (U^L)^*.  The paper
- * gives only the forward product (Sec. 3); this is its exact adjoint.
+ * gives only the forward product (Sec. 3); this is its exact adjoint.  For a
+ * 2D plan it is the adjoint of the multiscale sum (Sec. 5.2): the direct
+ * centre sum transposed, and per corona box its butterfly steps transposed,
+ * each box writing its own frequencies of g.
  *   y : device array N x nrhs (rows in the caller's x order).
  *   g : device array N x nrhs (rows xi_k).  Overwritten.
  * Same layout, alignment and stream rules as ibf_apply.

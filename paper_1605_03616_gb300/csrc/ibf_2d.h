@@ -35,6 +35,7 @@ struct Plan2D {
 
 int build_2d(ibf_plan* p);
 int apply_2d(ibf_plan* p, const void* g, void* u, int nrhs, cudaStream_t st);
+int apply_2d_adjoint(ibf_plan* p, const void* y, void* g, int nrhs, cudaStream_t st);
 int launches_2d(const ibf_plan* p);
 
 }  // namespace ibf

@@ -46,6 +46,13 @@ __device__ __forceinline__ void addc(C& a, C b)
     a.x += b.x;
     a.y += b.y;
 }
+// a b, or conj(a) b when CONJ
+template <bool CONJ, typename C>
+__device__ __forceinline__ C mulcx(C a, C b)
+{
+    if (CONJ) a.y = -a.y;
+    return mulc(a, b);
+}
 // acc += a b as a chain of four fused multiply-adds
 template <typename C>
 __device__ __forceinline__ void cmac(C& acc, C a, C b)
@@ -54,6 +61,12 @@ __device__ __forceinline__ void cmac(C& acc, C a, C b)
     acc.x = fma(-a.y, b.y, acc.x);
     acc.y = fma(a.x, b.y, acc.y);
     acc.y = fma(a.y, b.x, acc.y);
+}
+template <bool CONJ, typename C>
+__device__ __forceinline__ void cmacx(C& acc, C a, C b)
+{
+    if (CONJ) a.y = -a.y;
+    cmac(acc, a, b);
 }
 // Two-lane arithmetic on (re, im) pairs: packed FP32 instructions in single
 // precision (one issue slot for both lanes), per-component operations in
@@ -165,14 +178,25 @@ __device__ __forceinline__ void cp_async_cx(double2* dst, const double2* src, bo
 }
 
 // Shared prologue of both level kernels: the CTA's unit and rhs tile, its
-// four input blocks X[c][s][col] and all sixteen diagonals D[a][c][s].
-template <typename Real, int RP>
+// four input blocks X[ki][s][col] and all sixteen diagonals, staged as
+// Ds[ko][ki][s] for kernel output ko and kernel input ki.  Forward
+// (ADJ = false) the inputs are the unit's four pairs (ip, child c of j) of
+// level l-1 and the outputs its four pairs (child a of ip, j) of level l,
+// Ds[a][c] = D_{a,c}.  The adjoint runs the other way: inputs the level-l
+// pairs (child a of ip, j), outputs the level-(l-1) pairs (ip, child c of j),
+// Ds[c][a] = D_{a,c}, conjugated by the kernels when they use it.
+template <typename Real, int RP, bool ADJ = false>
 struct LevelTile {
     typedef typename C2D<Real>::T cx;
     static constexpr int R2 = RP * RP;
     int64_t ip, j, nj;
-    int col0, ncol;
+    int col0, ncol, Lq, l;
     cx* outb;
+    // pair index of kernel output ko (the block start is its R2 nc elements)
+    __device__ int64_t out_pair(int ko) const
+    {
+        return ADJ ? ip * nj * 4 + child2s(Lq - l, j, ko) : child2s(l - 1, ip, ko) * nj + j;
+    }
     // With g0 != nullptr (level 1) the inputs are Lambda^0 = V' g formed here
     // from the box's V table and g, instead of read from the workspace.
     __device__ void stage(const RingArgs& A, int l, const cx* D, const cx* in, cx* out, int rt, int lrt, cx* X,
@@ -185,6 +209,8 @@ struct LevelTile {
         const int b = (int)(blockIdx.x / (ntile * units));
         col0 = tile << lrt;
         ncol = min(rt, A.nc - col0);
+        Lq = A.Lq;
+        this->l = l;
         const int ql = 2 * (A.Lq - l);
         nj = 1LL << ql;
         ip = u >> ql;
@@ -214,7 +240,8 @@ struct LevelTile {
         } else {
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                const cx* src = inb + (ip * nC + child2s(A.Lq - l, j, c)) * R2 * A.nc;
+                const int64_t pin = ADJ ? child2s(l - 1, ip, c) * nj + j : ip * nC + child2s(A.Lq - l, j, c);
+                const cx* src = inb + pin * R2 * A.nc;
                 for (int sidx = srow; sidx < R2; sidx += sstep)
                     cp_async_cx(X + (c * R2 + sidx) * rt + cl, cl < ncol ? src + (int64_t)sidx * A.nc + cl : src,
                                 cl < ncol);
@@ -222,8 +249,8 @@ struct LevelTile {
         }
         for (int e = threadIdx.x; e < 16 * R2; e += blockDim.x) {
             const int ac = e / R2, sidx = e - ac * R2;
-            cp_async_cx(Ds + e, Db + (child2s(l - 1, ip, ac >> 2) * nC + child2s(A.Lq - l, j, ac & 3)) * R2 + sidx,
-                        true);
+            const int a = ADJ ? (ac & 3) : (ac >> 2), c = ADJ ? (ac >> 2) : (ac & 3);
+            cp_async_cx(Ds + e, Db + (child2s(l - 1, ip, a) * nC + child2s(A.Lq - l, j, c)) * R2 + sidx, true);
         }
         asm volatile("cp.async.commit_group;\n" ::);
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -247,7 +274,7 @@ constexpr int k2_level_blocks() { return sizeof(Real) == 8 ? 1 : (RP > 7 ? 2 : 3
 //   W_{c1}[s1][.] = P T_0 (Y_{c1,0}[s1] + J Y_{c1,1}[s1]) + Q T_0 (Y_{c1,0}[s1] - J Y_{c1,1}[s1]),
 //   Y_c = D_{a,c} * X_c, then the same over s1 for c1 = 0, 1.  Two outputs
 // per pass: 4 r rt tasks in pass 1, 2 r rt in pass 2, 2 r rt threads.
-template <typename Real, int RP>
+template <typename Real, int RP, bool ADJ>
 __global__ void __launch_bounds__(k2_level_threads<Real, RP>(), k2_level_blocks<Real, RP>())
     k2_level_h(const __grid_constant__ EO2<Real, RP> W, const RingArgs A, int l,
                const typename C2D<Real>::T* __restrict__ D, const typename C2D<Real>::T* __restrict__ in,
@@ -260,7 +287,7 @@ __global__ void __launch_bounds__(k2_level_threads<Real, RP>(), k2_level_blocks<
     cx* X = reinterpret_cast<cx*>(sraw);            // [4 c][R2][rt]
     cx* Ws = X + 4 * R2 * rt;                         // [2 a][2 c1][RP s1][RP t2][rt]
     cx* Ds = Ws + 4 * R2 * rt;                        // [4 a][4 c][R2] (+ level-1 V rows and g)
-    LevelTile<Real, RP> T;
+    LevelTile<Real, RP, ADJ> T;
     T.stage(A, l, D, in, out, rt, lrt, X, Ds, g0, V0);
     const int msk = rt - 1;
     for (int a0 = 0; a0 < 4; a0 += 2) {
@@ -281,8 +308,8 @@ __global__ void __launch_bounds__(k2_level_threads<Real, RP>(), k2_level_blocks<
             for (int t = 0; t < HQ; ++t) wo[t] = zc<cx>();
 #pragma unroll
             for (int s2 = 0; s2 < RP; ++s2) {
-                const cx y0 = mulc(d0[s2], x0[s2 * rt]);
-                const cx y1 = mulc(d1[RP - 1 - s2], x1[(RP - 1 - s2) * rt]);
+                const cx y0 = mulcx<ADJ>(d0[s2], x0[s2 * rt]);
+                const cx y1 = mulcx<ADJ>(d1[RP - 1 - s2], x1[(RP - 1 - s2) * rt]);
                 const cx pv = p2add(y0, y1), mv = p2sub(y0, y1);
 #pragma unroll
                 for (int t = 0; t < HR; ++t) we[t] = p2fma(W.PmT[s2][t], pv, we[t]);
@@ -320,8 +347,7 @@ __global__ void __launch_bounds__(k2_level_threads<Real, RP>(), k2_level_blocks<
                 for (int t = 0; t < HQ; ++t) wo[t] = p2fma(W.QmT[s1][t], mv, wo[t]);
             }
             if (cl < T.ncol) {
-                const int64_t Aa = child2s(l - 1, T.ip, a0 + ah);
-                cx* od = T.outb + ((Aa * T.nj + T.j) * R2 + t2) * A.nc + cl;
+                cx* od = T.outb + (T.out_pair(a0 + ah) * R2 + t2) * A.nc + cl;
 #pragma unroll
                 for (int t = 0; t < HQ; ++t) {
                     od[(int64_t)(t * RP) * A.nc] = p2add(we[t], wo[t]);
@@ -337,7 +363,7 @@ __global__ void __launch_bounds__(k2_level_threads<Real, RP>(), k2_level_blocks<
 // T_1^T x = J(e - f)) so the four outputs share one pass per input.  Two
 // inputs per pass 1 (2 r rt tasks); thread (a1, t1, col) keeps
 // out_{(a1,a2)}[t1][.] for a2 = 0, 1 in registers over all four inputs.
-template <typename Real, int RP>
+template <typename Real, int RP, bool ADJ>
 __global__ void __launch_bounds__(k2_level_threads<Real, RP>(), k2_level_blocks<Real, RP>())
     k2_level_g(const __grid_constant__ EO2<Real, RP> W, const RingArgs A, int l,
                const typename C2D<Real>::T* __restrict__ D, const typename C2D<Real>::T* __restrict__ in,
@@ -349,7 +375,7 @@ __global__ void __launch_bounds__(k2_level_threads<Real, RP>(), k2_level_blocks<
     cx* X = reinterpret_cast<cx*>(sraw);            // [4 c][R2][rt]
     cx* Zs = X + 4 * R2 * rt;                         // [2 ch][2 a1][RP t1][RP s2][rt]
     cx* Ds = Zs + 4 * R2 * rt;                        // [4 a][4 c][R2]
-    LevelTile<Real, RP> T;
+    LevelTile<Real, RP, ADJ> T;
     T.stage(A, l, D, in, out, rt, lrt, X, Ds);
     const int msk = rt - 1;
     const bool mine = threadIdx.x < 2 * RP * rt;
@@ -411,8 +437,8 @@ __global__ void __launch_bounds__(k2_level_threads<Real, RP>(), k2_level_blocks<
                     for (int sidx = 0; sidx < HR; ++sidx) ev = p2fma(W.E[t2][sidx], xe[sidx], ev);
 #pragma unroll
                     for (int sidx = 0; sidx < HQ; ++sidx) fv = p2fma(W.F[t2][sidx], xo[sidx], fv);
-                    cmac(acc[0][t2], d0[t2], p2add(ev, fv));
-                    cmac(acc[1][RP - 1 - t2], d1[RP - 1 - t2], p2sub(ev, fv));
+                    cmacx<ADJ>(acc[0][t2], d0[t2], p2add(ev, fv));
+                    cmacx<ADJ>(acc[1][RP - 1 - t2], d1[RP - 1 - t2], p2sub(ev, fv));
                 }
             }
         }
@@ -420,8 +446,7 @@ __global__ void __launch_bounds__(k2_level_threads<Real, RP>(), k2_level_blocks<
     if (mine && mcl < T.ncol) {
 #pragma unroll
         for (int a2 = 0; a2 < 2; ++a2) {
-            const int64_t Aa = child2s(l - 1, T.ip, 2 * ma1 + a2);
-            cx* od = T.outb + ((Aa * T.nj + T.j) * R2 + mt1 * RP) * A.nc + mcl;
+            cx* od = T.outb + (T.out_pair(2 * ma1 + a2) * R2 + mt1 * RP) * A.nc + mcl;
 #pragma unroll
             for (int t2 = 0; t2 < RP; ++t2) od[(int64_t)t2 * A.nc] = acc[a2][t2];
         }
@@ -433,7 +458,7 @@ __global__ void __launch_bounds__(k2_level_threads<Real, RP>(), k2_level_blocks<
 // staged by asynchronous copies; thread (column group cg, row group tg)
 // keeps outputs t = tg + 16k for the columns cg + 8q (q < 4) in registers,
 // so one shared load of M serves four columns and one of x four rows.
-template <typename Real, int RP>
+template <typename Real, int RP, bool ADJ = false>
 __global__ void __launch_bounds__(128) k2_switch(const RingArgs A, const typename C2D<Real>::T* __restrict__ M,
                                                  const typename C2D<Real>::T* __restrict__ in,
                                                  typename C2D<Real>::T* __restrict__ out)
@@ -451,7 +476,17 @@ __global__ void __launch_bounds__(128) k2_switch(const RingArgs A, const typenam
     const int64_t p = bp % mm;
     const int col0 = tile * CW, ncol = min(CW, A.nc - col0);
     const cx* Mr = M + b * A.m_stride + p * R2 * R2;
-    for (int e = threadIdx.x; e < R2 * R2; e += blockDim.x) cp_async_cx(Ms + e, Mr + e, true);
+    if (!ADJ) {
+        for (int e = threadIdx.x; e < R2 * R2; e += blockDim.x) cp_async_cx(Ms + e, Mr + e, true);
+    } else {
+        // adjoint: out[s] = sum_t conj(M[t][s]) in[t], staged as the conjugate transpose
+        for (int e = threadIdx.x; e < R2 * R2; e += blockDim.x) {
+            const int t = e / R2, sidx = e - t * R2;
+            cx v = Mr[e];
+            v.y = -v.y;
+            Ms[sidx * R2 + t] = v;
+        }
+    }
     const cx* xin = in + (size_t)bp * R2 * A.nc + col0;
     for (int e = threadIdx.x; e < R2 * CW; e += blockDim.x) {
         const int sidx = e >> 5, cl = e & 31;
@@ -593,12 +628,184 @@ __global__ void __launch_bounds__(256) k2_term(const RingArgs A, const typename 
     }
 }
 
+// ---------------------------------------------------------------- adjoint
+// Adjoint of the termination: for box b and leaf (PB-free form),
+//   Lambda^L[b][leaf][t1 RP + t2][col] = sum over the leaf's K x K points of
+//   conj(uph[b][pt]) lw[o1][t1] lw[o2][t2] y[pt][col].
+// CTA = (box, leaf, rhs tile); the leaf's points stream in chunks of RC rows
+// (RC K <= 64 points); per chunk the o2 weights are applied once per
+// (row, t2, col), then the o1 weights accumulate into registers.
 template <typename Real, int RP>
-static int apply_2d_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStream_t st)
+__global__ void __launch_bounds__(256) k2_term_adj(const RingArgs A, const typename C2D<Real>::T* __restrict__ uph,
+                                                   const Real* __restrict__ lw,
+                                                   const typename C2D<Real>::T* __restrict__ y,
+                                                   typename C2D<Real>::T* __restrict__ lam, int rt)
 {
     typedef typename C2D<Real>::T cx;
-    constexpr int R2 = RP * RP;
-    Plan2D* P = (Plan2D*)p->p2d;
+    constexpr int R2 = RP * RP, KA = (R2 * 32 + 255) / 256;
+    extern __shared__ __align__(16) unsigned char sraw[];
+    const int K = A.n / A.m;
+    const int RC = min(K, max(1, 64 / K));
+    const int YS = rt + 1;                               // padded point stride
+    cx* Ys = reinterpret_cast<cx*>(sraw);                // [RC K <= max(64, K)][YS]
+    cx* Ss = Ys + max(64, K) * YS;                       // [RC <= 8][RP][rt]
+    Real* Wl = reinterpret_cast<Real*>(Ss + 8 * RP * rt);   // [K][RP]
+    const int64_t N = (int64_t)A.n * A.n, mm = (int64_t)A.m * A.m;
+    const int ntile = (A.nc + rt - 1) / rt;
+    const int tile = (int)(blockIdx.x % ntile);
+    const int64_t rest = blockIdx.x / ntile;
+    const int64_t leaf = rest % mm;
+    const int b = (int)(rest / mm);
+    const int64_t n1b = (leaf / A.m) * K, n2b = (leaf % A.m) * K;
+    const int col0 = tile * rt, ncol = min(rt, A.nc - col0);
+    for (int e = threadIdx.x; e < K * RP; e += blockDim.x) Wl[e] = lw[e];
+    cx acc[KA];
+#pragma unroll
+    for (int k = 0; k < KA; ++k) acc[k] = zc<cx>();
+    for (int r0 = 0; r0 < K; r0 += RC) {
+        __syncthreads();
+        const int np = RC * K;
+        for (int e = threadIdx.x; e < np * rt; e += blockDim.x) {
+            const int pidx = e % np, cl = e / np;
+            const int64_t pt = (n1b + r0 + pidx / K) * A.n + n2b + pidx % K;
+            cx v = zc<cx>();
+            if (cl < ncol) {
+                cx w = uph[b * N + pt];
+                w.y = -w.y;
+                v = mulc(w, y[pt + N * (col0 + cl)]);
+            }
+            Ys[pidx * YS + cl] = v;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < RC * RP * rt; e += blockDim.x) {
+            const int cl = e % rt, t2 = (e / rt) % RP, row = e / (rt * RP);
+            const cx* yr = Ys + (row * K) * YS + cl;
+            cx sv = zc<cx>();
+            for (int o2 = 0; o2 < K; ++o2) {
+                const Real w = Wl[o2 * RP + t2];
+                const cx x = yr[o2 * YS];
+                sv.x += w * x.x;
+                sv.y += w * x.y;
+            }
+            Ss[(row * RP + t2) * rt + cl] = sv;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < KA; ++k) {
+            const int q = threadIdx.x + k * 256;
+            if (q < R2 * rt) {
+                const int cl = q % rt, t = q / rt, t1 = t / RP, t2 = t % RP;
+                for (int row = 0; row < RC; ++row) {
+                    const Real w = Wl[(r0 + row) * RP + t1];
+                    const cx x = Ss[(row * RP + t2) * rt + cl];
+                    acc[k].x += w * x.x;
+                    acc[k].y += w * x.y;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < KA; ++k) {
+        const int q = threadIdx.x + k * 256;
+        if (q < R2 * rt) {
+            const int cl = q % rt, t = q / rt;
+            if (cl < ncol) lam[((size_t)(b * mm + leaf) * R2 + t) * A.nc + col0 + cl] = acc[k];
+        }
+    }
+}
+
+// Adjoint of Lambda^0 = V' g: g(q_box + leaf) = sum_s conj(V[box][leaf][s]) Lambda^0[box][leaf][s]
+// (the boxes of a ring cover disjoint frequencies, so every g entry is written once)
+template <typename Real>
+__global__ void k2_init_adj(const RingArgs A, int r2, const typename C2D<Real>::T* __restrict__ V,
+                            const typename C2D<Real>::T* __restrict__ lam, typename C2D<Real>::T* __restrict__ g)
+{
+    typedef typename C2D<Real>::T cx;
+    const int64_t mm = (int64_t)A.m * A.m, N = (int64_t)A.n * A.n;
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= 12 * mm * A.nc) return;
+    const int64_t leaf = e % mm;
+    const int b = (int)((e / mm) % 12);
+    const int col = (int)(e / (12 * mm));
+    const cx* vr = V + b * A.v_stride + leaf * r2;
+    const cx* lr = lam + ((size_t)(b * mm + leaf) * r2) * A.nc + col;
+    cx acc = zc<cx>();
+    for (int s2 = 0; s2 < r2; ++s2) {
+        cx v = vr[s2];
+        v.y = -v.y;
+        cmac(acc, v, lr[(int64_t)s2 * A.nc]);
+    }
+    const int64_t a1 = (int64_t)(A.q1[b] + 0.5 * A.n) + (leaf >> A.Lq);
+    const int64_t a2 = (int64_t)(A.q2[b] + 0.5 * A.n) + (leaf & (A.m - 1));
+    g[a1 * A.n + a2 + N * col] = acc;
+}
+
+// Adjoint of the centre sum, part 1: for each chunk of 1024 points,
+//   part[chunk][k][col] = sum_pt conj(KC[pt][k]) y[pt][col];
+// thread k keeps all rt columns of its centre frequency.
+template <typename Real>
+__global__ void __launch_bounds__(256) k2_center_adj_part(const typename C2D<Real>::T* __restrict__ KC,
+                                                          const typename C2D<Real>::T* __restrict__ y,
+                                                          typename C2D<Real>::T* __restrict__ part, int n, int cc,
+                                                          int nc, int rt)
+{
+    typedef typename C2D<Real>::T cx;
+    constexpr int CH = 1024, SUB = 16;
+    extern __shared__ __align__(16) unsigned char sraw[];
+    cx* Ks = reinterpret_cast<cx*>(sraw);   // [SUB][cc]
+    cx* Ys = Ks + SUB * cc;                   // [SUB][rt]
+    const int64_t N = (int64_t)n * n;
+    const int ntile = (nc + rt - 1) / rt;
+    const int tile = (int)(blockIdx.x % ntile);
+    const int64_t chunk = blockIdx.x / ntile;
+    const int col0 = tile * rt, ncol = min(rt, nc - col0);
+    cx acc[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) acc[c] = zc<cx>();
+    const int k = threadIdx.x;
+    for (int p0 = 0; p0 < CH; p0 += SUB) {
+        __syncthreads();
+        const int64_t pt0 = chunk * CH + p0;
+        for (int e = threadIdx.x; e < SUB * cc; e += blockDim.x) Ks[e] = KC[pt0 * cc + e];
+        for (int e = threadIdx.x; e < SUB * rt; e += blockDim.x) {
+            const int pp = e % SUB, c = e / SUB;
+            Ys[pp * rt + c] = c < ncol ? y[pt0 + pp + N * (col0 + c)] : zc<cx>();
+        }
+        __syncthreads();
+        if (k < cc)
+            for (int pp = 0; pp < SUB; ++pp) {
+                cx kv = Ks[pp * cc + k];
+                kv.y = -kv.y;
+#pragma unroll
+                for (int c = 0; c < 32; ++c)
+                    if (c < rt) cmac(acc[c], kv, Ys[pp * rt + c]);
+            }
+    }
+    if (k < cc)
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+            if (c < ncol) part[(chunk * cc + k) * nc + col0 + c] = acc[c];
+}
+
+// part 2: g(centre frequency k)[col] = sum over chunks of part[chunk][k][col]
+template <typename Real>
+__global__ void k2_center_adj_sum(const typename C2D<Real>::T* __restrict__ part, typename C2D<Real>::T* __restrict__ g,
+                                  int n, int csd, int nc, int64_t nchunk)
+{
+    typedef typename C2D<Real>::T cx;
+    const int cc = csd * csd;
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)cc * nc) return;
+    const int k = (int)(e % cc), col = (int)(e / cc);
+    cx acc = zc<cx>();
+    for (int64_t ch = 0; ch < nchunk; ++ch) addc(acc, part[(ch * cc + k) * nc + col]);
+    const int a1 = k / csd + n / 2 - csd / 2, a2 = k % csd + n / 2 - csd / 2;
+    g[(int64_t)a1 * n + a2 + (int64_t)n * n * col] = acc;
+}
+
+template <typename Real, int RP>
+static EO2<Real, RP> make_eo2(const ibf_plan* p)
+{
     EO2<Real, RP> W;
     {
         constexpr int HQ = EO2<Real, RP>::HQ;
@@ -623,14 +830,24 @@ static int apply_2d_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStrea
             if (RP & 1) W.E[t][HQ] = pr(T0[HQ][t]);
         }
     }
+    return W;
+}
+
+template <typename Real, int RP>
+static int apply_2d_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStream_t st)
+{
+    typedef typename C2D<Real>::T cx;
+    constexpr int R2 = RP * RP;
+    Plan2D* P = (Plan2D*)p->p2d;
+    const EO2<Real, RP> W = make_eo2<Real, RP>(p);
     const int64_t N = (int64_t)P->n * P->n;
     static bool attr = false;
     if (!attr) {
         int dev = 0, optin = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        cudaFuncSetAttribute(k2_level_h<Real, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-        cudaFuncSetAttribute(k2_level_g<Real, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        cudaFuncSetAttribute(k2_level_h<Real, RP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        cudaFuncSetAttribute(k2_level_g<Real, RP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
         cudaFuncSetAttribute(k2_switch<Real, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
         cudaFuncSetAttribute(k2_center<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
         cudaFuncSetAttribute(k2_term<Real, RP, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
@@ -683,10 +900,10 @@ static int apply_2d_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStrea
             const int64_t blocks2 = 12 * (mm / 4) * ((nc + rt2 - 1) / rt2);
             for (int l = 1; l <= R.Lq; ++l) {
                 if (l <= R.hq)
-                    k2_level_h<Real, RP><<<(unsigned)blocks2, lthreads, l == 1 ? smem_l1 : smem_l, st>>>(
+                    k2_level_h<Real, RP, false><<<(unsigned)blocks2, lthreads, l == 1 ? smem_l1 : smem_l, st>>>(
                         W, A, l, (const cx*)R.D[l], a, b, rt2, lrt2, l == 1 ? g : nullptr, (const cx*)R.V);
                 else
-                    k2_level_g<Real, RP><<<(unsigned)blocks2, lthreads, smem_l, st>>>(W, A, l, (const cx*)R.D[l], a, b,
+                    k2_level_g<Real, RP, false><<<(unsigned)blocks2, lthreads, smem_l, st>>>(W, A, l, (const cx*)R.D[l], a, b,
                                                                                        rt2, lrt2);
                 prof_mark(p, st, IBF_K_2D);
                 std::swap(a, b);
@@ -708,6 +925,114 @@ static int apply_2d_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStrea
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? IBF_OK : cuda_error(e, "2D apply launch");
+}
+
+// g = K^* y: per column slice the centre's adjoint sum, then per ring the
+// adjoint steps in reverse order -- termination, G levels Lq..hq+1 (H-form
+// kernels with roles swapped), switch, H levels hq..1 (G-form kernels), and
+// the V' g adjoint, which writes the ring's own frequencies of g.
+template <typename Real, int RP>
+static int apply_2d_adj_t(ibf_plan* p, const void* yv, void* gv, int nrhs, cudaStream_t st)
+{
+    typedef typename C2D<Real>::T cx;
+    constexpr int R2 = RP * RP;
+    Plan2D* P = (Plan2D*)p->p2d;
+    const EO2<Real, RP> W = make_eo2<Real, RP>(p);
+    const int64_t N = (int64_t)P->n * P->n;
+    static bool attr = false;
+    if (!attr) {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaFuncSetAttribute(k2_level_h<Real, RP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        cudaFuncSetAttribute(k2_level_g<Real, RP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        cudaFuncSetAttribute(k2_switch<Real, RP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        cudaFuncSetAttribute(k2_term_adj<Real, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        cudaFuncSetAttribute(k2_center_adj_part<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        attr = true;
+    }
+    const int cc = P->center * P->center;
+    if (cc > 256) return set_error(IBF_ERR_UNSUPPORTED, "2D adjoint: centre side above 16");
+    for (int c0 = 0; c0 < nrhs; c0 += p->max_nrhs) {
+        const int nc = std::min(p->max_nrhs, nrhs - c0);
+        const cx* y = (const cx*)yv + N * c0;
+        cx* g = (cx*)gv + N * c0;
+        prof_start(p, st);
+        int rts = 1;
+        while (rts < 32 && rts < nc) rts *= 2;
+        const int ntile_s = (nc + rts - 1) / rts;
+        {
+            // centre: partial sums per 1024 points into the ring workspace, then their sum
+            const int64_t nchunk = N / 1024;
+            const size_t smem_c = ((size_t)16 * cc + 16 * rts) * sizeof(cx);
+            k2_center_adj_part<Real><<<(unsigned)(nchunk * ntile_s), 256, smem_c, st>>>(
+                (const cx*)P->KC, y, (cx*)P->ws[0], P->n, cc, nc, rts);
+            k2_center_adj_sum<Real><<<(unsigned)((cc * nc + 255) / 256), 256, 0, st>>>((const cx*)P->ws[0], g, P->n,
+                                                                                      P->center, nc, nchunk);
+            prof_mark(p, st, IBF_K_2D);
+        }
+        int rt2 = 1, lrt2 = 0;
+        while (rt2 < (sizeof(Real) == 8 ? 8 : 16) && rt2 < nc) rt2 *= 2, ++lrt2;
+        const int lthreads = (2 * RP * rt2 + 31) / 32 * 32;
+        const size_t smem_l = (8 * (size_t)R2 * rt2 + 16 * R2) * sizeof(cx);
+        const size_t smem_s = ((size_t)R2 * R2 + (size_t)R2 * 32) * sizeof(cx);
+        for (const Ring2D& R : P->rings) {
+            RingArgs A;
+            memcpy(A.q1, R.q1, sizeof(A.q1));
+            memcpy(A.q2, R.q2, sizeof(A.q2));
+            A.v_stride = R.v_stride;
+            A.d_stride = R.d_stride;
+            A.m_stride = R.m_stride;
+            A.n = P->n;
+            A.m = R.m;
+            A.Lq = R.Lq;
+            A.hq = R.hq;
+            A.nc = nc;
+            const int64_t mm = (int64_t)R.m * R.m;
+            const int K = P->n / R.m;
+            cx* a = (cx*)P->ws[0];
+            cx* b = (cx*)P->ws[1];
+            const size_t smem_t = ((size_t)std::max(64, K) * (rts + 1) + 8 * RP * rts) * sizeof(cx) +
+                                  (size_t)K * RP * sizeof(Real);
+            k2_term_adj<Real, RP><<<(unsigned)(12 * mm * ntile_s), 256, smem_t, st>>>(A, (const cx*)R.uph,
+                                                                                    (const Real*)R.lw, y, a, rts);
+            prof_mark(p, st, IBF_K_2D);
+            const int64_t blocks2 = 12 * (mm / 4) * ((nc + rt2 - 1) / rt2);
+            auto switch_adj = [&]() {
+                k2_switch<Real, RP, true><<<(unsigned)(12 * mm * ((nc + 31) / 32)), 128, smem_s, st>>>(
+                    A, (const cx*)R.M, a, b);
+                prof_mark(p, st, IBF_K_2D);
+                std::swap(a, b);
+            };
+            if (R.hq == R.Lq) switch_adj();   // forward: the switch follows the last level
+            for (int l = R.Lq; l >= 1; --l) {
+                if (l > R.hq)
+                    k2_level_h<Real, RP, true><<<(unsigned)blocks2, lthreads, smem_l, st>>>(
+                        W, A, l, (const cx*)R.D[l], a, b, rt2, lrt2, nullptr, nullptr);
+                else
+                    k2_level_g<Real, RP, true><<<(unsigned)blocks2, lthreads, smem_l, st>>>(
+                        W, A, l, (const cx*)R.D[l], a, b, rt2, lrt2);
+                prof_mark(p, st, IBF_K_2D);
+                std::swap(a, b);
+                if (l == R.hq + 1) switch_adj();   // forward: the switch sits between levels hq and hq+1
+            }
+            k2_init_adj<Real><<<(unsigned)((12 * mm * nc + 255) / 256), 256, 0, st>>>(A, R2, (const cx*)R.V, a, g);
+            prof_mark(p, st, IBF_K_2D);
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? IBF_OK : cuda_error(e, "2D adjoint launch");
+}
+
+int apply_2d_adjoint(ibf_plan* p, const void* y, void* g, int nrhs, cudaStream_t st)
+{
+    const bool d = p->dtype == IBF_C128;
+    switch (p->r) {
+    case 5: return d ? apply_2d_adj_t<double, 5>(p, y, g, nrhs, st) : apply_2d_adj_t<float, 5>(p, y, g, nrhs, st);
+    case 7: return d ? apply_2d_adj_t<double, 7>(p, y, g, nrhs, st) : apply_2d_adj_t<float, 7>(p, y, g, nrhs, st);
+    case 9: return d ? apply_2d_adj_t<double, 9>(p, y, g, nrhs, st) : apply_2d_adj_t<float, 9>(p, y, g, nrhs, st);
+    default: return set_error(IBF_ERR_UNSUPPORTED, "2D: r must be 5, 7 or 9");
+    }
 }
 
 int apply_2d(ibf_plan* p, const void* g, void* u, int nrhs, cudaStream_t st)

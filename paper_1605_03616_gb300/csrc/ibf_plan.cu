@@ -631,7 +631,7 @@ extern "C" int ibf_apply_adjoint(ibf_plan* p, const void* y, void* g, int nrhs, 
 {
     int rc = check_apply(p, y, g, nrhs);
     if (rc) return rc;
-    if (p->d == 2) return set_error(IBF_ERR_UNSUPPORTED, "2D plans have no adjoint apply");
+    if (p->d == 2) return apply_2d_adjoint(p, y, g, nrhs, (cudaStream_t)stream);
     if (p->form != IBF_FORM_STRUCTURED) return explicit_adjoint(p, y, g, nrhs, (cudaStream_t)stream);
     return fused_apply(p, y, g, nrhs, true, (cudaStream_t)stream);
 }
@@ -672,7 +672,6 @@ extern "C" int ibf_apply_host(ibf_plan* p, const void* hin, void* hout, int nrhs
     if (nrhs < 1) return set_error(IBF_ERR_INVALID, "nrhs must be >= 1");
     const size_t esz = p->dtype == IBF_C128 ? 16 : 8;
     if (((uintptr_t)hin % esz) || ((uintptr_t)hout % esz)) return set_error(IBF_ERR_INVALID, "misaligned vector pointer");
-    if (adjoint && p->d == 2) return set_error(IBF_ERR_UNSUPPORTED, "2D plans have no adjoint apply");
     int rc = host_setup(p);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;

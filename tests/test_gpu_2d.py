@@ -70,3 +70,28 @@ def test_2d_full_size_fp32_vs_fp64_and_sampled_direct(ibf):
     print("\n2d n=512 r=7: fp32 vs fp64 %.3e, fp64 vs direct (64 rows) %.3e" % (e, ei))
     assert e < 1e-5
     assert ei < 5e-3
+
+
+@pytest.mark.parametrize("phase,n,r,nrhs,max_nrhs", [(O.PHASE_FIO2D, 32, 7, 3, 32), (O.PHASE_SEPARABLE, 64, 5, 2, 32),
+                                                     (O.PHASE_FIO2D, 64, 9, 6, 4)])   # slices of 4 and 2
+def test_2d_adjoint_matches_oracle(ibf, phase, n, r, nrhs, max_nrhs):
+    """g = K^* y of the 2D multiscale IBF against the oracle's adjoint, FP64
+    and FP32, with the dot-product identity against the GPU forward apply."""
+    x = W.grid_x_2d(n)
+    y = W.complex_normal((n * n, nrhs), W.rng(980))
+    ref = O.mibf_adjoint_2d(phase, n, r, x, y)
+    out = {}
+    for dt, cdt in ((ibf.C128, np.complex128), (ibf.C64_FP32, np.complex64)):
+        plan = ibf.Plan(phase, n * n, r, dt, d=2, max_nrhs=max_nrhs)
+        yd = torch.from_numpy(y.astype(cdt)).cuda()
+        out[dt] = plan.adjoint(yd).cpu().numpy()
+        if dt == ibf.C128:
+            g = W.complex_normal((n * n, nrhs), W.rng(981))
+            u = plan.apply(torch.from_numpy(g).cuda()).cpu().numpy()
+            lhs, rhs = np.vdot(y, u), np.vdot(out[dt], g)
+            assert abs(lhs - rhs) < 1e-11 * abs(lhs)
+        plan.close()
+    e64, e32 = O.rel_l2(out[ibf.C128], ref), O.rel_l2(out[ibf.C64_FP32], ref)
+    print("\nadjoint 2d phase=%d n=%d r=%d nrhs=%d fp64 %.3e fp32 %.3e" % (phase, n, r, nrhs, e64, e32))
+    assert e64 < 1e-11
+    assert e32 < 1e-5

@@ -80,7 +80,12 @@ def test_2d_adjoint_dot_product_identity_and_separable_exactness():
     lhs = np.vdot(y, O.mibf_apply_2d(O.PHASE_FIO2D, n, r, x, g))
     rhs = np.vdot(O.mibf_adjoint_2d(O.PHASE_FIO2D, n, r, x, y), g)
     assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+    # separable phase: e(Phi(x_p, xi_k)) = e(Phi(x_p, xi_0)) e(Phi(x_0, xi_k)) e(-Phi(x_0, xi_0)),
+    # so K^* y is rank one: conj(e(Phi(x_0, xi_k))) e(Phi(x_0, xi_0)) sum_p conj(e(Phi(x_p, xi_0))) y_p
     ga = O.mibf_adjoint_2d(O.PHASE_SEPARABLE, n, 5, x, y)
     xi = W.omega_2d(n)
-    K = np.exp(2j * np.pi * np.array([[O.phi_2d(O.PHASE_SEPARABLE, a[0], a[1], b[0], b[1]) for b in xi] for a in x]))
-    assert O.rel_l2(ga, K.conj().T @ y) < 1e-12
+    ph = lambda a, b: O.phi_2d(O.PHASE_SEPARABLE, a[0], a[1], b[0], b[1])
+    col0 = np.exp(2j * np.pi * np.array([ph(a, xi[0]) for a in x]))
+    row0 = np.exp(2j * np.pi * np.array([ph(x[0], b) for b in xi]))
+    exact = np.conj(row0) * np.exp(2j * np.pi * ph(x[0], xi[0])) * np.vdot(col0, y)
+    assert O.rel_l2(ga, exact) < 1e-12
