@@ -396,9 +396,18 @@ def run_2d(ibf, torch, n=512, r=7, nrhs=32, reps=5):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
+    for _ in range(2):
+        plan.adjoint_raw(u.data_ptr(), g.data_ptr(), nrhs, cs)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        plan.adjoint_raw(u.data_ptr(), g.data_ptr(), nrhs, cs)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_adj = e0.elapsed_time(e1) / reps
     res = {"workload": "2D FIO n=%d (N=%d) r=%d nrhs=%d complex64, MIBF with 16x16 centre" % (n, N, r, nrhs),
-           "ms_per_apply": ms, "vectors_per_s": nrhs / (ms / 1e3), "launches": plan.query(ibf.Q_LAUNCHES),
-           "factor_bytes": plan.query(ibf.Q_FACTOR_BYTES)}
+           "ms_per_apply": ms, "vectors_per_s": nrhs / (ms / 1e3), "adjoint_ms_per_apply": ms_adj,
+           "launches": plan.query(ibf.Q_LAUNCHES), "factor_bytes": plan.query(ibf.Q_FACTOR_BYTES)}
     plan.close()
     return res
 
