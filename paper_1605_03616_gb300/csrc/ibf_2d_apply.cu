@@ -724,9 +724,10 @@ __global__ void k2_init_adj(const RingArgs A, int r2, const typename C2D<Real>::
     const int64_t mm = (int64_t)A.m * A.m, N = (int64_t)A.n * A.n;
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= 12 * mm * A.nc) return;
-    const int64_t leaf = e % mm;
-    const int b = (int)((e / mm) % 12);
-    const int col = (int)(e / (12 * mm));
+    // columns fastest: the r^2 reads of Lambda^0 are coalesced across the warp
+    const int col = (int)(e % A.nc);
+    const int64_t leaf = (e / A.nc) % mm;
+    const int b = (int)(e / ((int64_t)A.nc * mm));
     const cx* vr = V + b * A.v_stride + leaf * r2;
     const cx* lr = lam + ((size_t)(b * mm + leaf) * r2) * A.nc + col;
     cx acc = zc<cx>();
