@@ -70,6 +70,20 @@ def test_2d_full_size_fp32_vs_fp64_and_sampled_direct(ibf):
     print("\n2d n=512 r=7: fp32 vs fp64 %.3e, fp64 vs direct (64 rows) %.3e" % (e, ei))
     assert e < 1e-5
     assert ei < 5e-3
+    # the adjoint at full size: FP32 against FP64, and <K g, y> = <g, K^* y> in FP64
+    y64 = torch.from_numpy(W.complex_normal((4, N), W.rng(604))).cuda()
+    ga64 = torch.empty_like(y64)
+    p64.adjoint_raw(y64.data_ptr(), ga64.data_ptr(), 4, torch.cuda.current_stream().cuda_stream)
+    y32 = y64.to(torch.complex64).contiguous()
+    ga32 = torch.empty_like(y32)
+    p32.adjoint_raw(y32.data_ptr(), ga32.data_ptr(), 4, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    ea = float(torch.linalg.vector_norm(ga32.to(torch.complex128) - ga64) / torch.linalg.vector_norm(ga64))
+    lhs = torch.vdot(y64.flatten(), u64.flatten()).item()
+    rhs = torch.vdot(ga64.flatten(), g64.flatten()).item()
+    print("2d n=512 adjoint: fp32 vs fp64 %.3e, dot-product identity %.1e" % (ea, abs(lhs - rhs) / abs(lhs)))
+    assert ea < 1e-5
+    assert abs(lhs - rhs) < 1e-10 * abs(lhs)
 
 
 @pytest.mark.parametrize("phase,n,r,nrhs,max_nrhs", [(O.PHASE_FIO2D, 32, 7, 3, 32), (O.PHASE_SEPARABLE, 64, 5, 2, 32),
