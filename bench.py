@@ -42,14 +42,14 @@ FP32_LANES_PER_SM = 128
 # this benchmark at N = 2^20, r = 9, nrhs = 64, 4 levels per launch, tile 32
 # (profiles/k_fused_f32_fio1d_n2e20_nrhs64.md).  Keyed by the launch's level
 # range; valid only while the kernel sources hash to KERNEL_SRC_SHA.
-KERNEL_SRC_SHA = "1d8a6acd52921e7e"
+KERNEL_SRC_SHA = "fecf3fff897107d4"
 TRAFFIC_N20_R9_NRHS64_K4 = {
-    (0, 4, "H"): 1216552960 + 4771685888,
-    (4, 7, "H"): 5285033216 + 4778130944,
-    (7, 10, "H"): 5964489984 + 4782603008,
-    (10, 14, "G"): 5436348928 + 4779667200,
-    (14, 17, "G"): 5286072064 + 4779682816,
-    (17, 20, "G"): 5368783872 + 527380736,
+    (0, 4, "H"): 1216440576 + 4771523840,
+    (4, 7, "H"): 5285107968 + 4778114048,
+    (7, 10, "H"): 5964420352 + 4782394624,
+    (10, 14, "G"): 5435983104 + 4779323904,
+    (14, 17, "G"): 5284954112 + 4779703040,
+    (17, 20, "G"): 5370062336 + 527404288,
 }
 
 

@@ -658,112 +658,6 @@ __global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>
     fused_body<Real, RP, ADJ, KIND, RT>(c_eo<Real, RP>, descs[lo], b - start[lo], smraw);
 }
 
-// Persistent batched launch: CTAs take work items (one CTA-sized block of one
-// descriptor) from an atomic counter in descriptor order.  Descriptors are
-// ordered chunk-major, so every item a block waits for was handed out before
-// it, to a CTA that is already running: the waits cannot deadlock.  A block of
-// chunk c of a plan waits until all blocks of that plan's chunk c-1 have
-// finished (dep/need), with a bounded spin; on expiry it raises *status and
-// every CTA stops.  Inputs written earlier in the same launch are read with
-// L1-bypassing loads.
-struct PersistArgs {
-    const FusedDesc* descs;
-    const int64_t* start;      // first item of each descriptor (n entries)
-    const int* dep;            // descriptor this one waits for, or -1
-    const int64_t* need;       // blocks of dep that must be done
-    int* done;                 // finished blocks per descriptor (zeroed per apply)
-    unsigned long long* next;  // work counter (zeroed per apply)
-    int* status;               // 0, or 1 after a wait expired
-    int64_t total;
-    int n;
-    long long max_spin;
-};
-
-// Persistent form: 256 threads per CTA (fusion depth at most 4 with 32-column
-// tiles), as many CTAs as fit on the device at once.
-template <typename Real>
-struct PersistTraits {
-    static constexpr int kThreads = 256;
-    static constexpr int kMinBlocks = sizeof(Real) == 4 ? 3 : 1;
-};
-
-// Each CTA takes items from the shared counter in order (the next item is
-// claimed while the current one runs, hiding the atomic's latency).  An item
-// of a descriptor with a dependency may start once every item of that
-// dependency is done; a CTA checks this once per run of items of the same
-// descriptor.  Finished items are published (fence, then one atomic add per
-// run) whenever the CTA moves to another descriptor and when it exits, so a
-// CTA never waits while it holds unpublished work.  Waits are bounded: after
-// max_spin polls the CTA sets the sticky status and every waiting CTA gives up.
-template <typename Real, int RP, bool ADJ>
-__global__ void __launch_bounds__(PersistTraits<Real>::kThreads, PersistTraits<Real>::kMinBlocks)
-    k_fused_persist(const __grid_constant__ PersistArgs A)
-{
-    extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ long long s_item[2];
-    __shared__ int s_stop;
-    int cur = -1;                       // descriptor of the current run of items
-    int64_t cur_lo = 0, cur_hi = 0;     // its item range
-    int pending = 0;                    // thread 0: finished items of cur not yet published
-    if (threadIdx.x == 0) s_item[0] = (long long)atomicAdd(A.next, 1ULL);
-    __syncthreads();
-    for (int it = 0;; ++it) {
-        const long long item = s_item[it & 1];
-        if (item >= A.total) break;
-        if (item < cur_lo || item >= cur_hi) {
-            if (cur >= 0) {
-                __threadfence();   // this thread's outputs are visible device-wide ...
-                __syncthreads();   // ... for every thread of the block ...
-                if (threadIdx.x == 0 && pending) atomicAdd(A.done + cur, pending);   // ... then counted
-                pending = 0;
-            }
-            int lo = 0, hi = A.n - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (A.start[mid] <= item)
-                    lo = mid;
-                else
-                    hi = mid - 1;
-            }
-            cur = lo;
-            cur_lo = A.start[lo];
-            cur_hi = lo + 1 < A.n ? A.start[lo + 1] : A.total;
-            const int dep = A.dep[lo];
-            if (dep >= 0) {
-                if (threadIdx.x == 0) {
-                    long long spins = 0;
-                    int ok = 1;
-                    while (atomicAdd(A.done + dep, 0) < A.need[lo]) {
-                        if (++spins > A.max_spin || *(volatile int*)A.status) {
-                            ok = 0;
-                            break;
-                        }
-                        __nanosleep(200);
-                    }
-                    if (!ok) atomicExch(A.status, 1);
-                    __threadfence();
-                    s_stop = !ok;
-                }
-                __syncthreads();
-                if (s_stop) break;
-            }
-        }
-        if (threadIdx.x == 0) s_item[(it + 1) & 1] = (long long)atomicAdd(A.next, 1ULL);
-        const FusedDesc& d = A.descs[cur];
-        const int64_t blk = item - cur_lo;
-        // every descriptor of the persistent form uses 32-column tiles
-        if (d.kind == 0)
-            fused_body<Real, RP, ADJ, 0, 32, true>(c_eo<Real, RP>, d, blk, smraw);
-        else
-            fused_body<Real, RP, ADJ, 1, 32, true>(c_eo<Real, RP>, d, blk, smraw);
-        if (threadIdx.x == 0) ++pending;
-        __syncthreads();   // shared memory and the claimed item change hands
-    }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0 && cur >= 0 && pending) atomicAdd(A.done + cur, pending);
-}
-
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
