@@ -225,6 +225,10 @@ def run_nufft_latency(ibf, torch, N=1024, reps=200):
         out[name] = {"us_per_apply": t_launch, "us_per_apply_graph": e0.elapsed_time(e1) / reps * 1e3,
                      "launches": p.query(ibf.Q_LAUNCHES)}
         del graph
+        if dtype == ibf.C64_FP32:
+            k, rt, ms = p.autotune(1)
+            out[name]["autotuned"] = {"levels_per_launch": k, "rhs_tile": rt, "us_per_apply": ms * 1e3,
+                                      "launches": p.query(ibf.Q_LAUNCHES)}
         p.close()
     return out
 

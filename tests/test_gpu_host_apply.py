@@ -62,12 +62,15 @@ def test_host_apply_2d_and_explicit(ibf):
     g2 = W.complex_normal((20, n * n), W.rng(820), dtype=np.complex64)    # chunks of 16 and 4
     o2 = torch.empty_like(torch.from_numpy(g2)).pin_memory()
     p2.apply_host(torch.from_numpy(g2).pin_memory(), o2)
+    a2 = torch.empty_like(torch.from_numpy(g2)).pin_memory()
+    p2.apply_host(torch.from_numpy(g2).pin_memory(), a2, adjoint=True)
     pe = ibf.Plan(ibf.PHASE_FIO1D, 256, 9, ibf.C128, form=ibf.FORM_EXPLICIT, max_nrhs=4)
     ge = W.complex_normal((3, 256), W.rng(821))
     oe = torch.empty_like(torch.from_numpy(ge)).pin_memory()
     pe.apply_host(torch.from_numpy(ge).pin_memory(), oe)
     torch.cuda.current_stream().synchronize()
     assert torch.equal(o2, _device(p2, g2))
+    assert torch.equal(a2, _device(p2, g2, adjoint=True))
     assert torch.equal(oe, _device(pe, ge))
     p2.close()
     pe.close()
