@@ -618,8 +618,8 @@ def run_gpu(a):
     if rank == 0 and not a.skip_batch:
         batch = run_batch(ibf, torch)
 
-    # ---- construction (SURVEY-style count of phase evaluations of the
-    # explicit factors, (3 r L + r^2 + 2 r) N, FP64 on the GPU)
+    # ---- construction: plan build time and the number of phase evaluations
+    # of the explicit factors, (3 r L + r^2 + 2 r) N, FP64 on the GPU
     L = int(round(np.log2(N)))
     n_phase = (3 * r * L + r * r + 2 * r) * N
     construction = {"structured_fp32_plan_ms": t_struct,
