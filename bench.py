@@ -188,7 +188,7 @@ def run_reference(a):
 
 # ------------------------------------------------------- batched workload
 def run_nufft_latency(ibf, torch, N=1024, reps=200):
-    """Config 1: NUFFT-type phase x xi with N = 1024 sorted iid uniform
+    """Latency of a small nonuniform transform: phase x xi with N = 1024 sorted iid uniform
     points, one vector: apply latency in microseconds, FP64 explicit and FP32
     structured, as a sequence of launches and replayed from a CUDA graph."""
     gen = W.rng(workload=1)
@@ -270,7 +270,7 @@ def run_optimal(ibf, torch, N=1 << 16, nrhs=8, reps=3):
 
 
 def run_autograd(ibf, torch, N=1 << 18, nrhs=32, reps=5):
-    """Config 5: loss ||K g - y||^2 at N = 2^18, 32 columns, complex64; one
+    """Training-style step: loss ||K g - y||^2 at N = 2^18, 32 columns, complex64; one
     step = forward apply + backward (the hand-written adjoint) through
     torch.autograd, CUDA events."""
     from paper_1605_03616_gb300.autograd import ibf_apply
