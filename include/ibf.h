@@ -23,8 +23,9 @@
  *   - Multi-vector arguments are column-major: column c of an n x nrhs array
  *     starts at element n*c.
  *   - Streams are CUDA streams (cudaStream_t); NULL is the legacy default
- *     stream.  Apply calls are asynchronous on that stream, allocate nothing
- *     and do not synchronize the host.
+ *     stream.  Apply calls are asynchronous on that stream and do not
+ *     synchronize the host; they allocate nothing, except the first
+ *     ibf_apply_host call on a plan (its staging buffers, see there).
  */
 #ifndef IBF_GB300_H
 #define IBF_GB300_H
@@ -75,7 +76,10 @@ enum ibf_dtype {
     IBF_C128 = 0,       /* complex128 in and out, FP64 factors and FP64 arithmetic  */
     IBF_C64_FP32 = 1,   /* complex64 in and out, FP32 factors, FP32 arithmetic      */
     IBF_C64_BF16X3 = 2  /* complex64 in and out, three-term split-BF16 tensor-core
-                           products with FP32 accumulation                          */
+                           products with FP32 accumulation: not built -- plan
+                           creation returns IBF_ERR_UNSUPPORTED (at r <= 11 the
+                           contractions are too small for the tensor cores to
+                           beat the packed-FP32 SIMT form)                       */
 };
 
 /* Storage form of the factors. */
@@ -102,7 +106,8 @@ typedef struct ibf_options {
     int h;                 /* switch level in [1, L-1]; <= 0 means floor(L/2)        */
     int max_nrhs;          /* columns of the apply workspace; larger nrhs is
                               processed in slices of max_nrhs.  <= 0: 64 for the
-                              structured form, 8 for the explicit form.            */
+                              structured form, 8 for the explicit and optimal
+                              forms.                                               */
     int levels_per_launch; /* structured form: butterfly levels fused per kernel
                               (1..10); <= 0 lets the autotuner choose              */
     int rhs_tile;          /* structured form: right-hand sides per CTA (1..64,
@@ -123,7 +128,7 @@ typedef struct ibf_options {
  *              -- down to a 16 x 16 centre that is summed directly; every box
  *              gets a 2D butterfly of depth log2(side) switching at
  *              ceil(depth/2) (Sec. 5.1).  2D plans: structured form, r in
- *              {5, 7, 9}, the grid X only (x = NULL), forward apply only.
+ *              {5, 7, 9}, the grid X only (x = NULL); apply and adjoint.
  *              Vectors are n x n row-major in (n1, n2) and (k1, k2).
  *   N        : number of points, a power of two, 4 <= N <= 2^24 (d = 1), or
  *              n^2 with n a power of two, 32 <= n <= 2048 (d = 2).
