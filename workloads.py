@@ -9,6 +9,7 @@ Recipes (seed = 16050361600 + workload id unless a test passes its own):
 * 1D FIO, Sec. 6.2: x_j = j/N, xi_k = k - N/2.
 * 2D FIO, Sec. 6.3: x on the n x n grid of [0,1)^2, xi on [-n/2, n/2)^2.
 * g: real and imaginary parts iid N(0,1).
+* amplitude factors (non-unit a(x, xi), Sec. 1): ``separated_amplitude``.
 """
 from __future__ import annotations
 
@@ -59,3 +60,24 @@ def complex_normal(shape, gen: np.random.Generator, dtype=np.complex128) -> np.n
     re = gen.standard_normal(shape)
     im = gen.standard_normal(shape)
     return (re + 1j * im).astype(dtype)
+
+
+def separated_amplitude(x, xi, q: int, gen: np.random.Generator, dtype=np.complex128):
+    """Factors (alpha, beta) of a synthetic smooth amplitude
+    a(x, xi) = sum_t alpha_t(x) beta_t(xi), t < q (Sec. 1: a smooth symbol of
+    order zero in xi).  alpha_0 = beta_0 = 1; for t >= 1,
+    alpha_t(x) = c_t cos(2 pi t (x_1 + .. + x_d)) + i s_t sin(2 pi t x_1) with
+    c_t, s_t iid U(-1/2, 1/2), and beta_t(xi) = (xi_1 / sqrt(1 + |xi|^2))^t.
+    x: (nx,) or (nx, d); xi: (N,) or (N, d).  Returns column-major factor
+    arrays of shapes (nx, q) and (N, q)."""
+    xs = np.asarray(x, np.float64).reshape(len(x), -1)
+    ks = np.asarray(xi, np.float64).reshape(len(xi), -1)
+    alpha = np.ones((xs.shape[0], q), np.complex128)
+    beta = np.ones((ks.shape[0], q), np.complex128)
+    c = gen.uniform(-0.5, 0.5, q)
+    s = gen.uniform(-0.5, 0.5, q)
+    w = ks[:, 0] / np.sqrt(1.0 + (ks * ks).sum(axis=1))
+    for t in range(1, q):
+        alpha[:, t] = c[t] * np.cos(2 * np.pi * t * xs.sum(axis=1)) + 1j * s[t] * np.sin(2 * np.pi * t * xs[:, 0])
+        beta[:, t] = w ** t
+    return alpha.astype(dtype), beta.astype(dtype)
