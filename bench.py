@@ -302,6 +302,46 @@ def run_autograd(ibf, torch, N=1 << 18, nrhs=32, reps=5):
     return rec
 
 
+def run_amplitude(ibf, torch, N=1 << 20, nrhs=16, q=3, reps=5):
+    """Non-unit amplitude a(x, xi) = sum_t alpha_t(x) beta_t(xi) (Sec. 1),
+    1D FIO N = 2^20, r = 9, 16 columns complex64, q = 3 terms (one pass: the
+    phase-only apply runs on 48 columns), against the phase-only apply of the
+    same 16 and of 48 columns on the same plan; CUDA events."""
+    plan = ibf.Plan(ibf.PHASE_FIO1D, N, 9, ibf.C64_FP32, max_nrhs=nrhs * q)
+    gen = W.rng(workload=7)
+    x, xi = W.uniform_x(N), W.omega_1d(N)
+    alpha, beta = W.separated_amplitude(x, xi, q, gen, dtype=np.complex64)
+    # (N, m) views of contiguous (m, N) tensors: the column-major layout of
+    # the C ABI, so the binding passes them on without a copy
+    al = torch.from_numpy(alpha.T.copy()).cuda().t()
+    be = torch.from_numpy(beta.T.copy()).cuda().t()
+    g = torch.from_numpy(W.complex_normal((nrhs, N), gen, dtype=np.complex64)).cuda().t()
+    g3 = torch.from_numpy(W.complex_normal((nrhs * q, N), gen, dtype=np.complex64)).cuda().t()
+    work = torch.empty(2 * N * nrhs * q, dtype=torch.complex64, device="cuda")
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_amp = timed(lambda: plan.apply_amplitude(g, al, be, work=work))
+    ms_1 = timed(lambda: plan.apply(g))
+    ms_q = timed(lambda: plan.apply(g3))
+    rec = {"workload": "1D FIO N=2^20 r=9, 16 columns complex64, amplitude of q=3 separated terms",
+           "ms": ms_amp, "vectors_per_s": nrhs / (ms_amp / 1e3), "phase_only_ms_16_columns": ms_1,
+           "phase_only_ms_48_columns": ms_q, "scaling_kernels_ms": ms_amp - ms_q}
+    plan.close()
+    return rec
+
+
 def run_batch(ibf, torch, reps=5, count=256, seed=4):
     """256 independent 1D FIO transforms, N = 2^e with e uniform in 10..16,
     nrhs uniform in 1..64, complex64, r = 9: the batched launch captured in a
@@ -632,6 +672,9 @@ def run_gpu(a):
     grad5 = None
     if rank == 0 and not a.skip_batch:
         grad5 = run_autograd(ibf, torch)
+    amplitude = None
+    if rank == 0 and not a.skip_batch:
+        amplitude = run_amplitude(ibf, torch)
     optimal = nufft = None
     if rank == 0 and not a.skip_fp64:
         optimal = run_optimal(ibf, torch)
@@ -666,6 +709,7 @@ def run_gpu(a):
                            "parallelism": "independent rhs batches per GPU (dp%d)" % world},
                 "clocks": clk, "e2e": e2e, "gpu_launches": a.steps * launches, "roofline": roof,
                 "fp64_plain": fp64, "construction": construction, "batch256": batch, "autograd": grad5, "optimal_ibf": optimal, "nufft1024_latency": nufft,
+                "amplitude": amplitude,
                 "fio2d": fio2d, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     plan.close()

@@ -203,6 +203,36 @@ int ibf_apply_host(ibf_plan* plan, const void* in_host, void* out_host, int nrhs
                    ibf_stream_t stream);
 
 /*
+ * ibf_apply_amplitude -- u = A g (adjoint = 0) or g = A^* y (adjoint = 1) for
+ * the kernel with a non-unit amplitude, A(x, xi) = a(x, xi) exp(2 pi i
+ * Phi(x, xi)) (eq. FIO).  The paper sets a = 1 after noting that a smooth
+ * amplitude is numerically low rank jointly on X x Omega (Sec. 1); the
+ * caller supplies that low-rank form, a(x, xi) = sum_{t<q} alpha_t(x)
+ * beta_t(xi), and
+ *   A   = sum_t diag(alpha_t) K diag(beta_t),
+ *   A^* = sum_t diag(conj beta_t) K^* diag(conj alpha_t),
+ * with K the plan's phase-only operator, applied by ibf_apply /
+ * ibf_apply_adjoint (any form, 1D or 2D).
+ *   alpha : device array N x q column-major; column t holds alpha_t at the
+ *           points in the caller's x order.
+ *   beta  : device array N x q column-major; column t holds beta_t(xi_k).
+ *   in, out : as ibf_apply (adjoint = 0: g -> u) or ibf_apply_adjoint
+ *           (adjoint = 1: y -> g).  out is overwritten.
+ *   work  : caller-owned device scratch of work_elems elements of the plan's
+ *           element type, work_elems >= 2 N nrhs.  The terms are processed in
+ *           passes of m = min(q, floor(work_elems / (2 N nrhs))) terms: per
+ *           pass one scaling kernel, the phase-only apply on m nrhs columns,
+ *           one accumulation kernel.  2 N q nrhs elements take one pass.
+ * Allocates nothing; asynchronous on `stream`; calls on one plan must be
+ * ordered.  Errors: IBF_ERR_INVALID for a NULL plan or pointer, q < 1,
+ * nrhs < 1, a pointer not aligned to the element size, work_elems below
+ * 2 N nrhs, m nrhs above INT_MAX, out overlapping in, alpha or beta, or the
+ * used part of work overlapping any other argument; otherwise as ibf_apply.
+ */
+int ibf_apply_amplitude(ibf_plan* plan, const void* alpha, const void* beta, int q, const void* in, void* out,
+                        int nrhs, int adjoint, void* work, int64_t work_elems, ibf_stream_t stream);
+
+/*
  * ibf_apply_static_scratch -- u = K g like ibf_apply, for callers that may
  * not allocate device memory once their plans exist (for example a plug-in
  * whose host application owns the device heap and forbids further cudaMalloc

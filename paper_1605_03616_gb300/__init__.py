@@ -42,7 +42,7 @@ EXPORTS = ("ibf_plan_create", "ibf_plan_create_ex", "ibf_apply", "ibf_apply_adjo
            "ibf_plan_query", "ibf_get_last_error", "ibf_plan_profile_begin", "ibf_plan_profile_end",
            "ibf_apply_static_scratch", "ibf_batch_create", "ibf_batch_apply", "ibf_batch_query",
            "ibf_batch_destroy", "ibf_plan_autotune", "ibf_batch_apply_persistent", "ibf_batch_status",
-           "ibf_batch_set_wait_limit", "ibf_batch_test_withhold", "ibf_apply_host")
+           "ibf_batch_set_wait_limit", "ibf_batch_test_withhold", "ibf_apply_host", "ibf_apply_amplitude")
 
 BQ_LAUNCHES, BQ_WORKSPACE_BYTES, BQ_COUNT, BQ_PERSIST_ITEMS = range(4)
 
@@ -97,6 +97,7 @@ def load_library(path: str | None = None):
     L.ibf_batch_set_wait_limit.argtypes = [P, ctypes.c_longlong]
     L.ibf_batch_test_withhold.argtypes = [P, I, I]
     L.ibf_plan_profile_begin.argtypes = [P, I]
+    L.ibf_apply_amplitude.argtypes = [P, P, P, I, P, P, I, I, P, I64, P]
     L.ibf_plan_profile_end.argtypes = [P, P, P, I, ctypes.POINTER(I)]
     for nm in EXPORTS:
         getattr(L, nm).restype = I
@@ -252,6 +253,36 @@ class Plan:
         s = (stream or torch.cuda.current_stream()).cuda_stream
         _check(self._lib.ibf_apply_host(self._p, ctypes.c_void_p(ptr(src)), ctypes.c_void_p(ptr(dst)), nrhs,
                                         1 if adjoint else 0, ctypes.c_void_p(s)))
+
+    def apply_amplitude(self, v, alpha, beta, adjoint: bool = False, out=None, work=None, stream=None):
+        """u = A g (or g = A^* y with adjoint=True) for the amplitude
+        a(x, xi) = sum_t alpha[:, t] beta[:, t] (ibf_apply_amplitude).
+
+        `alpha`, `beta`: CUDA tensors of shape (N, q) and the plan's complex
+        dtype (rows: points in the caller's x order, resp. xi_k).  `v`: as in
+        `apply`.  `work`: optional 1-D scratch tensor of the plan's dtype; by
+        default 2 N q nrhs elements are allocated here (one pass)."""
+        torch = _torch()
+        src, nrhs = self._prep(v)
+        fa = [f.t().contiguous() for f in (alpha, beta)]      # column-major N x q == row-major (q, N)
+        q = fa[0].shape[0]
+        for f in fa:
+            if not f.is_cuda or f.dtype != self.cdtype or f.shape != (q, self.N):
+                raise ValueError("alpha and beta must be CUDA tensors of shape (N, q) and the plan's dtype")
+        if work is None:
+            work = torch.empty(2 * self.N * q * nrhs, dtype=self.cdtype, device=v.device)
+        elif not work.is_cuda or work.dtype != self.cdtype or not work.is_contiguous():
+            raise ValueError("work must be a contiguous CUDA tensor of the plan's dtype")
+        dst = torch.empty((nrhs, self.N), dtype=self.cdtype, device=v.device) if out is None else out
+        if dst.shape != (nrhs, self.N) or not dst.is_contiguous():
+            raise ValueError("out must be a contiguous (nrhs, N) tensor")
+        s = (stream or torch.cuda.current_stream(v.device)).cuda_stream
+        _check(self._lib.ibf_apply_amplitude(self._p, ctypes.c_void_p(fa[0].data_ptr()),
+                                             ctypes.c_void_p(fa[1].data_ptr()), q, ctypes.c_void_p(src.data_ptr()),
+                                             ctypes.c_void_p(dst.data_ptr()), nrhs, 1 if adjoint else 0,
+                                             ctypes.c_void_p(work.data_ptr()), work.numel(), ctypes.c_void_p(s)))
+        res = dst.t()
+        return res[:, 0] if v.dim() == 1 else res
 
 
 class Batch:

@@ -31,6 +31,7 @@ UNITS = {
     "ibf_2d_build.cu": ["-fmad=false"],
     "ibf_2d_apply.cu": [],
     "ibf_optimal.cu": [],
+    "ibf_amplitude.cu": [],
 }
 
 
