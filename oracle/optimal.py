@@ -26,6 +26,27 @@ The compressed factors have the preliminary IBF's block structure with r
 replaced by r0, so ``OptimalIBF.apply`` is the same sequence of block
 products: Lambda^0 = Vbar g, Hbar levels 1..h, identity switch, Gbar levels
 h+1..L, u = Ubar Lambda^L.
+
+With ``sweep_in=True`` the sweep-in stage (Sec. 4.3, eq. IBFin) follows,
+from the outer factors toward the middle:
+
+* Ubar = Udot C^L, per leaf: the rows of Ubar at the leaf's points
+  (n_i x r0) split as (n_i x K) (K x r0);
+* for l = L..h+1, per input pair q of level l-1, the stacked pencil
+  [C_{p0} Gbar_{p0,c}; C_{p1} Gbar_{p1,c}] = [Gdot_{p0,c}; Gdot_{p1,c}] C_q;
+* Vbar^* = R^0^* Vdot^*, per frequency leaf: the column Vbar_j (r0 x 1)
+  splits as (r0 x K) (K x 1);
+* for l = 1..h, per output pair p, the pencil
+  [Hbar_{p,0} R_{q0}^*, Hbar_{p,1} R_{q1}^*] = R_p^* [Hdot_{p,0}, Hdot_{p,1}];
+* Mdot = C^h Mbar R^h^* (Mbar is the identity after the sweep-out).
+
+The rank of each split is the number of points the boxes hold, capped at
+r0: an X box at level l holds at most K^G_l = min(max count, r0) points
+and an Omega box at level L-l holds 2^l frequencies, K^H_l = min(2^l, r0).
+A block with fewer points has at most that many independent rows, so every
+split is exact and the sweep-in leaves the operator unchanged (to
+rounding) while shrinking the outer blocks; with one point per leaf the
+leaf factors become 1 x 1.
 """
 from __future__ import annotations
 
@@ -48,9 +69,10 @@ def split_svd(Z: np.ndarray, r0: int) -> tuple[np.ndarray, np.ndarray]:
 
 
 class OptimalIBF:
-    """Sweep-out compression of the preliminary IBF to rank r0 (Sec. 4.2)."""
+    """Sweep-out compression of the preliminary IBF to rank r0 (Sec. 4.2),
+    optionally followed by the sweep-in stage (Sec. 4.3)."""
 
-    def __init__(self, phase_id: int, N: int, r: int, x, r0: int, h: int | None = None):
+    def __init__(self, phase_id: int, N: int, r: int, x, r0: int, h: int | None = None, sweep_in: bool = False):
         ex = ExplicitIBF(phase_id, N, r, x, h)
         self.N, self.r, self.r0, self.L, self.h = ex.N, ex.r, int(r0), ex.L, ex.h
         if not 1 <= self.r0 <= r:
@@ -99,9 +121,70 @@ class OptimalIBF:
             self.blocks[l] = B
             Rs = Rn
         self.V = np.einsum("kst,kt->ks", Rs, V)          # Vbar_k = R^0_k^* V_k
+        self.M = None                                    # identity middle factor
+        self.KG = {l: r0 for l in range(h, L + 1)}
+        self.KH = {l: r0 for l in range(0, h + 1)}
+        if sweep_in:
+            self._sweep_in()
+
+    def _sweep_in(self):
+        """Sec. 4.3: sweep from U^L and V^0 toward the middle (module docstring)."""
+        N, L, h, r0 = self.N, self.L, self.h, self.r0
+        KG = {l: min(int(np.bincount(self.leaf >> (L - l), minlength=1 << l).max()), r0) for l in range(h, L + 1)}
+        KH = {l: min(1 << l, r0) for l in range(0, h + 1)}
+        # Ubar = Udot C^L, leaf by leaf
+        C = np.zeros((N, KG[L], r0), np.complex128)
+        Ud = np.zeros((self.x.size, KG[L]), np.complex128)
+        for i in range(N):
+            rows = np.nonzero(self.leaf == i)[0]
+            if rows.size:
+                Ud[rows], C[i] = split_svd(self.U[rows], KG[L])
+        # C^l Gbar^(l-1 -> l) = Gdot C^(l-1), l = L .. h+1
+        for l in range(L, h, -1):
+            nj = 1 << (L - l)
+            nC = 2 * nj
+            Cn = np.zeros((N, KG[l - 1], r0), np.complex128)
+            B = np.zeros((N, 2, KG[l], KG[l - 1]), np.complex128)
+            for q in range(N):
+                ip, Cq = q // nC, q % nC
+                j, c = Cq >> 1, Cq & 1
+                p0, p1 = (2 * ip) * nj + j, (2 * ip + 1) * nj + j
+                Z = np.vstack([C[p0] @ self.blocks[l][p0, c], C[p1] @ self.blocks[l][p1, c]])
+                A, Cn[q] = split_svd(Z, KG[l - 1])
+                B[p0, c], B[p1, c] = A[:KG[l]], A[KG[l]:]
+            self.blocks[l] = B
+            C = Cn
+        # Vbar^* = R^0^* Vdot^*, leaf by leaf (one frequency per leaf)
+        Rs = np.zeros((N, r0, KH[0]), np.complex128)      # R^0_j^*
+        Vd = np.zeros((N, KH[0]), np.complex128)
+        for j in range(N):
+            Rs[j], Bv = split_svd(self.V[j][:, None], KH[0])
+            Vd[j] = Bv[:, 0]
+        # Hbar^(l-1 -> l) R^(l-1)^* = R^l^* Hdot, l = 1 .. h
+        for l in range(1, h + 1):
+            nj = 1 << (L - l)
+            Rn = np.zeros((N, r0, KH[l]), np.complex128)
+            B = np.zeros((N, 2, KH[l], KH[l - 1]), np.complex128)
+            for p in range(N):
+                i, j = p >> (L - l), p & (nj - 1)
+                q0 = (i >> 1) * (2 * nj) + 2 * j
+                P = np.hstack([self.blocks[l][p, 0] @ Rs[q0], self.blocks[l][p, 1] @ Rs[q0 + 1]])
+                Rn[p], Bp = split_svd(P, KH[l])
+                B[p, 0], B[p, 1] = Bp[:, :KH[l - 1]], Bp[:, KH[l - 1]:]
+            self.blocks[l] = B
+            Rs = Rn
+        self.M = np.einsum("pks,pst->pkt", C, Rs)          # Mdot = C^h I R^h^*
+        self.U, self.V, self.KG, self.KH = Ud, Vd, KG, KH
+
+    def nnz(self) -> int:
+        """Stored entries of the factors (V, the butterfly blocks, the middle
+        factor counted as r0 x r0 when it is the identity, U)."""
+        mid = self.N * self.r0 * self.r0 if self.M is None else self.M.size
+        return self.V.size + sum(b.size for b in self.blocks.values()) + mid + self.U.size
 
     def apply(self, g) -> np.ndarray:
-        """u = Ubar Gbar^{L-1..h} I Hbar^{h..1} Vbar g, g of shape (N,) or (N, nrhs)."""
+        """u = Ubar Gbar^{L-1..h} I Hbar^{h..1} Vbar g (after the sweep-in:
+        Udot Gdot Mdot Hdot Vdot g), g of shape (N,) or (N, nrhs)."""
         g = np.asarray(g, np.complex128)
         vec = g.ndim == 1
         g2 = g.reshape(self.N, -1)
@@ -114,6 +197,8 @@ class OptimalIBF:
             q0 = (i >> 1) * (2 * nj) + 2 * j
             B = self.blocks[l]
             lam = np.einsum("pts,psk->ptk", B[:, 0], lam[q0]) + np.einsum("pts,psk->ptk", B[:, 1], lam[q0 + 1])
+            if l == self.h and self.M is not None:
+                lam = np.einsum("pts,psk->ptk", self.M, lam)
         u = np.einsum("nt,ntk->nk", self.U, lam[self.leaf])
         return u[:, 0] if vec else u
 
@@ -123,15 +208,17 @@ class OptimalIBF:
         vec = y.ndim == 1
         y2 = y.reshape(self.x.size, -1)
         N, L = self.N, self.L
-        lam = np.zeros((N, self.r0, y2.shape[1]), np.complex128)
+        lam = np.zeros((N, self.U.shape[1], y2.shape[1]), np.complex128)
         np.add.at(lam, self.leaf, np.conj(self.U)[:, :, None] * y2[:, None, :])
         for l in range(L, 0, -1):
+            if l == self.h and self.M is not None:
+                lam = np.einsum("pts,ptk->psk", np.conj(self.M), lam)
             nj = 1 << (L - l)
             p = np.arange(N)
             i, j = p >> (L - l), p & (nj - 1)
             q0 = (i >> 1) * (2 * nj) + 2 * j
             B = self.blocks[l]
-            prev = np.zeros_like(lam)
+            prev = np.zeros((N, B.shape[3], lam.shape[2]), np.complex128)
             np.add.at(prev, q0, np.einsum("pts,ptk->psk", np.conj(B[:, 0]), lam))
             np.add.at(prev, q0 + 1, np.einsum("pts,ptk->psk", np.conj(B[:, 1]), lam))
             lam = prev

@@ -63,3 +63,55 @@ def test_error_does_not_grow_with_rank_and_adjoint():
     lhs = np.vdot(y, opt.apply(g))
     rhs = np.vdot(opt.adjoint(y), g)
     assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+# ---- sweep-in stage (Sec. 4.3)
+
+@pytest.mark.parametrize("phase,N,r,r0,rand", [(O.PHASE_FIO1D, 256, 9, 9, False), (O.PHASE_NUFFT, 256, 7, 7, True),
+                                               (O.PHASE_FIO1D, 64, 9, 9, False)])
+def test_sweep_in_full_rank_equals_preliminary(phase, N, r, r0, rand):
+    """Every sweep-in split has the rank of the points its boxes hold, so it is
+    exact: at full rank the fully compressed product is still the preliminary
+    IBF (N = 64 carries the sweep all the way into the middle factor)."""
+    x = W.random_sorted_x(N, W.rng(970)) if rand else W.uniform_x(N)
+    g = W.complex_normal((N, 2), W.rng(971))
+    ref = O.ExplicitIBF(phase, N, r, x).apply(g)
+    opt = OptimalIBF(phase, N, r, x, r0, sweep_in=True)
+    assert O.rel_l2(opt.apply(g), ref) < 1e-12
+
+
+@pytest.mark.parametrize("phase,N,r,r0,rand", [(O.PHASE_FIO1D, 512, 9, 6, False), (O.PHASE_NUFFT, 256, 9, 5, True),
+                                               (O.PHASE_FIO1D, 128, 12, 9, False)])
+def test_sweep_in_keeps_the_operator_and_shrinks_it(phase, N, r, r0, rand):
+    x = W.random_sorted_x(N, W.rng(972)) if rand else W.uniform_x(N)
+    g = W.complex_normal((N, 2), W.rng(973))
+    y = W.complex_normal((N, 2), W.rng(974))
+    out = OptimalIBF(phase, N, r, x, r0)
+    both = OptimalIBF(phase, N, r, x, r0, sweep_in=True)
+    assert O.rel_l2(both.apply(g), out.apply(g)) < 1e-12
+    assert O.rel_l2(both.adjoint(y), out.adjoint(y)) < 1e-12
+    assert abs(np.vdot(y, both.apply(g)) - np.vdot(both.adjoint(y), g)) < 1e-12 * np.linalg.norm(y) * np.linalg.norm(g) * N
+    L, h = both.L, both.h
+    # ranks are the point counts of the boxes, capped at r0
+    counts = np.bincount(np.clip(np.floor(x * N).astype(int), 0, N - 1), minlength=N)
+    assert both.KG[L] == min(counts.max(), r0)
+    assert all(both.KH[l] == min(2 ** l, r0) for l in range(h + 1))
+    if not rand:
+        assert all(both.KG[l] == min(2 ** (L - l), r0) for l in range(h, L + 1))
+        # one point per leaf: Ubar_n = Udot_n C_n with |Udot_n|^2 = |Ubar_n| (square roots of sigma on both sides)
+        assert both.U.shape[1] == 1
+        assert np.allclose(np.abs(both.U[:, 0]) ** 2, np.linalg.norm(out.U, axis=1))
+        assert np.allclose(np.abs(both.V[:, 0]) ** 2, np.linalg.norm(out.V, axis=1))
+    # stored entries, block by block
+    KG, KH = both.KG, both.KH
+    nnz = N * KH[0] + sum(2 * N * KH[l] * KH[l - 1] for l in range(1, h + 1)) + N * KG[h] * KH[h] \
+        + sum(2 * N * KG[l] * KG[l - 1] for l in range(h + 1, L + 1)) + N * KG[L]
+    assert both.nnz() == nnz < out.nnz()
+
+
+def test_sweep_in_separable_rank_one_is_exact():
+    N, r = 256, 7
+    x = W.uniform_x(N)
+    g = W.complex_normal((N, 2), W.rng(975))
+    opt = OptimalIBF(O.PHASE_SEPARABLE, N, r, x, 1, sweep_in=True)
+    assert O.rel_l2(opt.apply(g), O.direct_1d(O.PHASE_SEPARABLE, x, W.omega_1d(N), g)) < 1e-12
