@@ -234,15 +234,19 @@ def run_nufft_latency(ibf, torch, N=1024, reps=200):
 
 
 def run_optimal(ibf, torch, N=1 << 16, nrhs=8, reps=3):
-    """Optimal IBF (sweep-out stage, Sec. 4.2) against the preliminary IBF,
+    """Optimal IBF (sweep-out stage, Sec. 4.2, and with the sweep-in stage,
+    Sec. 4.3) against the preliminary IBF,
     FP64 explicit factors, 1D FIO N = 2^16, 8 columns: construction time,
     apply vectors/s, stored entries, and the relative L2 difference from the
     r = 12 preliminary IBF (itself ~7e-8 from the direct sum)."""
     gen = W.rng(workload=6)
     g = torch.from_numpy(W.complex_normal((N, nrhs), gen)).cuda()
     out, ref = [], None
+    names = {ibf.FORM_EXPLICIT: "preliminary", ibf.FORM_OPTIMAL: "optimal (sweep-out)",
+             ibf.FORM_OPTIMAL_IN: "optimal (sweep-out + sweep-in)"}
     for r, form, r0 in [(12, ibf.FORM_EXPLICIT, 0), (9, ibf.FORM_EXPLICIT, 0), (12, ibf.FORM_OPTIMAL, 9),
-                        (12, ibf.FORM_OPTIMAL, 7), (9, ibf.FORM_OPTIMAL, 7)]:
+                        (12, ibf.FORM_OPTIMAL_IN, 9), (12, ibf.FORM_OPTIMAL, 7), (12, ibf.FORM_OPTIMAL_IN, 7),
+                        (9, ibf.FORM_OPTIMAL, 7)]:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         p = ibf.Plan(ibf.PHASE_FIO1D, N, r, ibf.C128, form=form, rank=r0, max_nrhs=nrhs)
@@ -260,7 +264,7 @@ def run_optimal(ibf, torch, N=1 << 16, nrhs=8, reps=3):
         ms = e0.elapsed_time(e1) / reps
         if ref is None:
             ref = u.clone()
-        rec = {"form": "optimal" if form == ibf.FORM_OPTIMAL else "preliminary", "r": r,
+        rec = {"form": names[form], "r": r,
                "r0": r0 or r, "construct_ms": tc, "apply_ms": ms, "vectors_per_s": nrhs / (ms / 1e3),
                "nnz": p.query(ibf.Q_NNZ),
                "rel_diff_vs_r12_preliminary": float(torch.linalg.vector_norm(u - ref) / torch.linalg.vector_norm(ref))}

@@ -91,13 +91,18 @@ enum ibf_form {
                                 the two universal real Lagrange transfer matrices T_c
                                 and the diagonal phases of adjacent levels merged;
                                 several levels fused per kernel                       */
-    IBF_FORM_OPTIMAL = 3     /* the optimal IBF after the sweep-out stage of Sec. 4.2:
+    IBF_FORM_OPTIMAL = 3,    /* the optimal IBF after the sweep-out stage of Sec. 4.2:
                                 the explicit factors compressed from the middle level
                                 outward (eqs. KeqUCMRV, GC, HR) to blocks of rank
                                 ibf_options.rank by truncated SVDs, applied like the
-                                explicit form.  FP64 (IBF_C128), d = 1, r <= 12.
-                                The sweep-in stage (Sec. 4.3, for nonuniform points)
-                                is not part of it.                                    */
+                                explicit form.  FP64 (IBF_C128), d = 1, r <= 12.      */
+    IBF_FORM_OPTIMAL_IN = 4  /* IBF_FORM_OPTIMAL followed by the sweep-in stage of
+                                Sec. 4.3 (eq. IBFin): the outer factors compressed
+                                toward the middle, each block to the number of points
+                                its boxes hold (capped at the rank), so the operator is
+                                unchanged to rounding and the outer levels shrink
+                                (1 x 1 leaf factors with one point per leaf).  Same
+                                limits as IBF_FORM_OPTIMAL.                           */
 };
 
 /* Optional plan parameters; zero-initialise and set what you need. */

@@ -30,6 +30,7 @@ FORM_AUTO = 0
 FORM_EXPLICIT = 1
 FORM_STRUCTURED = 2
 FORM_OPTIMAL = 3
+FORM_OPTIMAL_IN = 4         # sweep-out then sweep-in (Sec. 4.3)
 
 Q_N, Q_L, Q_H, Q_R, Q_DTYPE, Q_FORM, Q_FACTOR_BYTES, Q_WORKSPACE_BYTES, Q_MAX_NRHS, Q_NNZ, Q_LAUNCHES, \
     Q_LEVELS_PER_LAUNCH, Q_RHS_TILE, Q_RANK = range(14)

@@ -6,6 +6,10 @@
 // (p r + t) nc + col, so the switch's reordering (Sec. 3, step 4) is only a
 // change of index arithmetic.  Each butterfly block maps
 // Lambda^{l-1}_{i/2, 2j+c} to Lambda^l_{i,j} (eqs. PIBF2, PIBF3).
+//
+// The optimal form runs the same kernels with its compressed blocks: rank r0
+// at every level after the sweep-out stage, and after the sweep-in stage a
+// rank per level (r_out x r_in blocks, an r_g x r_h middle factor).
 #include <algorithm>
 
 #include "ibf_internal.h"
@@ -44,35 +48,37 @@ __global__ void kx_init_adj(const cd* V, const cd* lam, cd* g, int64_t N, int r,
     g[k + N * col] = acc;
 }
 
-// one butterfly level l: out pair p = (i,j) from in pairs (i/2, 2j+c)
-__global__ void kx_level(const cd* blk, const cd* in, cd* out, int L, int l, int r, int nc, int64_t N)
+// one butterfly level l: out pair p = (i,j) (rank ro) from in pairs
+// (i/2, 2j+c) (rank ri) through the ro x ri blocks blk[p][c]
+__global__ void kx_level(const cd* blk, const cd* in, cd* out, int L, int l, int ro, int ri, int nc, int64_t N)
 {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= N * r * nc) return;
+    if (e >= N * ro * nc) return;
     int col = (int)(e % nc);
-    int t = (int)((e / nc) % r);
-    int64_t p = e / ((int64_t)nc * r);
+    int t = (int)((e / nc) % ro);
+    int64_t p = e / ((int64_t)nc * ro);
     int64_t nj = 1LL << (L - l);
     int64_t i = p >> (L - l), j = p & (nj - 1);
     int64_t q0 = (i >> 1) * (2 * nj) + 2 * j;
     cd acc = make_double2(0, 0);
     for (int c = 0; c < 2; ++c) {
-        const cd* row = blk + ((p * 2 + c) * r + t) * r;
-        const cd* v = in + (q0 + c) * r * nc + col;
-        for (int s = 0; s < r; ++s) cadd(acc, cmul(row[s], v[(int64_t)s * nc]));
+        const cd* row = blk + ((p * 2 + c) * ro + t) * ri;
+        const cd* v = in + (q0 + c) * ri * nc + col;
+        for (int s = 0; s < ri; ++s) cadd(acc, cmul(row[s], v[(int64_t)s * nc]));
     }
     out[e] = acc;
 }
 
 // adjoint of level l: in pair q = (i', C) at level l-1 gathers from the two
 // out pairs (2i'+a, C/2) at level l with the conjugated blocks
-__global__ void kx_level_adj(const cd* blk, const cd* out, cd* in, int L, int l, int r, int nc, int64_t N)
+__global__ void kx_level_adj(const cd* blk, const cd* out, cd* in, int L, int l, int ro, int ri, int nc,
+                             int64_t N)
 {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= N * r * nc) return;
+    if (e >= N * ri * nc) return;
     int col = (int)(e % nc);
-    int s = (int)((e / nc) % r);
-    int64_t q = e / ((int64_t)nc * r);
+    int s = (int)((e / nc) % ri);
+    int64_t q = e / ((int64_t)nc * ri);
     int64_t nC = 1LL << (L - l + 1), nj = nC >> 1;
     int64_t ip = q >> (L - l + 1), C = q & (nC - 1);
     int64_t j = C >> 1;
@@ -80,28 +86,30 @@ __global__ void kx_level_adj(const cd* blk, const cd* out, cd* in, int L, int l,
     cd acc = make_double2(0, 0);
     for (int a = 0; a < 2; ++a) {
         int64_t p = (2 * ip + a) * nj + j;
-        const cd* col_blk = blk + ((p * 2 + c) * r) * r + s;
-        const cd* v = out + p * r * nc + col;
-        for (int t = 0; t < r; ++t) cadd(acc, cmulc(col_blk[(int64_t)t * r], v[(int64_t)t * nc]));
+        const cd* col_blk = blk + ((p * 2 + c) * ro) * ri + s;
+        const cd* v = out + p * ro * nc + col;
+        for (int t = 0; t < ro; ++t) cadd(acc, cmulc(col_blk[(int64_t)t * ri], v[(int64_t)t * nc]));
     }
     in[e] = acc;
 }
 
-// switch at level h: out_p = M~_p in_p (eq. switchlocM), or its adjoint
-__global__ void kx_switch(const cd* M, const cd* in, cd* out, int r, int nc, int64_t N, int adj)
+// switch at level h: out_p = M~_p in_p (eq. switchlocM), M~_p of rows x cols
+// (rank after x rank before the switch), or its adjoint
+__global__ void kx_switch(const cd* M, const cd* in, cd* out, int rows, int cols, int nc, int64_t N, int adj)
 {
+    const int rout = adj ? cols : rows, rin = adj ? rows : cols;
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= N * r * nc) return;
+    if (e >= N * rout * nc) return;
     int col = (int)(e % nc);
-    int t = (int)((e / nc) % r);
-    int64_t p = e / ((int64_t)nc * r);
-    const cd* Mp = M + p * r * r;
-    const cd* v = in + p * r * nc + col;
+    int t = (int)((e / nc) % rout);
+    int64_t p = e / ((int64_t)nc * rout);
+    const cd* Mp = M + p * rows * cols;
+    const cd* v = in + p * rin * nc + col;
     cd acc = make_double2(0, 0);
     if (!adj)
-        for (int s = 0; s < r; ++s) cadd(acc, cmul(Mp[t * r + s], v[(int64_t)s * nc]));
+        for (int s = 0; s < cols; ++s) cadd(acc, cmul(Mp[t * cols + s], v[(int64_t)s * nc]));
     else
-        for (int s = 0; s < r; ++s) cadd(acc, cmulc(Mp[s * r + t], v[(int64_t)s * nc]));
+        for (int s = 0; s < rows; ++s) cadd(acc, cmulc(Mp[s * cols + t], v[(int64_t)s * nc]));
     out[e] = acc;
 }
 
@@ -135,33 +143,48 @@ __global__ void kx_term_adj(const cd* U, const int32_t* off, const int32_t* perm
 
 static inline unsigned nb(int64_t n) { return (unsigned)((n + 255) / 256); }
 
+// rank of Lambda^l before the switch (H side, l <= h) and after it (G side,
+// l >= h)
+static inline int rank_h(const ibf_plan* p, int l)
+{
+    return !p->rk_h.empty() ? p->rk_h[l] : (p->ra > 0 ? p->ra : p->r);
+}
+static inline int rank_g(const ibf_plan* p, int l)
+{
+    return !p->rk_g.empty() ? p->rk_g[l] : (p->ra > 0 ? p->ra : p->r);
+}
+// output and input rank of the butterfly blocks of level l
+static inline int rank_out(const ibf_plan* p, int l) { return l <= p->h ? rank_h(p, l) : rank_g(p, l); }
+static inline int rank_in(const ibf_plan* p, int l) { return l <= p->h ? rank_h(p, l - 1) : rank_g(p, l - 1); }
+
 int explicit_launches(const ibf_plan* p) { return p->L + 3; }
 
 int explicit_apply(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStream_t st)
 {
-    const int r = p->ra > 0 ? p->ra : p->r, L = p->L;   // r0 for the optimal form
+    const int L = p->L, h = p->h;
     const int64_t N = p->N;
+    const int k0 = rank_h(p, 0), kL = rank_g(p, L), mr = rank_g(p, h), mc = rank_h(p, h);
     for (int c0 = 0; c0 < nrhs; c0 += p->max_nrhs) {
         int nc = std::min(p->max_nrhs, nrhs - c0);
         const cd* g = (const cd*)gv + N * c0;
         cd* u = (cd*)uv + p->nx * c0;
         cd* a = (cd*)p->ws[0];
         cd* b = (cd*)p->ws[1];
-        int64_t tot = N * r * nc;
         prof_start(p, st);
-        kx_init<<<nb(tot), 256, 0, st>>>((const cd*)p->eV, g, a, N, r, nc);
+        kx_init<<<nb(N * k0 * nc), 256, 0, st>>>((const cd*)p->eV, g, a, N, k0, nc);
         prof_mark(p, st, IBF_K_EXPLICIT_INIT);
         for (int l = 1; l <= L; ++l) {
-            kx_level<<<nb(tot), 256, 0, st>>>((const cd*)p->eblk[l], a, b, L, l, r, nc, N);
+            const int ro = rank_out(p, l), ri = rank_in(p, l);
+            kx_level<<<nb(N * ro * nc), 256, 0, st>>>((const cd*)p->eblk[l], a, b, L, l, ro, ri, nc, N);
             prof_mark(p, st, IBF_K_EXPLICIT_LEVEL);
             std::swap(a, b);
-            if (l == p->h) {
-                kx_switch<<<nb(tot), 256, 0, st>>>((const cd*)p->eM, a, b, r, nc, N, 0);
+            if (l == h) {
+                kx_switch<<<nb(N * mr * nc), 256, 0, st>>>((const cd*)p->eM, a, b, mr, mc, nc, N, 0);
                 prof_mark(p, st, IBF_K_EXPLICIT_SWITCH);
                 std::swap(a, b);
             }
         }
-        kx_term<<<nb(p->nx * nc), 256, 0, st>>>((const cd*)p->eU, p->d_leaf, p->d_perm, a, u, p->nx, r, nc);
+        kx_term<<<nb(p->nx * nc), 256, 0, st>>>((const cd*)p->eU, p->d_leaf, p->d_perm, a, u, p->nx, kL, nc);
         prof_mark(p, st, IBF_K_EXPLICIT_TERM);
     }
     cudaError_t e = cudaGetLastError();
@@ -170,29 +193,30 @@ int explicit_apply(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStream_t
 
 int explicit_adjoint(ibf_plan* p, const void* yv, void* gv, int nrhs, cudaStream_t st)
 {
-    const int r = p->ra > 0 ? p->ra : p->r, L = p->L;   // r0 for the optimal form
+    const int L = p->L, h = p->h;
     const int64_t N = p->N;
+    const int k0 = rank_h(p, 0), kL = rank_g(p, L), mr = rank_g(p, h), mc = rank_h(p, h);
     for (int c0 = 0; c0 < nrhs; c0 += p->max_nrhs) {
         int nc = std::min(p->max_nrhs, nrhs - c0);
         const cd* y = (const cd*)yv + p->nx * c0;
         cd* g = (cd*)gv + N * c0;
         cd* a = (cd*)p->ws[0];
         cd* b = (cd*)p->ws[1];
-        int64_t tot = N * r * nc;
         prof_start(p, st);
-        kx_term_adj<<<nb(tot), 256, 0, st>>>((const cd*)p->eU, p->d_off, p->d_perm, y, a, N, p->nx, r, nc);
+        kx_term_adj<<<nb(N * kL * nc), 256, 0, st>>>((const cd*)p->eU, p->d_off, p->d_perm, y, a, N, p->nx, kL, nc);
         prof_mark(p, st, IBF_K_EXPLICIT_TERM);
         for (int l = L; l >= 1; --l) {
-            if (l == p->h) {
-                kx_switch<<<nb(tot), 256, 0, st>>>((const cd*)p->eM, a, b, r, nc, N, 1);
+            if (l == h) {
+                kx_switch<<<nb(N * mc * nc), 256, 0, st>>>((const cd*)p->eM, a, b, mr, mc, nc, N, 1);
                 prof_mark(p, st, IBF_K_EXPLICIT_SWITCH);
                 std::swap(a, b);
             }
-            kx_level_adj<<<nb(tot), 256, 0, st>>>((const cd*)p->eblk[l], a, b, L, l, r, nc, N);
+            const int ro = rank_out(p, l), ri = rank_in(p, l);
+            kx_level_adj<<<nb(N * ri * nc), 256, 0, st>>>((const cd*)p->eblk[l], a, b, L, l, ro, ri, nc, N);
             prof_mark(p, st, IBF_K_EXPLICIT_LEVEL);
             std::swap(a, b);
         }
-        kx_init_adj<<<nb(N * nc), 256, 0, st>>>((const cd*)p->eV, a, g, N, r, nc);
+        kx_init_adj<<<nb(N * nc), 256, 0, st>>>((const cd*)p->eV, a, g, N, k0, nc);
         prof_mark(p, st, IBF_K_EXPLICIT_INIT);
     }
     cudaError_t e = cudaGetLastError();

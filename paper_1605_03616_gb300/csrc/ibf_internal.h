@@ -28,6 +28,10 @@ struct ibf_plan {
     int max_nrhs = 0;
     int kfuse = 0, rtile = 0;   // structured form launch shape
     int ra = 0;                 // optimal form: rank r0 of the compressed blocks (0: r)
+    // optimal form after the sweep-in stage: rank of Lambda^l before the
+    // switch (rk_h[l], l = 0..h) and after it (rk_g[l], l = h..L); empty:
+    // every level has rank ra (or r)
+    std::vector<int> rk_h, rk_g;
     bool user_kfuse = false, user_rtile = false;
 
     // Chebyshev grid on [-1/2,1/2] and the two child-to-parent Lagrange
@@ -95,6 +99,8 @@ int build_structured(ibf_plan* p);
 // alloc returns device memory owned by the plan (nullptr on failure), release
 // frees one such block
 int compress_optimal(ibf_plan* p, int r0, void* (*alloc)(ibf_plan*, size_t), void (*release)(ibf_plan*, void*));
+int sweep_in_optimal(ibf_plan* p, const std::vector<int32_t>& off, void* (*alloc)(ibf_plan*, size_t),
+                     void (*release)(ibf_plan*, void*));
 
 // explicit-form apply (ibf_explicit.cu), FP64
 int explicit_apply(ibf_plan* p, const void* g, void* u, int nrhs, cudaStream_t s);

@@ -1,4 +1,5 @@
-// Optimal IBF, sweep-out stage (Sec. 4.1-4.2), FP64 on the GPU.
+// Optimal IBF, sweep-out stage (Sec. 4.1-4.2) and sweep-in stage (Sec. 4.3),
+// FP64 on the GPU.
 //
 // Starts from the explicit preliminary factors (V^0, H^l, M^h, G^l, U^L of
 // Sec. 3, built by build_explicit) and compresses every block to rank r0:
@@ -301,6 +302,297 @@ int compress_optimal(ibf_plan* p, int r0, void* (*alloc)(ibf_plan*, size_t), voi
     for (int l = 1; l <= L; ++l) p->eblk[l] = bar[l];
     p->ra = r0;
     p->nnz = N * r0 + (int64_t)L * N * 2 * r0 * r0 + N * r0 * r0 + p->nx * r0;
+    return IBF_OK;
+}
+
+// ---------------------------------------------------------------- sweep-in
+//
+// Sec. 4.3: after the sweep-out, the outer factors are compressed toward the
+// middle.  G side: Ubar = Udot C^L per leaf, then for l = L..h+1, per input
+// pair q of level l-1, [C_{p0} Gbar_{p0,c}; C_{p1} Gbar_{p1,c}] =
+// [Gdot_{p0,c}; Gdot_{p1,c}] C_q.  H side: Vbar_j = A_j Vdot_j per frequency
+// leaf, then for l = 1..h, per output pair p, [Hbar_{p,0} A_{q0},
+// Hbar_{p,1} A_{q1}] = A_p [Hdot_{p,0}, Hdot_{p,1}] (A = R^*).  Middle:
+// Mdot = C^h Mbar A^h with Mbar = I.  The rank of each split is the number
+// of points the boxes hold, capped at r0 (K^G_l: the largest X-box count at
+// level l; K^H_l = 2^l frequencies), so every split is exact.  Once a side's
+// rank reaches r0 the remaining splits would only change bases: that side
+// stops, merging its last C (or A) into the next level's blocks.
+
+// per leaf i (n <= K < r0 points): X = Ubar_i^* (r0 x n); Ubar_i = J W^*
+__global__ void kI_leaf_u(const cd* Ubar, const int32_t* off, cd* Ud, cd* C, int64_t N, int r0, int K)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int n0 = off[i];
+    const int n = min(off[i + 1] - n0, K);      // K bounds every leaf's count
+    cd X[kOptMaxR * kOptMaxR], J[kOptMaxR * kOptMaxR];
+    for (int a = 0; a < n; ++a)
+        for (int s = 0; s < r0; ++s) X[a * r0 + s] = cconj(Ubar[(int64_t)(n0 + a) * r0 + s]);
+    if (n > 0) jacobi_columns(X, r0, n, J);
+    int idx[kOptMaxR];
+    double sig[kOptMaxR];
+    top_columns(X, r0, n, K, idx, sig);
+    for (int k = 0; k < K; ++k) {
+        const double sq = sqrt(sig[k]), inv = sig[k] > 0.0 ? 1.0 / sq : 0.0;
+        for (int a = 0; a < n; ++a) {
+            const cd jv = idx[k] >= 0 ? J[idx[k] * n + a] : cz();
+            Ud[(int64_t)(n0 + a) * K + k] = make_double2(jv.x * sq, jv.y * sq);
+        }
+        for (int s = 0; s < r0; ++s) {
+            const cd w = idx[k] >= 0 ? cconj(X[idx[k] * r0 + s]) : cz();
+            C[(i * K + k) * r0 + s] = make_double2(w.x * inv, w.y * inv);
+        }
+    }
+}
+
+// G side, level l: input pair q of level l-1 feeds outputs p_a = (2 ip + a,
+// C/2) through child c; Z = [C_{p0} B_{p0,c}; C_{p1} B_{p1,c}] (2 ko x r0)
+// = [Gdot_{p0,c}; Gdot_{p1,c}] Cnew_q with Cnew_q ki x r0 and Gdot ko x ki
+__global__ void kI_g(const cd* blk, const cd* Cin, cd* Cout, cd* Gd, int L, int l, int64_t N, int r0, int ko, int ki)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= N) return;
+    const int64_t nj = 1LL << (L - l), nC = 2 * nj;
+    const int64_t ip = q / nC, Cq = q % nC, j = Cq >> 1;
+    const int c = (int)(Cq & 1);
+    const int m = 2 * ko;
+    cd X[2 * kOptMaxR * kOptMaxR], J[kOptMaxR * kOptMaxR];
+    for (int a = 0; a < 2; ++a) {
+        const int64_t pa = (2 * ip + a) * nj + j;
+        const cd* B = blk + (pa * 2 + c) * r0 * r0;
+        const cd* Cp = Cin + pa * ko * r0;
+        for (int k = 0; k < ko; ++k)
+            for (int s = 0; s < r0; ++s) {
+                cd acc = cz();
+                for (int t = 0; t < r0; ++t) cmac(acc, Cp[k * r0 + t], B[t * r0 + s]);
+                X[s * m + a * ko + k] = acc;
+            }
+    }
+    jacobi_columns(X, m, r0, J);
+    int idx[kOptMaxR];
+    double sig[kOptMaxR];
+    top_columns(X, m, r0, ki, idx, sig);
+    for (int k = 0; k < ki; ++k) {
+        const double sq = sqrt(sig[k]), inv = sig[k] > 0.0 ? 1.0 / sq : 0.0;
+        for (int s = 0; s < r0; ++s) {
+            const cd jv = idx[k] >= 0 ? cconj(J[idx[k] * r0 + s]) : cz();
+            Cout[(q * ki + k) * r0 + s] = make_double2(jv.x * sq, jv.y * sq);
+        }
+        for (int a = 0; a < 2; ++a) {
+            const int64_t pa = (2 * ip + a) * nj + j;
+            for (int k2 = 0; k2 < ko; ++k2) {
+                const cd w = idx[k] >= 0 ? X[idx[k] * m + a * ko + k2] : cz();
+                Gd[((pa * 2 + c) * ko + k2) * ki + k] = make_double2(w.x * inv, w.y * inv);
+            }
+        }
+    }
+}
+
+// G side stops: Gdot_{p,c} = C_p B_{p,c} (ko x r0), one thread per entry
+__global__ void kI_gmerge(const cd* blk, const cd* Cin, cd* Gd, int64_t N, int r0, int ko)
+{
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= N * 2 * ko * r0) return;
+    const int s = (int)(e % r0), k = (int)((e / r0) % ko);
+    const int64_t pc = e / ((int64_t)r0 * ko), p = pc >> 1;
+    cd acc = cz();
+    for (int t = 0; t < r0; ++t) cmac(acc, Cin[(p * ko + k) * r0 + t], blk[(pc * r0 + t) * r0 + s]);
+    Gd[e] = acc;
+}
+
+// per frequency leaf j (one frequency): Vbar_j (r0 x 1) = A_j Vdot_j with
+// sigma = |Vbar_j|, A_j = Vbar_j / sqrt(sigma), Vdot_j = sqrt(sigma)
+__global__ void kI_leaf_v(const cd* Vbar, cd* Vd, cd* A, int64_t N, int r0)
+{
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    double s2 = 0.0;
+    for (int t = 0; t < r0; ++t) s2 += Vbar[j * r0 + t].x * Vbar[j * r0 + t].x + Vbar[j * r0 + t].y * Vbar[j * r0 + t].y;
+    const double sq = sqrt(sqrt(s2)), inv = s2 > 0.0 ? 1.0 / sq : 0.0;
+    Vd[j] = make_double2(sq, 0.0);
+    for (int t = 0; t < r0; ++t) A[j * r0 + t] = make_double2(Vbar[j * r0 + t].x * inv, Vbar[j * r0 + t].y * inv);
+}
+
+// H side, level l: output pair p = (i, j) reads q0 + c = (i/2, 2j+c);
+// P = [B_{p,0} A_{q0}, B_{p,1} A_{q1}] (r0 x 2 ki) = Anew_p (r0 x ko) [Hdot_{p,0}, Hdot_{p,1}]
+__global__ void kI_h(const cd* blk, const cd* Ain, cd* Aout, cd* Hd, int L, int l, int64_t N, int r0, int ki, int ko)
+{
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= N) return;
+    const int64_t nj = 1LL << (L - l);
+    const int64_t i = p >> (L - l), j = p & (nj - 1);
+    const int64_t q0 = (i >> 1) * (2 * nj) + 2 * j;
+    const int m = 2 * ki;
+    cd X[2 * kOptMaxR * kOptMaxR], J[kOptMaxR * kOptMaxR];
+    // X = P^* (2 ki x r0)
+    for (int c = 0; c < 2; ++c)
+        for (int t = 0; t < r0; ++t) {
+            const cd* row = blk + ((p * 2 + c) * r0 + t) * r0;
+            const cd* Aq = Ain + (q0 + c) * r0 * ki;
+            for (int k = 0; k < ki; ++k) {
+                cd acc = cz();
+                for (int s = 0; s < r0; ++s) cmac(acc, row[s], Aq[s * ki + k]);
+                X[t * m + c * ki + k] = cconj(acc);
+            }
+        }
+    jacobi_columns(X, m, r0, J);
+    int idx[kOptMaxR];
+    double sig[kOptMaxR];
+    top_columns(X, m, r0, ko, idx, sig);
+    for (int k = 0; k < ko; ++k) {
+        const double sq = sqrt(sig[k]), inv = sig[k] > 0.0 ? 1.0 / sq : 0.0;
+        for (int t = 0; t < r0; ++t) {
+            const cd jv = idx[k] >= 0 ? J[idx[k] * r0 + t] : cz();
+            Aout[(p * r0 + t) * ko + k] = make_double2(jv.x * sq, jv.y * sq);
+        }
+        for (int c = 0; c < 2; ++c)
+            for (int s = 0; s < ki; ++s) {
+                const cd w = idx[k] >= 0 ? cconj(X[idx[k] * m + c * ki + s]) : cz();
+                Hd[((p * 2 + c) * ko + k) * ki + s] = make_double2(w.x * inv, w.y * inv);
+            }
+    }
+}
+
+// H side stops: Hdot_{p,c} = B_{p,c} A_{q_c} (r0 x ki), one thread per entry
+__global__ void kI_hmerge(const cd* blk, const cd* Ain, cd* Hd, int L, int l, int64_t N, int r0, int ki)
+{
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= N * 2 * r0 * ki) return;
+    const int k = (int)(e % ki), t = (int)((e / ki) % r0);
+    const int64_t pc = e / ((int64_t)ki * r0), p = pc >> 1;
+    const int c = (int)(pc & 1);
+    const int64_t nj = 1LL << (L - l);
+    const int64_t i = p >> (L - l), j = p & (nj - 1);
+    const int64_t q = (i >> 1) * (2 * nj) + 2 * j + c;
+    cd acc = cz();
+    for (int s = 0; s < r0; ++s) cmac(acc, blk[(pc * r0 + t) * r0 + s], Ain[(q * r0 + s) * ki + k]);
+    Hd[e] = acc;
+}
+
+// Mdot_p = C^h_p A^h_p (kg x kh); a NULL side is the identity (its rank is r0)
+__global__ void kI_mid(const cd* Cg, const cd* Ah, cd* Md, int64_t N, int r0, int kg, int kh)
+{
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= N * kg * kh) return;
+    const int k2 = (int)(e % kh), k = (int)((e / kh) % kg);
+    const int64_t p = e / ((int64_t)kg * kh);
+    cd acc = cz();
+    if (!Cg)
+        acc = Ah[(p * r0 + k) * kh + k2];
+    else if (!Ah)
+        acc = Cg[(p * kg + k) * r0 + k2];
+    else
+        for (int s = 0; s < r0; ++s) cmac(acc, Cg[(p * kg + k) * r0 + s], Ah[(p * r0 + s) * kh + k2]);
+    Md[e] = acc;
+}
+
+int sweep_in_optimal(ibf_plan* p, const std::vector<int32_t>& off, void* (*alloc)(ibf_plan*, size_t),
+                     void (*release)(ibf_plan*, void*))
+{
+    const int64_t N = p->N;
+    const int L = p->L, h = p->h, r0 = p->ra;
+    const size_t c16 = sizeof(cd);
+    // ranks: the largest point count of the X boxes of level l, and the 2^l
+    // frequencies of the Omega boxes of level L - l, capped at r0
+    std::vector<int> KG(L + 1, r0), KH(h + 1, r0);
+    for (int l = h; l <= L; ++l) {
+        const int64_t w = 1LL << (L - l);
+        int64_t mx = 0;
+        for (int64_t i = 0; i < (1LL << l); ++i) mx = std::max<int64_t>(mx, off[(i + 1) * w] - off[i * w]);
+        KG[l] = (int)std::min<int64_t>(mx, r0);
+    }
+    for (int l = 0; l <= h; ++l) KH[l] = (int)std::min<int64_t>(1LL << std::min(l, 40), r0);
+    const int B = 64;
+    auto fail = [&](const char* what) { return set_error(IBF_ERR_OOM, what); };
+    // a factor is freed only after the kernels that read it have finished
+    auto drop = [&](void* q) {
+        if (!q) return;
+        cudaDeviceSynchronize();
+        release(p, q);
+    };
+    // G side
+    cd* C = nullptr;
+    if (KG[L] < r0) {
+        cd* Ud = (cd*)alloc(p, c16 * p->nx * KG[L]);
+        C = (cd*)alloc(p, c16 * N * KG[L] * r0);
+        if (!Ud || !C) return fail("sweep-in: factor allocation");
+        kI_leaf_u<<<nbk(N, B), B>>>((const cd*)p->eU, p->d_off, Ud, C, N, r0, KG[L]);
+        drop(p->eU);
+        p->eU = Ud;
+        for (int l = L; l > h; --l) {
+            const int ko = KG[l], ki = KG[l - 1];
+            if (ki < r0) {
+                cd* Cn = (cd*)alloc(p, c16 * N * ki * r0);
+                cd* Gd = (cd*)alloc(p, c16 * N * 2 * ko * ki);
+                if (!Cn || !Gd) return fail("sweep-in: factor allocation");
+                kI_g<<<nbk(N, B), B>>>((const cd*)p->eblk[l], C, Cn, Gd, L, l, N, r0, ko, ki);
+                drop(C);
+                drop(p->eblk[l]);
+                p->eblk[l] = Gd;
+                C = Cn;
+            } else {
+                cd* Gd = (cd*)alloc(p, c16 * N * 2 * ko * r0);
+                if (!Gd) return fail("sweep-in: factor allocation");
+                kI_gmerge<<<nbk(N * 2 * ko * r0, 256), 256>>>((const cd*)p->eblk[l], C, Gd, N, r0, ko);
+                drop(C);
+                C = nullptr;
+                drop(p->eblk[l]);
+                p->eblk[l] = Gd;
+                break;
+            }
+        }
+    }
+    // H side
+    cd* A = nullptr;
+    if (KH[0] < r0) {
+        cd* Vd = (cd*)alloc(p, c16 * N * KH[0]);
+        A = (cd*)alloc(p, c16 * N * r0 * KH[0]);
+        if (!Vd || !A) return fail("sweep-in: factor allocation");
+        kI_leaf_v<<<nbk(N, 256), 256>>>((const cd*)p->eV, Vd, A, N, r0);
+        drop(p->eV);
+        p->eV = Vd;
+        for (int l = 1; l <= h; ++l) {
+            const int ki = KH[l - 1], ko = KH[l];
+            if (ko < r0) {
+                cd* An = (cd*)alloc(p, c16 * N * r0 * ko);
+                cd* Hd = (cd*)alloc(p, c16 * N * 2 * ko * ki);
+                if (!An || !Hd) return fail("sweep-in: factor allocation");
+                kI_h<<<nbk(N, B), B>>>((const cd*)p->eblk[l], A, An, Hd, L, l, N, r0, ki, ko);
+                drop(A);
+                drop(p->eblk[l]);
+                p->eblk[l] = Hd;
+                A = An;
+            } else {
+                cd* Hd = (cd*)alloc(p, c16 * N * 2 * r0 * ki);
+                if (!Hd) return fail("sweep-in: factor allocation");
+                kI_hmerge<<<nbk(N * 2 * r0 * ki, 256), 256>>>((const cd*)p->eblk[l], A, Hd, L, l, N, r0, ki);
+                drop(A);
+                A = nullptr;
+                drop(p->eblk[l]);
+                p->eblk[l] = Hd;
+                break;
+            }
+        }
+    }
+    // middle: either side that reached level h with rank below r0
+    if (C || A) {
+        cd* Md = (cd*)alloc(p, c16 * N * KG[h] * KH[h]);
+        if (!Md) return fail("sweep-in: factor allocation");
+        kI_mid<<<nbk(N * KG[h] * KH[h], 256), 256>>>(C, A, Md, N, r0, KG[h], KH[h]);
+        drop(p->eM);
+        p->eM = Md;
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    drop(C);
+    drop(A);
+    if (e != cudaSuccess) return cuda_error(e, "optimal IBF sweep-in");
+    p->rk_h = KH;
+    p->rk_g = KG;
+    int64_t nnz = N * KH[0] + N * (int64_t)KG[h] * KH[h] + p->nx * KG[L];
+    for (int l = 1; l <= h; ++l) nnz += N * 2 * (int64_t)KH[l] * KH[l - 1];
+    for (int l = h + 1; l <= L; ++l) nnz += N * 2 * (int64_t)KG[l] * KG[l - 1];
+    p->nnz = nnz;
     return IBF_OK;
 }
 

@@ -432,7 +432,7 @@ static int create_2d(int phase_id, int64_t N, int r, int dtype, const double* x,
     ibf_options o;
     memset(&o, 0, sizeof(o));
     if (opt) o = *opt;
-    if (o.form == IBF_FORM_EXPLICIT || o.form == IBF_FORM_OPTIMAL)
+    if (o.form == IBF_FORM_EXPLICIT || o.form == IBF_FORM_OPTIMAL || o.form == IBF_FORM_OPTIMAL_IN)
         return set_error(IBF_ERR_UNSUPPORTED, "2D: structured form only");
     ibf_plan* p = new ibf_plan();
     p->phase_id = phase_id;
@@ -490,9 +490,11 @@ extern "C" int ibf_plan_create_ex(int phase_id, int d, int64_t N, int r, int dty
     memset(&o, 0, sizeof(o));
     if (opt) o = *opt;
     int form = o.form == IBF_FORM_AUTO ? (dtype == IBF_C128 ? IBF_FORM_EXPLICIT : IBF_FORM_STRUCTURED) : o.form;
-    if (form != IBF_FORM_EXPLICIT && form != IBF_FORM_STRUCTURED && form != IBF_FORM_OPTIMAL)
+    if (form != IBF_FORM_EXPLICIT && form != IBF_FORM_STRUCTURED && form != IBF_FORM_OPTIMAL &&
+        form != IBF_FORM_OPTIMAL_IN)
         return set_error(IBF_ERR_INVALID, "unknown form");
-    if (form == IBF_FORM_OPTIMAL) {
+    const bool optimal = form == IBF_FORM_OPTIMAL || form == IBF_FORM_OPTIMAL_IN;
+    if (optimal) {
         if (dtype != IBF_C128) return set_error(IBF_ERR_UNSUPPORTED, "the optimal form is FP64 (IBF_C128) only");
         if (r > 12) return set_error(IBF_ERR_UNSUPPORTED, "the optimal form supports r <= 12");
         if (o.rank < 1 || o.rank > r) return set_error(IBF_ERR_INVALID, "optimal form: rank must be in [1, r]");
@@ -569,8 +571,9 @@ extern "C" int ibf_plan_create_ex(int phase_id, int d, int64_t N, int r, int dty
     cudaMemcpy(p->d_leaf, leaf.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice);
 
     rc = form == IBF_FORM_STRUCTURED ? build_structured(p) : build_explicit(p);
-    if (!rc && form == IBF_FORM_OPTIMAL) {
+    if (!rc && optimal) {
         rc = compress_optimal(p, o.rank, opt_alloc, opt_release);
+        if (!rc && form == IBF_FORM_OPTIMAL_IN) rc = sweep_in_optimal(p, off, opt_alloc, opt_release);
         if (!rc) p->factor_bytes = sizeof(double2) * (size_t)p->nnz;
     }
     if (rc) {

@@ -77,3 +77,45 @@ def test_optimal_rejects_bad_options(ibf):
     with pytest.raises(ibf.IBFError) as e:
         ibf.Plan(ibf.PHASE_FIO1D, 256, 13, ibf.C128, form=ibf.FORM_OPTIMAL, rank=6)
     assert e.value.code == 4
+    for kw, code in [(dict(dtype=ibf.C64_FP32, rank=4), 4), (dict(dtype=ibf.C128, rank=0), 1)]:
+        with pytest.raises(ibf.IBFError) as e:
+            ibf.Plan(ibf.PHASE_FIO1D, 256, 9, form=ibf.FORM_OPTIMAL_IN, **kw)
+        assert e.value.code == code
+    with pytest.raises(ibf.IBFError) as e:
+        ibf.Plan(ibf.PHASE_FIO2D, 32 * 32, 7, ibf.C128, d=2, form=ibf.FORM_OPTIMAL_IN, rank=4)
+    assert e.value.code == 4
+
+
+@pytest.mark.parametrize("phase,N,r,r0,nrhs", [
+    (O.PHASE_FIO1D, 1024, 9, 6, 2),
+    (O.PHASE_NUFFT, 1024, 9, 5, 3),       # random points: the leaf ranks follow the fullest leaf
+    (O.PHASE_FIO1D, 2048, 12, 9, 1),
+    (O.PHASE_FIO1D, 64, 9, 9, 2),         # both sides of the sweep-in reach the middle factor
+])
+def test_sweep_in_matches_oracle_and_keeps_the_operator(ibf, phase, N, r, r0, nrhs):
+    """Sweep-in (Sec. 4.3) on the GPU: its splits are exact, so the plan must
+    give the sweep-out plan's results to rounding with fewer stored entries,
+    exactly as many as the oracle's sweep-in, and match the oracle's optimal
+    IBF like the sweep-out form does."""
+    x = W.random_sorted_x(N, W.rng(963)) if phase == O.PHASE_NUFFT else W.uniform_x(N)
+    g = W.complex_normal((N, nrhs), W.rng(964))
+    y = W.complex_normal((N, nrhs), W.rng(965))
+    kw = dict(x=x if phase == O.PHASE_NUFFT else None, rank=r0)
+    pin = ibf.Plan(phase, N, r, ibf.C128, form=ibf.FORM_OPTIMAL_IN, **kw)
+    pout = ibf.Plan(phase, N, r, ibf.C128, form=ibf.FORM_OPTIMAL, **kw)
+    assert pin.query(ibf.Q_FORM) == ibf.FORM_OPTIMAL_IN and pin.query(ibf.Q_RANK) == r0
+    ui, uo = pin.apply(_dev(g)).cpu().numpy(), pout.apply(_dev(g)).cpu().numpy()
+    gi, go = pin.adjoint(_dev(y)).cpu().numpy(), pout.adjoint(_dev(y)).cpu().numpy()
+    ref = OptimalIBF(phase, N, r, x, r0, sweep_in=True)
+    e_io, e_ioa = O.rel_l2(ui, uo), O.rel_l2(gi, go)
+    ef, ea = O.rel_l2(ui, ref.apply(g)), O.rel_l2(gi, ref.adjoint(y))
+    trunc = O.rel_l2(ref.apply(g), O.ExplicitIBF(phase, N, r, x).apply(g))
+    tol = max(1e-10, 1e-3 * trunc)
+    print("\nsweep-in phase=%d N=%d r=%d r0=%d: vs sweep-out fwd %.2e adj %.2e; vs oracle fwd %.2e adj %.2e "
+          "(tol %.1e); nnz %d -> %d" % (phase, N, r, r0, e_io, e_ioa, ef, ea, tol, pout.query(ibf.Q_NNZ),
+                                         pin.query(ibf.Q_NNZ)))
+    assert pin.query(ibf.Q_NNZ) == ref.nnz() < pout.query(ibf.Q_NNZ)
+    assert e_io < 1e-11 and e_ioa < 1e-11
+    assert ef < tol and ea < tol
+    pin.close()
+    pout.close()
