@@ -1,4 +1,4 @@
-// Explicit-form apply of the preliminary IBF (Sec. 3), FP64: the plain form.
+// Explicit-form apply of the preliminary IBF (Sec. 3): the plain form.
 //
 // u = U^L G^{L-1} ... G^h M^h (H^h)^* ... (H^1)^* (V^0)^* g, one kernel per
 // factor.  Lambda^l_{i,j} (r complex per box pair and right-hand side) is kept
@@ -16,16 +16,32 @@
 
 namespace ibf {
 
-typedef double2 cd;
+// Kernels are templates on the complex type: double2 for FP64 plans, float2
+// for FP32 plans (factors built in FP64, then stored in FP32).
+template <typename cx> struct RealOf;
+template <> struct RealOf<double2> { typedef double T; };
+template <> struct RealOf<float2> { typedef float T; };
 
-__device__ __forceinline__ cd cmul(cd a, cd b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
-__device__ __forceinline__ cd cmulc(cd a, cd b)  // conj(a) * b
+template <typename cx>
+__device__ __forceinline__ cx cmk(typename RealOf<cx>::T re, typename RealOf<cx>::T im)
 {
-    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+    cx o;
+    o.x = re;
+    o.y = im;
+    return o;
 }
-__device__ __forceinline__ void cadd(cd& a, cd b) { a.x += b.x; a.y += b.y; }
+template <typename cx>
+__device__ __forceinline__ cx cmul(cx a, cx b) { return cmk<cx>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+template <typename cx>
+__device__ __forceinline__ cx cmulc(cx a, cx b)  // conj(a) * b
+{
+    return cmk<cx>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+template <typename cx>
+__device__ __forceinline__ void cadd(cx& a, cx b) { a.x += b.x; a.y += b.y; }
 
 // Lambda^0[k][t][col] = V[k][t] g[k + N col]       ((V^0)^* g, eq. step2mv1)
+template <typename cd>
 __global__ void kx_init(const cd* V, const cd* g, cd* lam, int64_t N, int r, int nc)
 {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -37,19 +53,21 @@ __global__ void kx_init(const cd* V, const cd* g, cd* lam, int64_t N, int r, int
 }
 
 // g[k + N col] = sum_t conj(V[k][t]) Lambda^0[k][t][col]
+template <typename cd>
 __global__ void kx_init_adj(const cd* V, const cd* lam, cd* g, int64_t N, int r, int nc)
 {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= N * nc) return;
     int64_t k = e % N;
     int col = (int)(e / N);
-    cd acc = make_double2(0, 0);
+    cd acc = cmk<cd>(0, 0);
     for (int t = 0; t < r; ++t) cadd(acc, cmulc(V[k * r + t], lam[(k * r + t) * nc + col]));
     g[k + N * col] = acc;
 }
 
 // one butterfly level l: out pair p = (i,j) (rank ro) from in pairs
 // (i/2, 2j+c) (rank ri) through the ro x ri blocks blk[p][c]
+template <typename cd>
 __global__ void kx_level(const cd* blk, const cd* in, cd* out, int L, int l, int ro, int ri, int nc, int64_t N)
 {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -60,7 +78,7 @@ __global__ void kx_level(const cd* blk, const cd* in, cd* out, int L, int l, int
     int64_t nj = 1LL << (L - l);
     int64_t i = p >> (L - l), j = p & (nj - 1);
     int64_t q0 = (i >> 1) * (2 * nj) + 2 * j;
-    cd acc = make_double2(0, 0);
+    cd acc = cmk<cd>(0, 0);
     for (int c = 0; c < 2; ++c) {
         const cd* row = blk + ((p * 2 + c) * ro + t) * ri;
         const cd* v = in + (q0 + c) * ri * nc + col;
@@ -71,6 +89,7 @@ __global__ void kx_level(const cd* blk, const cd* in, cd* out, int L, int l, int
 
 // adjoint of level l: in pair q = (i', C) at level l-1 gathers from the two
 // out pairs (2i'+a, C/2) at level l with the conjugated blocks
+template <typename cd>
 __global__ void kx_level_adj(const cd* blk, const cd* out, cd* in, int L, int l, int ro, int ri, int nc,
                              int64_t N)
 {
@@ -83,7 +102,7 @@ __global__ void kx_level_adj(const cd* blk, const cd* out, cd* in, int L, int l,
     int64_t ip = q >> (L - l + 1), C = q & (nC - 1);
     int64_t j = C >> 1;
     int c = (int)(C & 1);
-    cd acc = make_double2(0, 0);
+    cd acc = cmk<cd>(0, 0);
     for (int a = 0; a < 2; ++a) {
         int64_t p = (2 * ip + a) * nj + j;
         const cd* col_blk = blk + ((p * 2 + c) * ro) * ri + s;
@@ -95,6 +114,7 @@ __global__ void kx_level_adj(const cd* blk, const cd* out, cd* in, int L, int l,
 
 // switch at level h: out_p = M~_p in_p (eq. switchlocM), M~_p of rows x cols
 // (rank after x rank before the switch), or its adjoint
+template <typename cd>
 __global__ void kx_switch(const cd* M, const cd* in, cd* out, int rows, int cols, int nc, int64_t N, int adj)
 {
     const int rout = adj ? cols : rows, rin = adj ? rows : cols;
@@ -105,7 +125,7 @@ __global__ void kx_switch(const cd* M, const cd* in, cd* out, int rows, int cols
     int64_t p = e / ((int64_t)nc * rout);
     const cd* Mp = M + p * rows * cols;
     const cd* v = in + p * rin * nc + col;
-    cd acc = make_double2(0, 0);
+    cd acc = cmk<cd>(0, 0);
     if (!adj)
         for (int s = 0; s < cols; ++s) cadd(acc, cmul(Mp[t * cols + s], v[(int64_t)s * nc]));
     else
@@ -114,6 +134,7 @@ __global__ void kx_switch(const cd* M, const cd* in, cd* out, int rows, int cols
 }
 
 // u[perm[n] + nx col] = sum_t U[n][t] Lambda^L[leaf(n)][t][col]   (eq. PIBFbf3)
+template <typename cd>
 __global__ void kx_term(const cd* U, const int32_t* leaf, const int32_t* perm, const cd* lam, cd* u, int64_t nx,
                         int r, int nc)
 {
@@ -122,12 +143,13 @@ __global__ void kx_term(const cd* U, const int32_t* leaf, const int32_t* perm, c
     int64_t n = e % nx;
     int col = (int)(e / nx);
     const cd* v = lam + (int64_t)leaf[n] * r * nc + col;
-    cd acc = make_double2(0, 0);
+    cd acc = cmk<cd>(0, 0);
     for (int t = 0; t < r; ++t) cadd(acc, cmul(U[n * r + t], v[(int64_t)t * nc]));
     u[perm[n] + nx * col] = acc;
 }
 
 // Lambda^L[i][t][col] = sum_{n in leaf i} conj(U[n][t]) y[perm[n] + nx col]
+template <typename cd>
 __global__ void kx_term_adj(const cd* U, const int32_t* off, const int32_t* perm, const cd* y, cd* lam, int64_t N,
                             int64_t nx, int r, int nc)
 {
@@ -136,7 +158,7 @@ __global__ void kx_term_adj(const cd* U, const int32_t* off, const int32_t* perm
     int col = (int)(e % nc);
     int t = (int)((e / nc) % r);
     int64_t i = e / ((int64_t)nc * r);
-    cd acc = make_double2(0, 0);
+    cd acc = cmk<cd>(0, 0);
     for (int32_t n = off[i]; n < off[i + 1]; ++n) cadd(acc, cmulc(U[(int64_t)n * r + t], y[perm[n] + nx * col]));
     lam[e] = acc;
 }
@@ -159,7 +181,8 @@ static inline int rank_in(const ibf_plan* p, int l) { return l <= p->h ? rank_h(
 
 int explicit_launches(const ibf_plan* p) { return p->L + 3; }
 
-int explicit_apply(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStream_t st)
+template <typename cd>
+static int explicit_apply_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStream_t st)
 {
     const int L = p->L, h = p->h;
     const int64_t N = p->N;
@@ -191,7 +214,8 @@ int explicit_apply(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStream_t
     return e == cudaSuccess ? IBF_OK : cuda_error(e, "explicit apply launch");
 }
 
-int explicit_adjoint(ibf_plan* p, const void* yv, void* gv, int nrhs, cudaStream_t st)
+template <typename cd>
+static int explicit_adjoint_t(ibf_plan* p, const void* yv, void* gv, int nrhs, cudaStream_t st)
 {
     const int L = p->L, h = p->h;
     const int64_t N = p->N;
@@ -221,6 +245,50 @@ int explicit_adjoint(ibf_plan* p, const void* yv, void* gv, int nrhs, cudaStream
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? IBF_OK : cuda_error(e, "explicit adjoint launch");
+}
+
+int explicit_apply(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStream_t st)
+{
+    return p->dtype == IBF_C128 ? explicit_apply_t<double2>(p, gv, uv, nrhs, st)
+                                : explicit_apply_t<float2>(p, gv, uv, nrhs, st);
+}
+
+int explicit_adjoint(ibf_plan* p, const void* yv, void* gv, int nrhs, cudaStream_t st)
+{
+    return p->dtype == IBF_C128 ? explicit_adjoint_t<double2>(p, yv, gv, nrhs, st)
+                                : explicit_adjoint_t<float2>(p, yv, gv, nrhs, st);
+}
+
+__global__ void kx_demote(const double2* a, float2* b, int64_t n)
+{
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < n) b[e] = make_float2((float)a[e].x, (float)a[e].y);
+}
+
+// FP32 plans of the explicit and optimal forms: the factors are built (and
+// compressed) in FP64, then replaced by complex64 copies.
+int explicit_demote(ibf_plan* p, void* (*alloc)(ibf_plan*, size_t), void (*release)(ibf_plan*, void*))
+{
+    const int L = p->L, h = p->h;
+    const int64_t N = p->N;
+    auto one = [&](void*& f, int64_t n) -> int {
+        void* q = alloc(p, sizeof(float2) * (size_t)n);
+        if (!q) return set_error(IBF_ERR_OOM, "FP32 factor copy");
+        kx_demote<<<nb(n), 256>>>((const double2*)f, (float2*)q, n);
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_error(e, "FP32 factor copy");
+        release(p, f);
+        f = q;
+        return IBF_OK;
+    };
+    int rc;
+    if ((rc = one(p->eV, N * rank_h(p, 0)))) return rc;
+    if ((rc = one(p->eM, N * rank_g(p, h) * rank_h(p, h)))) return rc;
+    if ((rc = one(p->eU, p->nx * rank_g(p, L)))) return rc;
+    for (int l = 1; l <= L; ++l)
+        if ((rc = one(p->eblk[l], N * 2 * rank_out(p, l) * rank_in(p, l)))) return rc;
+    p->factor_bytes = sizeof(float2) * (size_t)p->nnz;
+    return IBF_OK;
 }
 
 }  // namespace ibf

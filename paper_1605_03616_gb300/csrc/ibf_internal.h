@@ -99,6 +99,7 @@ int build_structured(ibf_plan* p);
 // alloc returns device memory owned by the plan (nullptr on failure), release
 // frees one such block
 int compress_optimal(ibf_plan* p, int r0, void* (*alloc)(ibf_plan*, size_t), void (*release)(ibf_plan*, void*));
+int explicit_demote(ibf_plan* p, void* (*alloc)(ibf_plan*, size_t), void (*release)(ibf_plan*, void*));
 int sweep_in_optimal(ibf_plan* p, const std::vector<int32_t>& off, void* (*alloc)(ibf_plan*, size_t),
                      void (*release)(ibf_plan*, void*));
 

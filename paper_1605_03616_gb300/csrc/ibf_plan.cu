@@ -495,12 +495,13 @@ extern "C" int ibf_plan_create_ex(int phase_id, int d, int64_t N, int r, int dty
         return set_error(IBF_ERR_INVALID, "unknown form");
     const bool optimal = form == IBF_FORM_OPTIMAL || form == IBF_FORM_OPTIMAL_IN;
     if (optimal) {
-        if (dtype != IBF_C128) return set_error(IBF_ERR_UNSUPPORTED, "the optimal form is FP64 (IBF_C128) only");
+        if (dtype != IBF_C128 && dtype != IBF_C64_FP32)
+            return set_error(IBF_ERR_UNSUPPORTED, "the optimal form is FP64 or FP32");
         if (r > 12) return set_error(IBF_ERR_UNSUPPORTED, "the optimal form supports r <= 12");
         if (o.rank < 1 || o.rank > r) return set_error(IBF_ERR_INVALID, "optimal form: rank must be in [1, r]");
     }
-    if (form == IBF_FORM_EXPLICIT && dtype != IBF_C128)
-        return set_error(IBF_ERR_UNSUPPORTED, "the explicit form is FP64 (IBF_C128) only");
+    if (form == IBF_FORM_EXPLICIT && dtype != IBF_C128 && dtype != IBF_C64_FP32)
+        return set_error(IBF_ERR_UNSUPPORTED, "the explicit form is FP64 or FP32");
     if (dtype == IBF_C64_BF16X3)
         return set_error(IBF_ERR_UNSUPPORTED, "split-BF16 tensor-core apply is not built yet");
     if (form == IBF_FORM_STRUCTURED && !fused_supports_r(r))
@@ -576,6 +577,8 @@ extern "C" int ibf_plan_create_ex(int phase_id, int d, int64_t N, int r, int dty
         if (!rc && form == IBF_FORM_OPTIMAL_IN) rc = sweep_in_optimal(p, off, opt_alloc, opt_release);
         if (!rc) p->factor_bytes = sizeof(double2) * (size_t)p->nnz;
     }
+    // FP32 explicit and optimal plans: built in FP64, stored and applied in FP32
+    if (!rc && form != IBF_FORM_STRUCTURED && dtype == IBF_C64_FP32) rc = explicit_demote(p, opt_alloc, opt_release);
     if (rc) {
         free_plan(p);
         return rc;

@@ -70,14 +70,14 @@ def test_optimal_matches_oracle(ibf, phase, N, r, r0, nrhs):
 
 def test_optimal_rejects_bad_options(ibf):
     for kw, code in [(dict(dtype=ibf.C128, rank=0), 1), (dict(dtype=ibf.C128, rank=10), 1),
-                     (dict(dtype=ibf.C64_FP32, rank=4), 4)]:
+                     (dict(dtype=ibf.C64_BF16X3, rank=4), 4)]:
         with pytest.raises(ibf.IBFError) as e:
             ibf.Plan(ibf.PHASE_FIO1D, 256, 9, form=ibf.FORM_OPTIMAL, **kw)
         assert e.value.code == code
     with pytest.raises(ibf.IBFError) as e:
         ibf.Plan(ibf.PHASE_FIO1D, 256, 13, ibf.C128, form=ibf.FORM_OPTIMAL, rank=6)
     assert e.value.code == 4
-    for kw, code in [(dict(dtype=ibf.C64_FP32, rank=4), 4), (dict(dtype=ibf.C128, rank=0), 1)]:
+    for kw, code in [(dict(dtype=ibf.C64_BF16X3, rank=4), 4), (dict(dtype=ibf.C128, rank=0), 1)]:
         with pytest.raises(ibf.IBFError) as e:
             ibf.Plan(ibf.PHASE_FIO1D, 256, 9, form=ibf.FORM_OPTIMAL_IN, **kw)
         assert e.value.code == code
@@ -119,3 +119,43 @@ def test_sweep_in_matches_oracle_and_keeps_the_operator(ibf, phase, N, r, r0, nr
     assert ef < tol and ea < tol
     pin.close()
     pout.close()
+
+
+@pytest.mark.parametrize("form,phase,N,r,r0,nrhs", [
+    ("optimal_in", O.PHASE_FIO1D, 1024, 9, 6, 3),
+    ("optimal_in", O.PHASE_NUFFT, 1024, 9, 5, 2),
+    ("optimal", O.PHASE_FIO1D, 2048, 12, 9, 2),
+    ("explicit", O.PHASE_FIO1D, 1024, 9, 0, 5),
+    ("explicit", O.PHASE_NUFFT, 512, 7, 0, 1),
+])
+def test_fp32_explicit_and_optimal_forms(ibf, form, phase, N, r, r0, nrhs):
+    """FP32 plans of the explicit and optimal forms: factors built (and
+    compressed) in FP64, stored and applied in FP32.  Against the oracle's
+    IBF of the same form: the FP32 bar 1e-5 (plus the compression's
+    tolerance); against the FP64 plan of the same form: 1e-5."""
+    x = W.random_sorted_x(N, W.rng(966)) if phase == O.PHASE_NUFFT else W.uniform_x(N)
+    g = W.complex_normal((N, nrhs), W.rng(967))
+    y = W.complex_normal((N, nrhs), W.rng(968))
+    fm = {"optimal_in": ibf.FORM_OPTIMAL_IN, "optimal": ibf.FORM_OPTIMAL, "explicit": ibf.FORM_EXPLICIT}[form]
+    kw = dict(x=x if phase == O.PHASE_NUFFT else None, form=fm, rank=r0)
+    p32 = ibf.Plan(phase, N, r, ibf.C64_FP32, **kw)
+    p64 = ibf.Plan(phase, N, r, ibf.C128, **kw)
+    assert p32.query(ibf.Q_FACTOR_BYTES) == 8 * p32.query(ibf.Q_NNZ) and p32.query(ibf.Q_NNZ) == p64.query(ibf.Q_NNZ)
+    d32 = lambda a: torch.from_numpy(np.ascontiguousarray(a).astype(np.complex64)).cuda()
+    u32 = p32.apply(d32(g)).cpu().numpy()
+    g32 = p32.adjoint(d32(y)).cpu().numpy()
+    u64 = p64.apply(_dev(g)).cpu().numpy()
+    g64 = p64.adjoint(_dev(y)).cpu().numpy()
+    if form == "explicit":
+        ref = O.ExplicitIBF(phase, N, r, x)
+        tol = 1e-5
+    else:
+        ref = OptimalIBF(phase, N, r, x, r0, sweep_in=form == "optimal_in")
+        tol = 1e-5 + 1e-3 * O.rel_l2(ref.apply(g), O.ExplicitIBF(phase, N, r, x).apply(g))
+    ef, ea = O.rel_l2(u32, ref.apply(g)), O.rel_l2(g32, ref.adjoint(y))
+    print("\nfp32 %s phase=%d N=%d r=%d r0=%d: vs oracle fwd %.2e adj %.2e (tol %.1e); vs fp64 plan %.2e %.2e"
+          % (form, phase, N, r, r0, ef, ea, tol, O.rel_l2(u32, u64), O.rel_l2(g32, g64)))
+    assert ef < tol and ea < tol
+    assert O.rel_l2(u32, u64) < 1e-5 and O.rel_l2(g32, g64) < 1e-5
+    p32.close()
+    p64.close()
