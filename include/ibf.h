@@ -86,7 +86,9 @@ enum ibf_dtype {
 enum ibf_form {
     IBF_FORM_AUTO = 0,       /* EXPLICIT for IBF_C128, STRUCTURED otherwise             */
     IBF_FORM_EXPLICIT = 1,   /* every r x r block of V^0, H^l, M^h, G^l, U^L stored
-                                as in Sec. 3; one kernel per level (the plain form)   */
+                                as in Sec. 3; one kernel per level (the plain form).
+                                IBF_C128, or IBF_C64_FP32: built in FP64, stored and
+                                applied in FP32 (also for the optimal forms)          */
     IBF_FORM_STRUCTURED = 2, /* each butterfly block stored as diag * T_c * diag with
                                 the two universal real Lagrange transfer matrices T_c
                                 and the diagonal phases of adjacent levels merged;
@@ -95,7 +97,8 @@ enum ibf_form {
                                 the explicit factors compressed from the middle level
                                 outward (eqs. KeqUCMRV, GC, HR) to blocks of rank
                                 ibf_options.rank by truncated SVDs, applied like the
-                                explicit form.  FP64 (IBF_C128), d = 1, r <= 12.      */
+                                explicit form.  IBF_C128 or IBF_C64_FP32 (the
+                                compression runs in FP64 either way), d = 1, r <= 12. */
     IBF_FORM_OPTIMAL_IN = 4  /* IBF_FORM_OPTIMAL followed by the sweep-in stage of
                                 Sec. 4.3 (eq. IBFin): the outer factors compressed
                                 toward the middle, each block to the number of points
