@@ -233,7 +233,7 @@ def run_nufft_latency(ibf, torch, N=1024, reps=200):
     return out
 
 
-def run_optimal(ibf, torch, N=1 << 16, nrhs=8, reps=3):
+def run_optimal(ibf, torch, N=1 << 16, nrhs=8, reps=3, variants=None):
     """Optimal IBF (sweep-out stage, Sec. 4.2, and with the sweep-in stage,
     Sec. 4.3) against the preliminary IBF, explicit factors in FP64 and in
     FP32 (built in FP64, stored and applied in FP32), 1D FIO N = 2^16,
@@ -247,12 +247,13 @@ def run_optimal(ibf, torch, N=1 << 16, nrhs=8, reps=3):
     names = {ibf.FORM_EXPLICIT: "preliminary", ibf.FORM_OPTIMAL: "optimal (sweep-out)",
              ibf.FORM_OPTIMAL_IN: "optimal (sweep-out + sweep-in)"}
     C128, C64 = ibf.C128, ibf.C64_FP32
-    for r, form, r0, dt in [(12, ibf.FORM_EXPLICIT, 0, C128), (9, ibf.FORM_EXPLICIT, 0, C128),
+    variants = variants or [(12, ibf.FORM_EXPLICIT, 0, C128), (9, ibf.FORM_EXPLICIT, 0, C128),
                             (12, ibf.FORM_OPTIMAL, 9, C128), (12, ibf.FORM_OPTIMAL_IN, 9, C128),
                             (12, ibf.FORM_OPTIMAL, 7, C128), (12, ibf.FORM_OPTIMAL_IN, 7, C128),
                             (9, ibf.FORM_OPTIMAL, 7, C128),
                             (12, ibf.FORM_EXPLICIT, 0, C64), (12, ibf.FORM_OPTIMAL_IN, 9, C64),
-                            (12, ibf.FORM_OPTIMAL_IN, 7, C64)]:
+                            (12, ibf.FORM_OPTIMAL_IN, 7, C64)]
+    for r, form, r0, dt in variants:
         gin = g if dt == C128 else g32
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -278,7 +279,8 @@ def run_optimal(ibf, torch, N=1 << 16, nrhs=8, reps=3):
                "rel_diff_vs_r12_preliminary": float(torch.linalg.vector_norm(u - ref) / torch.linalg.vector_norm(ref))}
         out.append(rec)
         p.close()
-    return {"workload": "1D FIO N=2^16, 8 columns, explicit factors (FP64, and FP32 copies)", "variants": out}
+    return {"workload": "1D FIO N=2^%d, %d columns, explicit factors (FP64, and FP32 copies)" % (int(np.log2(N)), nrhs),
+            "variants": out}
 
 
 def run_autograd(ibf, torch, N=1 << 18, nrhs=32, reps=5):
@@ -347,7 +349,8 @@ def run_amplitude(ibf, torch, N=1 << 20, nrhs=16, q=3, reps=5):
     ms_amp = timed(lambda: plan.apply_amplitude(g, al, be, work=work))
     ms_1 = timed(lambda: plan.apply(g))
     ms_q = timed(lambda: plan.apply(g3))
-    rec = {"workload": "1D FIO N=2^20 r=9, 16 columns complex64, amplitude of q=3 separated terms",
+    rec = {"workload": "1D FIO N=2^%d r=9, %d columns complex64, amplitude of q=%d separated terms"
+                       % (int(np.log2(N)), nrhs, q),
            "ms": ms_amp, "vectors_per_s": nrhs / (ms_amp / 1e3), "phase_only_ms_16_columns": ms_1,
            "phase_only_ms_48_columns": ms_q, "scaling_kernels_ms": ms_amp - ms_q}
     plan.close()
@@ -750,16 +753,28 @@ def main():
                     help="profiling aid: time only the 2D apply on the n x n grid and print its record")
     ap.add_argument("--only-batch", action="store_true",
                     help="profiling aid: time only the 256-transform batch and print its record")
+    ap.add_argument("--only-optimal", type=int, default=0, metavar="N",
+                    help="profiling aid: time only the FP32 optimal IBF with sweep-in (r = 12 -> 9) at size N")
+    ap.add_argument("--only-amplitude", type=int, default=0, metavar="N",
+                    help="profiling aid: time only the amplitude apply (q = 3, 16 columns) at size N")
     a = ap.parse_args()
     if a.warmup < 3 and a.impl == "ibf":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if a.impl == "reference":
         return run_reference(a)
-    if a.only_2d or a.only_batch:
+    if a.only_2d or a.only_batch or a.only_optimal or a.only_amplitude:
         import torch
         import paper_1605_03616_gb300 as ibf
-        rec = run_2d(ibf, torch, n=a.only_2d) if a.only_2d else run_batch(ibf, torch)
-        print(json.dumps({"profile_only": "fio2d" if a.only_2d else "batch256", **rec}), flush=True)
+        if a.only_2d:
+            name, rec = "fio2d", run_2d(ibf, torch, n=a.only_2d)
+        elif a.only_batch:
+            name, rec = "batch256", run_batch(ibf, torch)
+        elif a.only_optimal:
+            name, rec = "optimal_ibf", run_optimal(ibf, torch, N=a.only_optimal,
+                                                   variants=[(12, ibf.FORM_OPTIMAL_IN, 9, ibf.C64_FP32)])
+        else:
+            name, rec = "amplitude", run_amplitude(ibf, torch, N=a.only_amplitude)
+        print(json.dumps({"profile_only": name, **rec}), flush=True)
         return 0
     return run_gpu(a)
 
