@@ -18,7 +18,8 @@ paper); this module compiles it with gcc and wraps it with ctypes/numpy:
   decomposition with a directly summed centre (Sec. 5.2); with
   ``ibf_adjoint_2d_box`` / ``mibf_adjoint_2d``, their conjugate transposes.
 * ``optimal.OptimalIBF`` (numpy, module ``oracle.optimal``) -- the optimal
-  IBF's sweep-out compression of the explicit factors (Sec. 4.2).
+  IBF's sweep-out compression of the explicit factors (Sec. 4.2) and,
+  optionally, its sweep-in stage (Sec. 4.3).
 * ``amplitude`` (numpy, module ``oracle.amplitude``) -- a non-unit amplitude
   a(x, xi) given as a separated sum (Sec. 1, eq. FIO): the dense definition
   and the sum of diagonally scaled phase-only applies, with its adjoint.
