@@ -1,0 +1,68 @@
+"""CPU checks of bench.py's host logic: the nvidia-smi clock record that
+decides whether a timed run is kept (median SM clock, throttle reasons), the
+algorithmic flop count behind the roofline fraction, the whole-job
+throughput, and the peak denominators."""
+import os
+
+import bench
+
+
+class _Proc:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+    def kill(self):
+        pass
+
+
+def _record(lines, tmp_path):
+    c = bench.Clocks(0)
+    p = tmp_path / "clocks.csv"
+    p.write_text("\n".join(lines) + "\n")
+    c.path, c.f, c.proc = str(p), open(os.devnull, "w"), _Proc()
+    return c.stop()
+
+
+OK = "0, 2070, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active"
+CAP = "0, 1965, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active"
+HOT = "0, 1500, 2070, 1400.0, 0x0000000000000040, Not Active, Active, Not Active, Not Active"
+
+
+def test_clock_record_median_and_reasons(tmp_path):
+    r = _record([OK, OK, CAP], tmp_path)
+    assert r == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    # a thermal slowdown is reported; unparsable lines are skipped
+    r = _record([OK, HOT, "not a sample", "0, [N/A], 2070, 1.0, 0x0, a, b, c, d"], tmp_path)
+    assert r["reasons"] == ["hw_thermal_slowdown"] and r["samples"] == 2 and r["sm_mhz"] == 1785.0
+
+
+def test_clock_record_without_nvidia_smi():
+    assert bench.Clocks(0).stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_structured_flops_per_unit_and_epilogues():
+    """One butterfly unit (N = 2), one level, one column: 8 r^2 + 36 r flops
+    for the H form and 8 r^2 + 44 r for the G form (972 and 1044 at r = 9);
+    the V^0 prologue adds 6 r, the switch 8 r^2 and U^L 8 r per point and
+    column."""
+    assert bench.structured_flops(1, 9, 2, 1, None, None, False) == 972
+    assert bench.structured_flops(1, 9, 2, 1, None, None, True) == 1044
+    N, nc, r = 1 << 10, 3, 9
+    base = bench.structured_flops(4, r, N, nc, None, None, False)
+    assert base == 4 * (N // 2) * nc * 972
+    assert bench.structured_flops(4, r, N, nc, "V", None, False) - base == 6 * r * N * nc
+    assert bench.structured_flops(4, r, N, nc, None, "switch", False) - base == 8 * r * r * N * nc
+    g = bench.structured_flops(3, r, N, nc, None, None, True)
+    assert bench.structured_flops(3, r, N, nc, None, "U", True) - g == 8 * r * N * nc
+
+
+def test_throughput_and_peaks():
+    # weak scaling: every rank's vectors count, divided by the slowest rank's time
+    assert bench.job_throughput(64, 10, 2, 1000.0) == 1280.0
+    assert bench.max_over_ranks(12.5, 1) == 12.5
+    d, src = bench.peaks()
+    assert src in ("measured", "fallback")
+    assert d["hbm_gbs"] > 1000.0
