@@ -115,3 +115,26 @@ def test_sweep_in_separable_rank_one_is_exact():
     g = W.complex_normal((N, 2), W.rng(975))
     opt = OptimalIBF(O.PHASE_SEPARABLE, N, r, x, 1, sweep_in=True)
     assert O.rel_l2(opt.apply(g), O.direct_1d(O.PHASE_SEPARABLE, x, W.omega_1d(N), g)) < 1e-12
+
+
+def test_compression_ratio_matches_table3_order():
+    """At the accuracy Table 3 prints for the optimal IBF, the oracle's
+    optimal IBF (sweep-out and sweep-in, the largest compression whose error
+    against the direct sum stays within that accuracy) compresses the
+    preliminary IBF by a ratio within 2x of the printed R_comp."""
+    from conftest import read_golden
+    for N, r, eps, rcomp in read_golden("table3_rcomp_1d.txt"):
+        N, r = int(N), int(r)
+        x = W.uniform_x(N)
+        g = W.complex_normal((N, 1), W.rng(976))
+        ud = O.direct_1d(O.PHASE_FIO1D, x, W.omega_1d(N), g)
+        L = N.bit_length() - 1
+        nnz_pre = N * r + L * N * 2 * r * r + N * r * r + N * r      # V, L levels, M, U of the explicit form
+        best = None
+        for r0 in range(r, 0, -1):
+            opt = OptimalIBF(O.PHASE_FIO1D, N, r, x, r0, sweep_in=True)
+            if O.rel_l2(opt.apply(g), ud) > eps:
+                break
+            best = nnz_pre / opt.nnz()
+        assert best is not None, (N, r)
+        assert rcomp / 2 <= best <= 2 * rcomp, (N, r, best, rcomp)
