@@ -69,3 +69,22 @@ def test_argument_validation_without_gpu(lib):
     assert lib.ibf_plan_destroy(None) == 0
     v = ctypes.c_int64()
     assert lib.ibf_plan_query(None, 0, ctypes.byref(v)) == 1
+
+
+def test_form_options_validated_without_gpu(lib):
+    """Plan options of the optimal forms are checked before any CUDA call."""
+    import paper_1605_03616_gb300 as ibf
+
+    def create(form, dtype=ibf.C128, r=9, rank=4, d=1, phase=ibf.PHASE_FIO1D, N=1024):
+        o = ibf.Options()
+        o.form, o.rank = form, rank
+        out = ctypes.c_void_p()
+        return lib.ibf_plan_create_ex(phase, d, N, r, dtype, None, ctypes.byref(o), ctypes.byref(out))
+
+    assert create(5) == 1                                            # unknown form
+    for form in (ibf.FORM_OPTIMAL, ibf.FORM_OPTIMAL_IN):
+        assert create(form, rank=0) == 1                             # rank below 1
+        assert create(form, rank=10) == 1                            # rank above r
+        assert create(form, r=13, rank=6) == 4                       # r above 12
+        assert create(form, dtype=ibf.C64_BF16X3) == 4               # no split-BF16 form
+        assert create(form, d=2, phase=ibf.PHASE_FIO2D, N=64 * 64) == 4   # 1D only
