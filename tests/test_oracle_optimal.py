@@ -138,3 +138,22 @@ def test_compression_ratio_matches_table3_order():
             best = nnz_pre / opt.nnz()
         assert best is not None, (N, r)
         assert rcomp / 2 <= best <= 2 * rcomp, (N, r, best, rcomp)
+
+
+def test_nufft_sweep_in_alone_gives_table1_compression():
+    """For the nonuniform transform Table 1 prints R_comp of 1.3-1.5 at the
+    preliminary IBF's own accuracy.  Without any rank truncation (r0 = r),
+    the oracle's sweep-in alone -- splits at the point counts of random
+    leaves -- compresses by a ratio within 1.5x of the printed one and
+    leaves the result unchanged."""
+    from conftest import read_golden
+    for N, r, eps, rcomp in read_golden("table1_rcomp_1d.txt"):
+        N, r = int(N), int(r)
+        x = W.random_sorted_x(N, W.rng(977))
+        g = W.complex_normal((N, 1), W.rng(976))
+        L = N.bit_length() - 1
+        nnz_pre = N * r + L * N * 2 * r * r + N * r * r + N * r
+        opt = OptimalIBF(O.PHASE_NUFFT, N, r, x, r, sweep_in=True)
+        ratio = nnz_pre / opt.nnz()
+        assert rcomp / 1.5 <= ratio <= 1.5 * rcomp, (N, r, ratio, rcomp)
+        assert O.rel_l2(opt.apply(g), O.ExplicitIBF(O.PHASE_NUFFT, N, r, x).apply(g)) < 1e-12
