@@ -66,3 +66,28 @@ def test_throughput_and_peaks():
     d, src = bench.peaks()
     assert src in ("measured", "fallback")
     assert d["hbm_gbs"] > 1000.0
+
+
+def test_reference_arm_line(tmp_path):
+    """`bench.py --impl reference` times the oracle on the host cores and
+    prints one JSON line with the base contract's keys (small N here); a
+    rank other than 0 prints nothing and exits 0."""
+    import json
+    import subprocess
+    import sys
+    cmd = [sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+           "--warmup", "3", "--N", "4096"]
+    out = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=str(tmp_path))
+    assert out.returncode == 0, out.stderr
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    env = dict(os.environ, RANK="1")
+    out = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=str(tmp_path), env=env)
+    assert out.returncode == 0 and out.stdout.strip() == ""
