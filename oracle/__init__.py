@@ -54,38 +54,42 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def _configure(lib):
+    """Declare the argument and result types of the library's functions."""
+    P = ctypes.c_void_p
+    I64 = ctypes.c_int64
+    Ci = ctypes.c_int
+    lib.orc_phi_1d.restype = ctypes.c_double
+    lib.orc_phi_1d.argtypes = [Ci, ctypes.c_double, ctypes.c_double]
+    lib.orc_phi_2d.restype = ctypes.c_double
+    lib.orc_phi_2d.argtypes = [Ci] + [ctypes.c_double] * 4
+    lib.orc_cheb_grid.argtypes = [Ci, P]
+    lib.orc_lagrange.restype = ctypes.c_double
+    lib.orc_lagrange.argtypes = [Ci, P, Ci, ctypes.c_double]
+    lib.orc_direct_1d.argtypes = [Ci, I64, P, I64, P, P, Ci, P]
+    lib.orc_direct_2d.argtypes = [Ci, I64, P, I64, P, P, Ci, P]
+    lib.orc_ibf_apply_1d.argtypes = [Ci, I64, Ci, Ci, I64, P, P, Ci, P]
+    lib.orc_ibf_adjoint_1d.argtypes = [Ci, I64, Ci, Ci, I64, P, P, Ci, P]
+    lib.orc_ibf_build_1d.restype = P
+    lib.orc_ibf_build_1d.argtypes = [Ci, I64, Ci, Ci, I64, P]
+    lib.orc_ibf_free.argtypes = [P]
+    lib.orc_ibf_explicit_apply.argtypes = [P, P, Ci, P]
+    lib.orc_ibf_explicit_adjoint.argtypes = [P, P, Ci, P]
+    for nm in ("orc_ibf_get_V", "orc_ibf_get_U", "orc_ibf_get_M"):
+        getattr(lib, nm).argtypes = [P, P]
+    lib.orc_ibf_get_blk.argtypes = [P, Ci, P]
+    D = ctypes.c_double
+    lib.orc_ibf_apply_2d.argtypes = [Ci, I64, Ci, Ci, I64, P, D, D, P, Ci, P]
+    lib.orc_mibf_apply_2d.argtypes = [Ci, I64, Ci, Ci, I64, P, P, Ci, P]
+    lib.orc_ibf_adjoint_2d.argtypes = [Ci, I64, Ci, Ci, I64, P, D, D, P, Ci, P]
+    lib.orc_mibf_adjoint_2d.argtypes = [Ci, I64, Ci, Ci, I64, P, P, Ci, P]
+    return lib
+
+
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
-        P = ctypes.c_void_p
-        I64 = ctypes.c_int64
-        Ci = ctypes.c_int
-        lib.orc_phi_1d.restype = ctypes.c_double
-        lib.orc_phi_1d.argtypes = [Ci, ctypes.c_double, ctypes.c_double]
-        lib.orc_phi_2d.restype = ctypes.c_double
-        lib.orc_phi_2d.argtypes = [Ci] + [ctypes.c_double] * 4
-        lib.orc_cheb_grid.argtypes = [Ci, P]
-        lib.orc_lagrange.restype = ctypes.c_double
-        lib.orc_lagrange.argtypes = [Ci, P, Ci, ctypes.c_double]
-        lib.orc_direct_1d.argtypes = [Ci, I64, P, I64, P, P, Ci, P]
-        lib.orc_direct_2d.argtypes = [Ci, I64, P, I64, P, P, Ci, P]
-        lib.orc_ibf_apply_1d.argtypes = [Ci, I64, Ci, Ci, I64, P, P, Ci, P]
-        lib.orc_ibf_adjoint_1d.argtypes = [Ci, I64, Ci, Ci, I64, P, P, Ci, P]
-        lib.orc_ibf_build_1d.restype = P
-        lib.orc_ibf_build_1d.argtypes = [Ci, I64, Ci, Ci, I64, P]
-        lib.orc_ibf_free.argtypes = [P]
-        lib.orc_ibf_explicit_apply.argtypes = [P, P, Ci, P]
-        lib.orc_ibf_explicit_adjoint.argtypes = [P, P, Ci, P]
-        for nm in ("orc_ibf_get_V", "orc_ibf_get_U", "orc_ibf_get_M"):
-            getattr(lib, nm).argtypes = [P, P]
-        lib.orc_ibf_get_blk.argtypes = [P, Ci, P]
-        D = ctypes.c_double
-        lib.orc_ibf_apply_2d.argtypes = [Ci, I64, Ci, Ci, I64, P, D, D, P, Ci, P]
-        lib.orc_mibf_apply_2d.argtypes = [Ci, I64, Ci, Ci, I64, P, P, Ci, P]
-        lib.orc_ibf_adjoint_2d.argtypes = [Ci, I64, Ci, Ci, I64, P, D, D, P, Ci, P]
-        lib.orc_mibf_adjoint_2d.argtypes = [Ci, I64, Ci, Ci, I64, P, P, Ci, P]
-        _lib = lib
+        _lib = _configure(ctypes.CDLL(build()))
     return _lib
 
 
