@@ -3,8 +3,9 @@ mistake in a copy of the oracle -- the C source recompiled with gcc, or a
 Python module re-executed from its edited source -- runs one of the real pin
 tests against the copy, and requires that pin to fail.  Mistakes: a sign of
 the phase factor, the Chebyshev grid, a dropped Lagrange factor, the child
-centre or a phase sign of a butterfly level, a dropped conjugate in an
-adjoint level, swapped amplitude factors, a missing conjugate in the amplitude
+centre or a phase sign of a butterfly level, a transposed switch block, a
+wrong box width in U^L, a dropped phase factor in V^0, a skipped corona box
+in 2D, a dropped conjugate in an adjoint level, swapped amplitude factors, a missing conjugate in the amplitude
 adjoint, a swapped pencil in the sweep-in, a rank one short, and a truncated
 SVD split without the square roots."""
 import ctypes
@@ -18,6 +19,7 @@ import oracle as O
 import oracle.amplitude as OA
 import oracle.optimal as OO
 import test_oracle as T
+import test_oracle_2d as T2
 import test_oracle_amplitude as TA
 import test_oracle_optimal as TO
 
@@ -42,6 +44,22 @@ C_MUTATIONS = [
     ("H-level phase sign", "next[(i * nj + j) * r + t] = e2pi(-orc_phi_1d(ph, cA, gBt)) * acc;",
      "next[(i * nj + j) * r + t] = e2pi(orc_phi_1d(ph, cA, gBt)) * acc;",
      lambda: T.test_separable_phase_is_exact(64, 5, 3)),
+    ("switch block transposed",
+     "acc += e2pi(orc_phi_1d(ph, gridpt(cA, wA, z, t), gridpt(cB, wB, z, s))) * old[s];",
+     "acc += e2pi(orc_phi_1d(ph, gridpt(cA, wA, z, s), gridpt(cB, wB, z, t))) * old[s];",
+     lambda: T.test_separable_phase_is_exact(64, 5, 3)),
+    ("U^L box width", "acc += orc_lagrange(r, z, t, (x[n] - cA) / wA) * e2pi(-orc_phi_1d(ph, gridpt(cA, wA, z, t), cB)) *",
+     "acc += orc_lagrange(r, z, t, (x[n] - cA) / (2 * wA)) * e2pi(-orc_phi_1d(ph, gridpt(cA, wA, z, t), cB)) *",
+     # partition of unity hides an x-interpolation point from the separable
+     # phase; the explicit factors (separate code) expose it
+     lambda: T.test_dense_factor_product_matches_apply(16, 5, O.PHASE_FIO1D)),
+    ("V^0 phase factor dropped",
+     "orc_lagrange(r, z, t, (xi - cB) / wB) * e2pi(orc_phi_1d(ph, cA, xi)) * g[k];",
+     "orc_lagrange(r, z, t, (xi - cB) / wB) * g[k];",
+     lambda: T.test_separable_phase_is_exact(64, 5, 3)),
+    ("2D corona ring box skipped", "if (b1 >= 1 && b1 <= 2 && b2 >= 1 && b2 <= 2) continue;   /* inner",
+     "if (b1 >= 1 && b1 <= 2 && b2 >= 1 && b2 <= 3) continue;   /* inner",
+     lambda: T2.test_separable_2d_box_and_mibf_exact(32, 7)),
     ("adjoint conjugate dropped", "                                 e2pi(-orc_phi_1d(ph, gPs, cC));\n"
      "                        acc += conj(w) * ln[t];",
      "                                 e2pi(-orc_phi_1d(ph, gPs, cC));\n                        acc += w * ln[t];",
