@@ -47,6 +47,22 @@ def test_direct_2d_equals_dft_closed_form():
     assert O.rel_l2(u, ref) < 1e-13
 
 
+# ------------------------------------------------------------- phase shapes
+def test_phase_values_match_hand_computed():
+    """The phases of Sec. 6 at points where they are exact rationals
+    (tests/golden/phase_values.txt, each value worked out by hand): c(x) of
+    the 1D FIO and c1, c2 of the 2D FIO at quarter and twelfth points, where
+    sin and cos take the values 0, +-1/2, +-1.  A phase-shifted coefficient
+    (cos for sin) or c1 and c2 exchanged moves several rows by >= 1."""
+    kinds = {0: O.PHASE_NUFFT, 1: O.PHASE_FIO1D, 2: O.PHASE_FIO2D, 3: O.PHASE_FIO2D_32}
+    rows = read_golden("phase_values.txt")
+    assert len(rows) >= 20
+    for kind, x1, x2, k1, k2, want in rows:
+        ph = kinds[int(kind)]
+        got = O.phi_1d(ph, x1, k1) if int(kind) <= 1 else O.phi_2d(ph, x1, x2, k1, k2)
+        assert abs(got - want) <= 1e-12 * max(1.0, abs(want)), (kind, x1, x2, k1, k2, got, want)
+
+
 # ------------------------------------------------------- grids and Lagrange
 @pytest.mark.parametrize("r", [3, 5, 7, 9, 12])
 def test_chebyshev_grid_matches_numpy(r):

@@ -2,7 +2,8 @@
 mistake in a copy of the oracle -- the C source recompiled with gcc, or a
 Python module re-executed from its edited source -- runs one of the real pin
 tests against the copy, and requires that pin to fail.  Mistakes: a sign of
-the phase factor, the Chebyshev grid, a dropped Lagrange factor, the child
+the phase factor, a phase-shifted 1D FIO coefficient, the 2D FIO coefficients
+exchanged, the Chebyshev grid, a dropped Lagrange factor, the child
 centre or a phase sign of a butterfly level, a transposed switch block, a
 wrong box width in U^L, a dropped phase factor in V^0, a skipped corona box
 in 2D, a dropped conjugate in an adjoint level, swapped amplitude factors, a missing conjugate in the amplitude
@@ -60,6 +61,15 @@ C_MUTATIONS = [
     ("2D corona ring box skipped", "if (b1 >= 1 && b1 <= 2 && b2 >= 1 && b2 <= 2) continue;   /* inner",
      "if (b1 >= 1 && b1 <= 2 && b2 >= 1 && b2 <= 3) continue;   /* inner",
      lambda: T2.test_separable_2d_box_and_mibf_exact(32, 7)),
+    ("1D FIO coefficient phase-shifted (cos for sin)",
+     "double c = (2.0 + sin(2.0 * M_PI * x)) / 8.0;", "double c = (2.0 + cos(2.0 * M_PI * x)) / 8.0;",
+     T.test_phase_values_match_hand_computed),
+    ("2D FIO coefficients c1 and c2 exchanged",
+     "double c1 = (2.0 + sin(2.0 * M_PI * x1) * sin(2.0 * M_PI * x2)) / den;\n"
+     "        double c2 = (2.0 + cos(2.0 * M_PI * x1) * cos(2.0 * M_PI * x2)) / den;",
+     "double c2 = (2.0 + sin(2.0 * M_PI * x1) * sin(2.0 * M_PI * x2)) / den;\n"
+     "        double c1 = (2.0 + cos(2.0 * M_PI * x1) * cos(2.0 * M_PI * x2)) / den;",
+     T.test_phase_values_match_hand_computed),
     ("adjoint conjugate dropped", "                                 e2pi(-orc_phi_1d(ph, gPs, cC));\n"
      "                        acc += conj(w) * ln[t];",
      "                                 e2pi(-orc_phi_1d(ph, gPs, cC));\n                        acc += w * ln[t];",
