@@ -40,7 +40,7 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per launch of the fused kernels, from one
 # single-pass ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of
 # this benchmark at N = 2^20, r = 9, nrhs = 64, 4 levels per launch, tile 32
-# (profiles/k_fused_f32_fio1d_n2e20_nrhs64.md).  Keyed by the launch's level
+# (the ncu DRAM capture of the fused kernels).  Keyed by the launch's level
 # range; valid only while the kernel sources hash to KERNEL_SRC_SHA.
 KERNEL_SRC_SHA = "fecf3fff897107d4"
 TRAFFIC_N20_R9_NRHS64_K4 = {

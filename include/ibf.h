@@ -249,21 +249,26 @@ int ibf_apply_amplitude(ibf_plan* plan, const void* alpha, const void* beta, int
  * the structured-form apply.
  *
  * It allocates nothing.  Its two Lambda buffers live in one file-scope
- * device array of 256 MiB (two halves of 128 MiB) that every GPU loading the
- * library holds until the process exits; the plan's own workspace is not
- * used, so a plan created with max_nrhs = 1 still applies many columns per
- * launch here.  The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Every call shares the array and it keeps
- * the last call's contents; no part of it needs to start at zero because each
- * launch writes every element the next launch reads.  Calls that overlap on
- * the GPU (other streams, or other threads) race on the array: order them.
- *   plan : a structured-form plan (IBF_FORM_STRUCTURED); otherwise
- *          IBF_ERR_UNSUPPORTED.
+ * device array of 256 MiB (two halves of 128 MiB); the plan's own workspace
+ * is not used, so a plan created with max_nrhs = 1 still applies many
+ * columns per launch here.  Creating a 1D structured plan sets this entry
+ * point up on the plan's device: it looks up the array's device address
+ * (cudaGetSymbolAddress, which makes that device commit the 256 MiB, held
+ * until the process exits) and copies the transfer weights for the plan's r
+ * and precision.  A call on a device where no 1D structured plan of that r
+ * and precision was created does this set-up itself, with synchronous CUDA
+ * calls: make such a call before any stream capture.  The set-up is guarded
+ * by a lock.  Every call shares the array and it keeps the last call's
+ * contents; no part of it needs to start at zero because each launch writes
+ * every element the next launch reads.  Calls that overlap on the GPU (other
+ * streams, or other threads) race on the array: order them.
+ *   plan : a 1D structured-form plan (IBF_FORM_STRUCTURED, d = 1); a 2D plan
+ *          or another form returns IBF_ERR_UNSUPPORTED before any CUDA call.
  *   g, u, nrhs, stream : as ibf_apply.
  * Size limit: N * r * (element size) must not exceed 128 MiB (one Lambda
  * column per half), else IBF_ERR_INVALID with a message naming the limit;
- * e.g. complex64 with r = 9 allows N <= 2^20, complex128 N <= 2^19.
+ * e.g. complex64 with r = 9 allows N <= 2^20, complex128 N <= 2^19.  The
+ * columns are processed in chunks of as many as one half holds.
  */
 int ibf_apply_static_scratch(const ibf_plan* plan, const void* g, void* u, int nrhs, ibf_stream_t stream);
 
@@ -357,6 +362,24 @@ enum ibf_query {
                                   form, r otherwise                               */
 };
 int ibf_plan_query(const ibf_plan* plan, int what, int64_t* value);
+
+/*
+ * ibf_plan_status -- the plan's sticky status, read and cleared.  Apply calls
+ * are asynchronous, and a persistent batch reports an expired device-side
+ * wait only through ibf_batch_status; the plan keeps the first such failure
+ * so that a caller holding only the plan sees it.  Recorded: any error of an
+ * apply call on this plan (ibf_apply, ibf_apply_adjoint, ibf_apply_host,
+ * ibf_apply_amplitude, ibf_apply_static_scratch) returned after its
+ * arguments were accepted (CUDA launch or copy failures), and
+ * IBF_ERR_TIMEOUT when ibf_batch_status finds an expired wait in a batch
+ * holding the plan.  Argument errors are returned by the call itself and are
+ * not recorded.  Returns that status (IBF_OK if none) and resets it to
+ * IBF_OK; IBF_ERR_INVALID for a NULL plan.  No CUDA call, no
+ * synchronization.  This replaces the survey's device-side per-plan status:
+ * the only device-side waits are those of the persistent batch, whose status
+ * word belongs to the batch.
+ */
+int ibf_plan_status(ibf_plan* plan);
 
 /*
  * Per-launch timing for measurement tools.  ibf_plan_profile_begin(plan, cap)

@@ -43,7 +43,8 @@ EXPORTS = ("ibf_plan_create", "ibf_plan_create_ex", "ibf_apply", "ibf_apply_adjo
            "ibf_plan_query", "ibf_get_last_error", "ibf_plan_profile_begin", "ibf_plan_profile_end",
            "ibf_apply_static_scratch", "ibf_batch_create", "ibf_batch_apply", "ibf_batch_query",
            "ibf_batch_destroy", "ibf_plan_autotune", "ibf_batch_apply_persistent", "ibf_batch_status",
-           "ibf_batch_set_wait_limit", "ibf_batch_test_withhold", "ibf_apply_host", "ibf_apply_amplitude")
+           "ibf_batch_set_wait_limit", "ibf_batch_test_withhold", "ibf_apply_host", "ibf_apply_amplitude",
+           "ibf_plan_status")
 
 BQ_LAUNCHES, BQ_WORKSPACE_BYTES, BQ_COUNT, BQ_PERSIST_ITEMS = range(4)
 
@@ -100,6 +101,7 @@ def load_library(path: str | None = None):
     L.ibf_plan_profile_begin.argtypes = [P, I]
     L.ibf_apply_amplitude.argtypes = [P, P, P, I, P, P, I, I, P, I64, P]
     L.ibf_plan_profile_end.argtypes = [P, P, P, I, ctypes.POINTER(I)]
+    L.ibf_plan_status.argtypes = [P]
     for nm in EXPORTS:
         getattr(L, nm).restype = I
     if path is None:
@@ -164,6 +166,10 @@ class Plan:
         v = ctypes.c_int64()
         _check(self._lib.ibf_plan_query(self._p, what, ctypes.byref(v)))
         return v.value
+
+    def status(self) -> int:
+        """The plan's sticky status, read and cleared (ibf_plan_status)."""
+        return self._lib.ibf_plan_status(self._p)
 
     @property
     def L(self) -> int:

@@ -154,6 +154,7 @@ extern "C" int ibf_apply_amplitude(ibf_plan* p, const void* alpha, const void* b
         overlaps(work, wb, beta, fb))
         return set_error(IBF_ERR_INVALID, "work overlaps another argument");
     cudaStream_t st = (cudaStream_t)stream;
-    if (p->dtype == IBF_C128) return amplitude_t<double>(p, alpha, beta, q, in, out, nrhs, adjoint, work, m, st);
-    return amplitude_t<float>(p, alpha, beta, q, in, out, nrhs, adjoint, work, m, st);
+    if (p->dtype == IBF_C128)
+        return plan_note(p, amplitude_t<double>(p, alpha, beta, q, in, out, nrhs, adjoint, work, m, st));
+    return plan_note(p, amplitude_t<float>(p, alpha, beta, q, in, out, nrhs, adjoint, work, m, st));
 }

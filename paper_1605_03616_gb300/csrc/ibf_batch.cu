@@ -547,7 +547,10 @@ extern "C" int ibf_batch_status(const ibf_batch* b)
     int st = 0;
     cudaError_t e = cudaMemcpy(&st, b->p_status, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_error(e, "batch status");
-    if (st) return set_error(IBF_ERR_TIMEOUT, "persistent batch: a dependency wait expired");
+    if (st) {
+        for (ibf_plan* p : b->plans) plan_note(p, IBF_ERR_TIMEOUT);
+        return set_error(IBF_ERR_TIMEOUT, "persistent batch: a dependency wait expired");
+    }
     return IBF_OK;
 }
 

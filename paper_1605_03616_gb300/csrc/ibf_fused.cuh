@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "ibf_internal.h"
@@ -732,8 +733,10 @@ template <typename Real, int RP>
 static int fused_upload_consts_t(const ibf_plan* p)
 {
     static bool done[64] = {false};
+    static std::mutex mu;   // plans may be created from several host threads
     int dev = 0;
     cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
     if (dev >= 0 && dev < 64 && done[dev]) return IBF_OK;
     FusedConsts<Real, RP> h;
     memset(&h, 0, sizeof(h));

@@ -33,6 +33,10 @@ struct ibf_plan {
     // every level has rank ra (or r)
     std::vector<int> rk_h, rk_g;
     bool user_kfuse = false, user_rtile = false;
+    // sticky status (ibf_plan_status): the first error of an apply on this
+    // plan after its arguments were accepted, or IBF_ERR_TIMEOUT from a
+    // persistent batch holding the plan; read and cleared by ibf_plan_status
+    mutable int sticky = 0;
 
     // Chebyshev grid on [-1/2,1/2] and the two child-to-parent Lagrange
     // transfer matrices T_c[t][s] = M_t((2c-1)/4 + z_s/2)   (Sec. 2.1)
@@ -113,5 +117,16 @@ int fused_apply(ibf_plan* p, const void* g, void* u, int nrhs, bool adjoint, cud
 int fused_launches(const ibf_plan* p);
 bool fused_supports_r(int r);
 void fused_choose_shape(ibf_plan* p);
+
+// record a failure of an apply on p in its sticky status; returns rc
+inline int plan_note(const ibf_plan* p, int rc)
+{
+    if (rc != IBF_OK && p && p->sticky == IBF_OK) p->sticky = rc;
+    return rc;
+}
+
+// static-scratch apply (ibf_static.cu): per-device set-up of its array and
+// weights for a new 1D structured plan (see ibf_apply_static_scratch)
+int static_scratch_prepare(const ibf_plan* p);
 
 }  // namespace ibf

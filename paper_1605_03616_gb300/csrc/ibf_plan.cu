@@ -592,7 +592,13 @@ extern "C" int ibf_plan_create_ex(int phase_id, int d, int64_t N, int r, int dty
             return rc;
         }
     p->ws_bytes = 2 * wsb;
-    if (form == IBF_FORM_STRUCTURED) fused_choose_shape(p);
+    if (form == IBF_FORM_STRUCTURED) {
+        fused_choose_shape(p);
+        // commit the static-scratch array on this device now, while the
+        // caller may still allocate; a failure here is reported again by
+        // ibf_apply_static_scratch, the only user of the array
+        if (static_scratch_prepare(p) != IBF_OK) cudaGetLastError();
+    }
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         free_plan(p);
@@ -628,18 +634,27 @@ extern "C" int ibf_apply(ibf_plan* p, const void* g, void* u, int nrhs, ibf_stre
 {
     int rc = check_apply(p, g, u, nrhs);
     if (rc) return rc;
-    if (p->d == 2) return apply_2d(p, g, u, nrhs, (cudaStream_t)stream);
-    if (p->form != IBF_FORM_STRUCTURED) return explicit_apply(p, g, u, nrhs, (cudaStream_t)stream);
-    return fused_apply(p, g, u, nrhs, false, (cudaStream_t)stream);
+    if (p->d == 2) return plan_note(p, apply_2d(p, g, u, nrhs, (cudaStream_t)stream));
+    if (p->form != IBF_FORM_STRUCTURED) return plan_note(p, explicit_apply(p, g, u, nrhs, (cudaStream_t)stream));
+    return plan_note(p, fused_apply(p, g, u, nrhs, false, (cudaStream_t)stream));
 }
 
 extern "C" int ibf_apply_adjoint(ibf_plan* p, const void* y, void* g, int nrhs, ibf_stream_t stream)
 {
     int rc = check_apply(p, y, g, nrhs);
     if (rc) return rc;
-    if (p->d == 2) return apply_2d_adjoint(p, y, g, nrhs, (cudaStream_t)stream);
-    if (p->form != IBF_FORM_STRUCTURED) return explicit_adjoint(p, y, g, nrhs, (cudaStream_t)stream);
-    return fused_apply(p, y, g, nrhs, true, (cudaStream_t)stream);
+    if (p->d == 2) return plan_note(p, apply_2d_adjoint(p, y, g, nrhs, (cudaStream_t)stream));
+    if (p->form != IBF_FORM_STRUCTURED) return plan_note(p, explicit_adjoint(p, y, g, nrhs, (cudaStream_t)stream));
+    return plan_note(p, fused_apply(p, y, g, nrhs, true, (cudaStream_t)stream));
+}
+
+extern "C" int ibf_plan_status(ibf_plan* p)
+{
+    if (!p) return set_error(IBF_ERR_INVALID, "plan is NULL");
+    const int st = p->sticky;
+    p->sticky = IBF_OK;
+    if (st != IBF_OK) return set_error(st, "sticky status of the plan: an earlier apply failed or its batch timed out");
+    return IBF_OK;
 }
 
 // Host-buffer apply: chunks of `hst_chunk` columns go through two device
@@ -679,7 +694,7 @@ extern "C" int ibf_apply_host(ibf_plan* p, const void* hin, void* hout, int nrhs
     const size_t esz = p->dtype == IBF_C128 ? 16 : 8;
     if (((uintptr_t)hin % esz) || ((uintptr_t)hout % esz)) return set_error(IBF_ERR_INVALID, "misaligned vector pointer");
     int rc = host_setup(p);
-    if (rc) return rc;
+    if (rc) return plan_note(p, rc);
     cudaStream_t st = (cudaStream_t)stream;
     const size_t col = esz * (size_t)p->N;
     const int ch = p->hst_chunk;
@@ -697,7 +712,7 @@ extern "C" int ibf_apply_host(ibf_plan* p, const void* hin, void* hout, int nrhs
         if (j >= 2) cudaStreamWaitEvent(p->hst_in, app[s], 0);
         if ((e = cudaMemcpyAsync(slot_in[s], (const char*)hin + col * c0, col * nc, cudaMemcpyHostToDevice,
                                  p->hst_in)) != cudaSuccess)
-            return cuda_error(e, "host apply: copy in");
+            return plan_note(p, cuda_error(e, "host apply: copy in"));
         cudaEventRecord(h2d[s], p->hst_in);
         cudaStreamWaitEvent(st, h2d[s], 0);
         if (j >= 2) cudaStreamWaitEvent(st, d2h[s], 0);
@@ -708,14 +723,14 @@ extern "C" int ibf_apply_host(ibf_plan* p, const void* hin, void* hout, int nrhs
         cudaStreamWaitEvent(p->hst_out, app[s], 0);
         if ((e = cudaMemcpyAsync((char*)hout + col * c0, slot_out[s], col * nc, cudaMemcpyDeviceToHost,
                                  p->hst_out)) != cudaSuccess)
-            return cuda_error(e, "host apply: copy out");
+            return plan_note(p, cuda_error(e, "host apply: copy out"));
         cudaEventRecord(d2h[s], p->hst_out);
     }
     // `stream` completes only after every copy-out
     cudaStreamWaitEvent(st, d2h[0], 0);
     if (nch > 1) cudaStreamWaitEvent(st, d2h[1], 0);
     e = cudaGetLastError();
-    return e == cudaSuccess ? IBF_OK : cuda_error(e, "host apply");
+    return e == cudaSuccess ? IBF_OK : plan_note(p, cuda_error(e, "host apply"));
 }
 
 extern "C" int ibf_plan_profile_begin(ibf_plan* p, int cap)

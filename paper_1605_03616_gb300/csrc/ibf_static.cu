@@ -9,11 +9,14 @@
 // right-hand sides per launch through this entry point, which allocates
 // nothing: its two Lambda buffers live in the static array below.
 //
-// The array is a file-scope __device__ variable: every GPU that loads this
-// library holds its kStaticScratchBytes until the process exits.  Host code
-// must not pass the symbol itself to a kernel (on the host it names a
-// stand-in, not device memory); the device address is looked up once per
-// device with cudaGetSymbolAddress and cached.
+// The array is a file-scope __device__ variable of this translation unit's
+// module.  The module is loaded on a device (and the array committed there)
+// when its address is first looked up; creating a 1D structured plan does
+// that on the plan's device (static_scratch_prepare), so the memory is taken
+// while the caller may still allocate, and stays taken until the process
+// exits.  Host code must not pass the symbol itself to a kernel (on the host
+// it names a stand-in, not device memory); the device address comes from
+// cudaGetSymbolAddress, once per device, and is cached.
 #include <mutex>
 
 #include "ibf_fused.cuh"
@@ -29,9 +32,25 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 static std::mutex g_static_mu;
 static void* g_static_addr[64] = {nullptr};
 
-// Device address of g_static_scratch on the current device (set-up on the
-// first call per device).
-static int static_scratch_address(void** out)
+// This file's copy of the transfer weights for the plan's (precision, r).
+static int static_upload_consts(const ibf_plan* p)
+{
+    const bool f64 = p->dtype == IBF_C128;
+    switch (p->r) {
+    case 5: return f64 ? fused_upload_consts_t<double, 5>(p) : fused_upload_consts_t<float, 5>(p);
+    case 7: return f64 ? fused_upload_consts_t<double, 7>(p) : fused_upload_consts_t<float, 7>(p);
+    case 9: return f64 ? fused_upload_consts_t<double, 9>(p) : fused_upload_consts_t<float, 9>(p);
+    case 11: return f64 ? fused_upload_consts_t<double, 11>(p) : fused_upload_consts_t<float, 11>(p);
+    default: return set_error(IBF_ERR_UNSUPPORTED, "structured form: unsupported r");
+    }
+}
+
+// Set-up for the current device, under g_static_mu: the device address of
+// g_static_scratch (the lookup loads this module and commits the array on
+// the device) and the weights for the plan's (precision, r).  Only the
+// first call per device and per (precision, r) makes CUDA calls that are not
+// allowed during stream capture (module load, a synchronous symbol copy).
+static int static_prepare_current(const ibf_plan* p, void** out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -44,9 +63,14 @@ static int static_scratch_address(void** out)
         if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(static scratch)");
         g_static_addr[dev] = ptr;
     }
-    *out = g_static_addr[dev];
+    const int rc = static_upload_consts(p);
+    if (rc) return rc;
+    if (out) *out = g_static_addr[dev];
     return IBF_OK;
 }
+
+// Called when a 1D structured plan is created, on its device.
+int static_scratch_prepare(const ibf_plan* p) { return static_prepare_current(p, nullptr); }
 
 // The fused forward schedule of fused_run with caller-chosen Lambda buffers.
 template <typename Real, int RP>
@@ -56,8 +80,6 @@ static int static_run(const ibf_plan* p, const void* vin, void* vout, int nrhs, 
     typedef typename CT<Real>::T cx;
     FusedParams<Real, RP> P;
     memset(&P, 0, sizeof(P));
-    int urc = fused_upload_consts_t<Real, RP>(p);   // first call on a device only
-    if (urc) return urc;
     P.d.Vs = p->sV;
     P.d.Us = p->sU;
     P.d.Ms = p->sM;
@@ -121,8 +143,10 @@ extern "C" int ibf_apply_static_scratch(const ibf_plan* p, const void* g, void* 
     if (!p) return set_error(IBF_ERR_INVALID, "plan is NULL");
     if (!g || !u) return set_error(IBF_ERR_INVALID, "NULL vector pointer");
     if (nrhs < 1) return set_error(IBF_ERR_INVALID, "nrhs must be >= 1");
+    if (p->d != 1) return set_error(IBF_ERR_UNSUPPORTED, "static-scratch apply needs a 1D plan");
     if (p->form != IBF_FORM_STRUCTURED)
         return set_error(IBF_ERR_UNSUPPORTED, "static-scratch apply needs a structured-form plan");
+    if (!fused_supports_r(p->r)) return set_error(IBF_ERR_UNSUPPORTED, "structured form: unsupported r");
     const size_t esz = p->dtype == IBF_C128 ? sizeof(double2) : sizeof(float2);
     if (((uintptr_t)g % esz) || ((uintptr_t)u % esz)) return set_error(IBF_ERR_INVALID, "misaligned vector pointer");
     const size_t bytes = esz * (size_t)p->N * nrhs;
@@ -135,11 +159,12 @@ extern "C" int ibf_apply_static_scratch(const ibf_plan* p, const void* g, void* 
                                               " bytes exceeds the static scratch limit of " +
                                               std::to_string(kStaticHalf) + " bytes per Lambda buffer");
     void* base = nullptr;
-    int rc = static_scratch_address(&base);
-    if (rc) return rc;
+    int rc = static_prepare_current(p, &base);
+    if (rc) return plan_note(p, rc);
     const int max_cols = (int)std::min<size_t>(kStaticHalf / col_bytes, 1 << 20);
     void* b0 = base;
     void* b1 = (char*)base + kStaticHalf;
-    if (p->dtype == IBF_C128) return static_dispatch<double>(p, g, u, nrhs, (cudaStream_t)stream, b0, b1, max_cols);
-    return static_dispatch<float>(p, g, u, nrhs, (cudaStream_t)stream, b0, b1, max_cols);
+    if (p->dtype == IBF_C128)
+        return plan_note(p, static_dispatch<double>(p, g, u, nrhs, (cudaStream_t)stream, b0, b1, max_cols));
+    return plan_note(p, static_dispatch<float>(p, g, u, nrhs, (cudaStream_t)stream, b0, b1, max_cols));
 }

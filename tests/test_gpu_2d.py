@@ -32,7 +32,8 @@ def _run(ibf, phase, n, r, dtype, g):
 
 @pytest.mark.parametrize("phase,n,r,nrhs", [(O.PHASE_SEPARABLE, 32, 5, 2), (O.PHASE_FIO2D, 32, 7, 3),
                                             (O.PHASE_FIO2D, 64, 5, 1), (O.PHASE_NUFFT, 64, 7, 2),
-                                            (O.PHASE_FIO2D, 64, 9, 2), (O.PHASE_FIO2D, 64, 7, 37)])
+                                            (O.PHASE_FIO2D, 64, 9, 2), (O.PHASE_FIO2D, 64, 7, 37),
+                                            (O.PHASE_FIO2D, 128, 7, 1)])   # rings of side-32 boxes: odd depth
 def test_2d_matches_oracle_mibf(ibf, phase, n, r, nrhs):
     x = W.grid_x_2d(n)
     g = W.complex_normal((n * n, nrhs), W.rng(601))
@@ -41,7 +42,7 @@ def test_2d_matches_oracle_mibf(ibf, phase, n, r, nrhs):
     u32 = _run(ibf, phase, n, r, ibf.C64_FP32, g)
     e64, e32 = O.rel_l2(u64, ref), O.rel_l2(u32, ref)
     print("\nparity 2d phase=%d n=%d r=%d nrhs=%d fp64 %.3e fp32 %.3e" % (phase, n, r, nrhs, e64, e32))
-    assert e64 < 1e-11
+    assert e64 < 1e-12
     assert e32 < 1e-5
     if phase == O.PHASE_SEPARABLE:
         ud = O.direct_2d(phase, x, W.omega_2d(n), g)
@@ -107,5 +108,5 @@ def test_2d_adjoint_matches_oracle(ibf, phase, n, r, nrhs, max_nrhs):
         plan.close()
     e64, e32 = O.rel_l2(out[ibf.C128], ref), O.rel_l2(out[ibf.C64_FP32], ref)
     print("\nadjoint 2d phase=%d n=%d r=%d nrhs=%d fp64 %.3e fp32 %.3e" % (phase, n, r, nrhs, e64, e32))
-    assert e64 < 1e-11
+    assert e64 < 1e-12
     assert e32 < 1e-5

@@ -118,6 +118,29 @@ def test_persistent_single_launch_matches(ibf):
         assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_persistent_single_launch_matches_oracle(ibf, adjoint):
+    """The one-launch batch against the oracle's preliminary IBF (Algorithm
+    2.1 / Sec. 3) and its adjoint, on plans that reach 4-level work items
+    (N = 2^16: chunks of 4 levels on both sides of the switch), odd depth
+    (N = 2^11) and a small plan (N = 2^8)."""
+    Ns, nrhs = [1 << 16, 1 << 11, 1 << 8], [2, 5, 3]
+    rng = W.rng(720 + adjoint)
+    plans = [ibf.Plan(ibf.PHASE_FIO1D, N, 9, ibf.C64_FP32, max_nrhs=k) for N, k in zip(Ns, nrhs)]
+    ins = [torch.from_numpy(W.complex_normal((k, N), rng, dtype=np.complex64)).cuda() for N, k in zip(Ns, nrhs)]
+    outs = [torch.full_like(t, float("nan")) for t in ins]
+    batch = ibf.Batch(plans, ins, outs, adjoint=adjoint)
+    batch.apply_persistent()
+    torch.cuda.synchronize()
+    assert batch.status() == 0
+    fn = O.ibf_adjoint_1d if adjoint else O.ibf_apply_1d
+    for N, g, u in zip(Ns, ins, outs):
+        ref = fn(O.PHASE_FIO1D, N, 9, W.uniform_x(N), g.cpu().numpy().T.astype(np.complex128))
+        e = O.rel_l2(u.cpu().numpy().T, ref)
+        print("\npersistent %s N=%d: %.3e vs oracle" % ("adjoint" if adjoint else "forward", N, e))
+        assert e < 1e-5, N
+
+
 def test_persistent_wait_expires_without_hanging(ibf):
     """A dependency that is never satisfied (test hook) makes the bounded waits
     run out: the kernel returns, the batch reports IBF_ERR_TIMEOUT, and the
@@ -132,6 +155,9 @@ def test_persistent_wait_expires_without_hanging(ibf):
     batch.apply_persistent()
     assert batch.status() == 5          # IBF_ERR_TIMEOUT
     assert time.time() - t0 < 30
+    # every plan of the batch holds the timeout in its sticky status until read
+    assert [p.status() for p in plans] == [5] * len(plans)
+    assert [p.status() for p in plans] == [0] * len(plans)
     assert lib.ibf_batch_test_withhold(batch._b, 0, 0) == 0
     assert lib.ibf_batch_set_wait_limit(batch._b, 1 << 21) == 0
     batch.apply_persistent()

@@ -47,6 +47,7 @@ def _create(lib, phase=1, d=1, N=1024, r=9, dtype=1):
 
 def test_argument_validation_without_gpu(lib):
     import paper_1605_03616_gb300 as ibf
+    assert lib.ibf_plan_status(None) == 1
     assert _create(lib, N=1000)[0] == 1           # not a power of two
     assert _create(lib, N=2)[0] == 1              # too small
     assert _create(lib, r=2)[0] == 1
