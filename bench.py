@@ -316,6 +316,45 @@ def run_autograd(ibf, torch, N=1 << 18, nrhs=32, reps=5):
     return rec
 
 
+def run_tensorcore(ibf, torch, N=1 << 20, nrhs=64, k=4, reps=5, profile=True):
+    """Tensor-core form against the packed-FP32 SIMT form on the same workload
+    (1D FIO, r = 9, 32-column tiles, k levels per launch): per-apply and
+    per-launch CUDA-event times, and the relative difference of the results.
+    Each plan runs one warm-up apply, `reps` timed applies and (profile) one
+    apply with per-launch events."""
+    g = torch.from_numpy(W.complex_normal((nrhs, N), W.rng(workload=2), dtype=np.complex64)).cuda()
+    out, rec = {}, {"workload": "1D FIO N=%d r=9 nrhs=%d complex64, %d levels per launch, tile 32" % (N, nrhs, k)}
+    s = torch.cuda.current_stream().cuda_stream
+    for dt, name in ((ibf.C64_FP32, "fp32_simt"), (ibf.C64_TF32X3, "tf32x3_tensor")):
+        p = ibf.Plan(ibf.PHASE_FIO1D, N, 9, dt, max_nrhs=nrhs, levels_per_launch=k, rhs_tile=32)
+        u = torch.empty_like(g)
+        p.apply_raw(g.data_ptr(), u.data_ptr(), nrhs, s)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            p.apply_raw(g.data_ptr(), u.data_ptr(), nrhs, s)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        r = {"ms_per_apply": ms, "vectors_per_s": nrhs / ms * 1e3}
+        if profile:
+            p.profile_begin(64)
+            p.apply_raw(g.data_ptr(), u.data_ptr(), nrhs, s)
+            prof = p.profile_end()
+            r["launch_ms"] = [round(m, 4) for _, m in prof]
+            r["launch_kind"] = ["H" if kk == ibf.K_FUSED_H else "G" for kk, _ in prof]
+        torch.cuda.synchronize()
+        r["status"] = p.status()
+        out[name] = u
+        rec[name] = r
+        p.close()
+    a, b = out["tf32x3_tensor"], out["fp32_simt"]
+    rec["tf32x3_rel_diff_vs_fp32"] = float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+    rec["tensor_over_simt_time"] = rec["tf32x3_tensor"]["ms_per_apply"] / rec["fp32_simt"]["ms_per_apply"]
+    return rec
+
+
 def run_amplitude(ibf, torch, N=1 << 20, nrhs=16, q=3, reps=5):
     """Non-unit amplitude a(x, xi) = sum_t alpha_t(x) beta_t(xi) (Sec. 1),
     1D FIO N = 2^20, r = 9, 16 columns complex64, q = 3 terms (one pass: the
@@ -699,6 +738,10 @@ def run_gpu(a):
     if rank == 0 and not a.skip_2d:
         fio2d = run_2d(ibf, torch)
 
+    tensorcore = None
+    if rank == 0 and not a.skip_tc:
+        tensorcore = run_tensorcore(ibf, torch, N=N, nrhs=nrhs)
+
     # ---- CPU oracle on the host cores (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not a.skip_cpu:
@@ -724,7 +767,7 @@ def run_gpu(a):
                            "parallelism": "independent rhs batches per GPU (dp%d)" % world},
                 "clocks": clk, "e2e": e2e, "gpu_launches": a.steps * launches, "roofline": roof,
                 "fp64_plain": fp64, "construction": construction, "batch256": batch, "autograd": grad5, "optimal_ibf": optimal, "nufft1024_latency": nufft,
-                "amplitude": amplitude,
+                "amplitude": amplitude, "tensorcore": tensorcore,
                 "fio2d": fio2d, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     plan.close()
@@ -757,12 +800,16 @@ def main():
                     help="profiling aid: time only the FP32 optimal IBF with sweep-in (r = 12 -> 9) at size N")
     ap.add_argument("--only-amplitude", type=int, default=0, metavar="N",
                     help="profiling aid: time only the amplitude apply (q = 3, 16 columns) at size N")
+    ap.add_argument("--only-tc", type=int, default=0, metavar="N",
+                    help="profiling aid: one warm-up and one timed apply of an FP32 and a TF32X3 plan at size N "
+                         "(--nrhs columns, --levels-per-launch levels, default 4)")
+    ap.add_argument("--skip-tc", action="store_true")
     a = ap.parse_args()
     if a.warmup < 3 and a.impl == "ibf":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if a.impl == "reference":
         return run_reference(a)
-    if a.only_2d or a.only_batch or a.only_optimal or a.only_amplitude:
+    if a.only_2d or a.only_batch or a.only_optimal or a.only_amplitude or a.only_tc:
         import torch
         import paper_1605_03616_gb300 as ibf
         if a.only_2d:
@@ -772,6 +819,9 @@ def main():
         elif a.only_optimal:
             name, rec = "optimal_ibf", run_optimal(ibf, torch, N=a.only_optimal,
                                                    variants=[(12, ibf.FORM_OPTIMAL_IN, 9, ibf.C64_FP32)])
+        elif a.only_tc:
+            name, rec = "tensorcore", run_tensorcore(ibf, torch, N=a.only_tc, nrhs=a.nrhs,
+                                                     k=a.levels_per_launch or 4, reps=1, profile=False)
         else:
             name, rec = "amplitude", run_amplitude(ibf, torch, N=a.only_amplitude)
         print(json.dumps({"profile_only": name, **rec}), flush=True)

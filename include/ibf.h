@@ -19,7 +19,7 @@
  *     failure of the calling thread.
  *   - Complex vectors are interleaved (re, im).  Their element type follows the
  *     plan's dtype: complex128 (two doubles) for IBF_C128, complex64 (two
- *     floats) for IBF_C64_FP32 and IBF_C64_BF16X3.
+ *     floats) for IBF_C64_FP32, IBF_C64_TF32X3 and IBF_C64_BF16X3.
  *   - Multi-vector arguments are column-major: column c of an n x nrhs array
  *     starts at element n*c.
  *   - Streams are CUDA streams (cudaStream_t); NULL is the legacy default
@@ -75,11 +75,17 @@ enum ibf_phase {
 enum ibf_dtype {
     IBF_C128 = 0,       /* complex128 in and out, FP64 factors and FP64 arithmetic  */
     IBF_C64_FP32 = 1,   /* complex64 in and out, FP32 factors, FP32 arithmetic      */
-    IBF_C64_BF16X3 = 2  /* complex64 in and out, three-term split-BF16 tensor-core
+    IBF_C64_BF16X3 = 2, /* complex64 in and out, three-term split-BF16 tensor-core
                            products with FP32 accumulation: not built -- plan
-                           creation returns IBF_ERR_UNSUPPORTED (at r <= 11 the
-                           contractions are too small for the tensor cores to
-                           beat the packed-FP32 SIMT form)                       */
+                           creation returns IBF_ERR_UNSUPPORTED (IBF_C64_TF32X3
+                           is the tensor-core form that is built)                */
+    IBF_C64_TF32X3 = 3  /* complex64 in and out, FP32 factors (structured form,
+                           d = 1); the transfer products of the G-form levels
+                           (forward G levels, adjoint H levels) of 32-column
+                           tiles run on the tensor cores (tcgen05, kind::tf32)
+                           with both operands split in two TF32 terms and three
+                           products kept, FP32 accumulation in tensor memory;
+                           everything else as IBF_C64_FP32                       */
 };
 
 /* Storage form of the factors. */
@@ -372,10 +378,12 @@ int ibf_plan_query(const ibf_plan* plan, int what, int64_t* value);
  * ibf_apply_amplitude, ibf_apply_static_scratch) returned after its
  * arguments were accepted (CUDA launch or copy failures), and
  * IBF_ERR_TIMEOUT when ibf_batch_status finds an expired wait in a batch
- * holding the plan.  Argument errors are returned by the call itself and are
- * not recorded.  Returns that status (IBF_OK if none) and resets it to
- * IBF_OK; IBF_ERR_INVALID for a NULL plan.  No CUDA call, no
- * synchronization.  This replaces the survey's device-side per-plan status:
+ * holding the plan, or when a bounded wait of the tensor-core levels of an
+ * IBF_C64_TF32X3 plan expired on the device.  Argument errors are returned
+ * by the call itself and are not recorded.  Returns that status (IBF_OK if
+ * none) and resets it to IBF_OK; IBF_ERR_INVALID for a NULL plan.  No CUDA
+ * call except, for IBF_C64_TF32X3 plans, one synchronous read (and reset) of
+ * the device status word.  This replaces the survey's device-side per-plan status:
  * the only device-side waits are those of the persistent batch, whose status
  * word belongs to the batch.
  */

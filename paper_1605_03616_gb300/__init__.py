@@ -25,6 +25,7 @@ PHASE_SEPARABLE = 100
 C128 = 0
 C64_FP32 = 1
 C64_BF16X3 = 2
+C64_TF32X3 = 3             # tensor-core G-form levels (tcgen05 kind::tf32, two-term splits)
 
 FORM_AUTO = 0
 FORM_EXPLICIT = 1

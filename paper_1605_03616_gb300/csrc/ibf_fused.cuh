@@ -220,11 +220,150 @@ __device__ __forceinline__ double2 p2fma(double2 w, double2 x, double2 acc)
     return make_double2(fma(w.x, x.x, acc.x), fma(w.y, x.y, acc.y));
 }
 
+}  // namespace ibf
+
+#include "ibf_tc.cuh"
+
+namespace ibf {
+
+// The k butterfly levels of one block, in place in shared memory: sm holds
+// the 2^k positions of the Lambda tile (stride PS = r rt + 1), dsm the staged
+// phase tables [s-1][u][a][c][RP] (per-unit stride 4r+1).  Every level ends
+// with a barrier.
+template <typename Real, int RP, bool ADJ, int KIND, int RT>
+__device__ __forceinline__ void fused_levels(const FusedConsts<Real, RP>& C, int k, int rt_run, int ncol,
+                                             typename CT<Real>::T* sm, const typename CT<Real>::T* dsm)
+{
+    typedef typename CT<Real>::T cx;
+    const int rt = RT ? RT : rt_run;
+    const int PS = RP * rt + 1;
+    const int G = 1 << k;
+    constexpr int DS = 4 * RP + 1;
+    constexpr int HR = EO<RP>::HR, HQ = EO<RP>::HQ;
+    constexpr bool ODD = RP & 1;
+    const int nunit = G >> 1;
+    // One thread per (unit, column) computes both outputs of the unit and
+    // writes them over its two inputs.  H form (forward H levels, adjoint
+    // G levels): out_a = P T_0 (y_a0 + J y_a1) + Q T_0 (y_a0 - J y_a1).
+    // G form (forward G levels, adjoint H levels): both outputs share
+    // e = T_0^T P x_q and f = T_0^T Q x_q.
+    constexpr bool TD = (!ADJ && KIND == 1) || (ADJ && KIND == 0);
+    for (int st = 0; st < k; ++st) {
+        const int s = ADJ ? (k - st) : (st + 1);
+        const int bit = s - 1;
+        const cx* dl = dsm + (size_t)(s - 1) * nunit * DS;
+        if (!TD) {
+            for (int w = threadIdx.x; w < nunit * rt; w += blockDim.x) {
+                const int c = w % rt, u = w / rt;
+                if (c < ncol) {
+                    const int p0 = ((u >> bit) << (bit + 1)) | (u & ((1 << bit) - 1));
+                    const int p1 = p0 | (1 << bit);
+                    const cx* x0p = sm + (size_t)p0 * PS + c;
+                    const cx* x1p = sm + (size_t)p1 * PS + c;
+                    const cx* du = dl + (size_t)u * DS;
+                    // output a uses D_{a,q} (forward H) or conj(D_{q,a}) (adjoint G)
+                    const cx* d00 = du + (ADJ ? 0 : 0) * RP;
+                    const cx* d01 = du + (ADJ ? 2 : 1) * RP;
+                    const cx* d10 = du + (ADJ ? 1 : 2) * RP;
+                    const cx* d11 = du + 3 * RP;
+                    cx we0[HR], wo0[HQ > 0 ? HQ : 1], we1[HR], wo1[HQ > 0 ? HQ : 1];
+#pragma unroll
+                    for (int t = 0; t < HR; ++t) we0[t] = we1[t] = cz<cx>();
+#pragma unroll
+                    for (int t = 0; t < HQ; ++t) wo0[t] = wo1[t] = cz<cx>();
+#pragma unroll
+                    for (int s2 = 0; s2 < RP; ++s2) {
+                        const cx xa = x0p[s2 * rt], xb = x1p[(RP - 1 - s2) * rt];
+                        const cx y00 = ADJ ? cmulc(d00[s2], xa) : cmul(d00[s2], xa);
+                        const cx y01 = ADJ ? cmulc(d01[RP - 1 - s2], xb) : cmul(d01[RP - 1 - s2], xb);
+                        const cx y10 = ADJ ? cmulc(d10[s2], xa) : cmul(d10[s2], xa);
+                        const cx y11 = ADJ ? cmulc(d11[RP - 1 - s2], xb) : cmul(d11[RP - 1 - s2], xb);
+                        const cx pv0 = p2add(y00, y01), mv0 = p2sub(y00, y01);
+                        const cx pv1 = p2add(y10, y11), mv1 = p2sub(y10, y11);
+#pragma unroll
+                        for (int t = 0; t < HR; ++t) {
+                            const cx pm = C.Pm2[s2][t];
+                            we0[t] = p2fma(pm, pv0, we0[t]);
+                            we1[t] = p2fma(pm, pv1, we1[t]);
+                        }
+#pragma unroll
+                        for (int t = 0; t < HQ; ++t) {
+                            const cx qm = C.Qm2[s2][t];
+                            wo0[t] = p2fma(qm, mv0, wo0[t]);
+                            wo1[t] = p2fma(qm, mv1, wo1[t]);
+                        }
+                    }
+                    cx* o0 = sm + (size_t)p0 * PS + c;
+                    cx* o1 = sm + (size_t)p1 * PS + c;
+#pragma unroll
+                    for (int t = 0; t < HQ; ++t) {
+                        o0[t * rt] = p2add(we0[t], wo0[t]);
+                        o0[(RP - 1 - t) * rt] = p2sub(we0[t], wo0[t]);
+                        o1[t * rt] = p2add(we1[t], wo1[t]);
+                        o1[(RP - 1 - t) * rt] = p2sub(we1[t], wo1[t]);
+                    }
+                    if (ODD) {
+                        o0[HQ * rt] = we0[HQ];
+                        o1[HQ * rt] = we1[HQ];
+                    }
+                }
+            }
+        } else {
+            for (int w = threadIdx.x; w < nunit * rt; w += blockDim.x) {
+                const int c = w % rt, u = w / rt;
+                if (c < ncol) {
+                    const int p0 = ((u >> bit) << (bit + 1)) | (u & ((1 << bit) - 1));
+                    const int p1 = p0 | (1 << bit);
+                    const cx* du = dl + (size_t)u * DS;
+                    // even and odd parts of both inputs (all reads before any write)
+                    cx xe[2][HR], xo[2][HQ > 0 ? HQ : 1];
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const cx* xp = sm + (size_t)(q ? p1 : p0) * PS + c;
+#pragma unroll
+                        for (int s2 = 0; s2 < HQ; ++s2) {
+                            const cx lo = xp[s2 * rt], hi = xp[(RP - 1 - s2) * rt];
+                            xe[q][s2] = p2add(lo, hi);
+                            xo[q][s2] = p2sub(lo, hi);
+                        }
+                        if (ODD) xe[q][HQ] = xp[HQ * rt];
+                    }
+                    cx* o0 = sm + (size_t)p0 * PS + c;
+                    cx* o1 = sm + (size_t)p1 * PS + c;
+#pragma unroll
+                    for (int t = 0; t < RP; ++t) {
+                        cx a0 = cz<cx>(), a1 = cz<cx>();
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            cx e = cz<cx>(), f = cz<cx>();
+#pragma unroll
+                            for (int s2 = 0; s2 < HR; ++s2) e = p2fma(C.E2[t][s2], xe[q][s2], e);
+#pragma unroll
+                            for (int s2 = 0; s2 < HQ; ++s2) f = p2fma(C.F2[t][s2], xo[q][s2], f);
+                            // (T_0^T x_q)[t] and (T_1^T x_q)[RP-1-t]
+                            const cx z0 = p2add(e, f), z1 = p2sub(e, f);
+                            // forward G: output a uses D_{a,q}; adjoint H: output c uses conj(D_{q,c})
+                            const cx* dA = du + (ADJ ? (q * 2 + 0) : (0 * 2 + q)) * RP;
+                            const cx* dB = du + (ADJ ? (q * 2 + 1) : (1 * 2 + q)) * RP;
+                            cmacx<ADJ>(a0, dA[t], z0);
+                            cmacx<ADJ>(a1, dB[RP - 1 - t], z1);
+                        }
+                        o0[t * rt] = a0;
+                        o1[(RP - 1 - t) * rt] = a1;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    
+}
+
 // KIND: 0 = H levels (1..h), 1 = G levels (h+1..L).  RT: the rhs tile width
 // when it is known at compile time (32, the batched case), 0 otherwise.
-template <typename Real, int RP, bool ADJ, int KIND, int RT, bool COH = false>
+template <typename Real, int RP, bool ADJ, int KIND, int RT, bool COH = false, bool TCL = false>
 __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const FusedDesc& P, int64_t blk,
-                                           unsigned char* smraw)
+                                           unsigned char* smraw, TcCtx* tc = nullptr)
 {
     typedef typename CT<Real>::T cx;
     cx* sm = reinterpret_cast<cx*>(smraw);
@@ -351,125 +490,16 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
     }
     __syncthreads();
 
-    // --------------------------------------------------------------- levels
-    {
-        constexpr int HR = EO<RP>::HR, HQ = EO<RP>::HQ;
-        constexpr bool ODD = RP & 1;
-        const int nunit = G >> 1;
-        // One thread per (unit, column) computes both outputs of the unit and
-        // writes them over its two inputs.  H form (forward H levels, adjoint
-        // G levels): out_a = P T_0 (y_a0 + J y_a1) + Q T_0 (y_a0 - J y_a1).
-        // G form (forward G levels, adjoint H levels): both outputs share
-        // e = T_0^T P x_q and f = T_0^T Q x_q.
-        constexpr bool TD = (!ADJ && KIND == 1) || (ADJ && KIND == 0);
+    if constexpr (TCL) {
+        // tensor-core G-form levels (forward G, adjoint H), FP32 only
+        static_assert(sizeof(Real) == 4 && ((!ADJ && KIND == 1) || (ADJ && KIND == 0)), "G form, FP32");
         for (int st = 0; st < k; ++st) {
             const int s = ADJ ? (k - st) : (st + 1);
-            const int bit = s - 1;
-            const cx* dl = dsm + (size_t)(s - 1) * nunit * DS;
-            if (!TD) {
-                for (int w = threadIdx.x; w < nunit * rt; w += blockDim.x) {
-                    const int c = w % rt, u = w / rt;
-                    if (c < ncol) {
-                        const int p0 = ((u >> bit) << (bit + 1)) | (u & ((1 << bit) - 1));
-                        const int p1 = p0 | (1 << bit);
-                        const cx* x0p = sm + (size_t)p0 * PS + c;
-                        const cx* x1p = sm + (size_t)p1 * PS + c;
-                        const cx* du = dl + (size_t)u * DS;
-                        // output a uses D_{a,q} (forward H) or conj(D_{q,a}) (adjoint G)
-                        const cx* d00 = du + (ADJ ? 0 : 0) * RP;
-                        const cx* d01 = du + (ADJ ? 2 : 1) * RP;
-                        const cx* d10 = du + (ADJ ? 1 : 2) * RP;
-                        const cx* d11 = du + 3 * RP;
-                        cx we0[HR], wo0[HQ > 0 ? HQ : 1], we1[HR], wo1[HQ > 0 ? HQ : 1];
-#pragma unroll
-                        for (int t = 0; t < HR; ++t) we0[t] = we1[t] = cz<cx>();
-#pragma unroll
-                        for (int t = 0; t < HQ; ++t) wo0[t] = wo1[t] = cz<cx>();
-#pragma unroll
-                        for (int s2 = 0; s2 < RP; ++s2) {
-                            const cx xa = x0p[s2 * rt], xb = x1p[(RP - 1 - s2) * rt];
-                            const cx y00 = ADJ ? cmulc(d00[s2], xa) : cmul(d00[s2], xa);
-                            const cx y01 = ADJ ? cmulc(d01[RP - 1 - s2], xb) : cmul(d01[RP - 1 - s2], xb);
-                            const cx y10 = ADJ ? cmulc(d10[s2], xa) : cmul(d10[s2], xa);
-                            const cx y11 = ADJ ? cmulc(d11[RP - 1 - s2], xb) : cmul(d11[RP - 1 - s2], xb);
-                            const cx pv0 = p2add(y00, y01), mv0 = p2sub(y00, y01);
-                            const cx pv1 = p2add(y10, y11), mv1 = p2sub(y10, y11);
-#pragma unroll
-                            for (int t = 0; t < HR; ++t) {
-                                const cx pm = C.Pm2[s2][t];
-                                we0[t] = p2fma(pm, pv0, we0[t]);
-                                we1[t] = p2fma(pm, pv1, we1[t]);
-                            }
-#pragma unroll
-                            for (int t = 0; t < HQ; ++t) {
-                                const cx qm = C.Qm2[s2][t];
-                                wo0[t] = p2fma(qm, mv0, wo0[t]);
-                                wo1[t] = p2fma(qm, mv1, wo1[t]);
-                            }
-                        }
-                        cx* o0 = sm + (size_t)p0 * PS + c;
-                        cx* o1 = sm + (size_t)p1 * PS + c;
-#pragma unroll
-                        for (int t = 0; t < HQ; ++t) {
-                            o0[t * rt] = p2add(we0[t], wo0[t]);
-                            o0[(RP - 1 - t) * rt] = p2sub(we0[t], wo0[t]);
-                            o1[t * rt] = p2add(we1[t], wo1[t]);
-                            o1[(RP - 1 - t) * rt] = p2sub(we1[t], wo1[t]);
-                        }
-                        if (ODD) {
-                            o0[HQ * rt] = we0[HQ];
-                            o1[HQ * rt] = we1[HQ];
-                        }
-                    }
-                }
-            } else {
-                for (int w = threadIdx.x; w < nunit * rt; w += blockDim.x) {
-                    const int c = w % rt, u = w / rt;
-                    if (c < ncol) {
-                        const int p0 = ((u >> bit) << (bit + 1)) | (u & ((1 << bit) - 1));
-                        const int p1 = p0 | (1 << bit);
-                        const cx* du = dl + (size_t)u * DS;
-                        // even and odd parts of both inputs (all reads before any write)
-                        cx xe[2][HR], xo[2][HQ > 0 ? HQ : 1];
-#pragma unroll
-                        for (int q = 0; q < 2; ++q) {
-                            const cx* xp = sm + (size_t)(q ? p1 : p0) * PS + c;
-#pragma unroll
-                            for (int s2 = 0; s2 < HQ; ++s2) {
-                                const cx lo = xp[s2 * rt], hi = xp[(RP - 1 - s2) * rt];
-                                xe[q][s2] = p2add(lo, hi);
-                                xo[q][s2] = p2sub(lo, hi);
-                            }
-                            if (ODD) xe[q][HQ] = xp[HQ * rt];
-                        }
-                        cx* o0 = sm + (size_t)p0 * PS + c;
-                        cx* o1 = sm + (size_t)p1 * PS + c;
-#pragma unroll
-                        for (int t = 0; t < RP; ++t) {
-                            cx a0 = cz<cx>(), a1 = cz<cx>();
-#pragma unroll
-                            for (int q = 0; q < 2; ++q) {
-                                cx e = cz<cx>(), f = cz<cx>();
-#pragma unroll
-                                for (int s2 = 0; s2 < HR; ++s2) e = p2fma(C.E2[t][s2], xe[q][s2], e);
-#pragma unroll
-                                for (int s2 = 0; s2 < HQ; ++s2) f = p2fma(C.F2[t][s2], xo[q][s2], f);
-                                // (T_0^T x_q)[t] and (T_1^T x_q)[RP-1-t]
-                                const cx z0 = p2add(e, f), z1 = p2sub(e, f);
-                                // forward G: output a uses D_{a,q}; adjoint H: output c uses conj(D_{q,c})
-                                const cx* dA = du + (ADJ ? (q * 2 + 0) : (0 * 2 + q)) * RP;
-                                const cx* dB = du + (ADJ ? (q * 2 + 1) : (1 * 2 + q)) * RP;
-                                cmacx<ADJ>(a0, dA[t], z0);
-                                cmacx<ADJ>(a1, dB[RP - 1 - t], z1);
-                            }
-                            o0[t * rt] = a0;
-                            o1[(RP - 1 - t) * rt] = a1;
-                        }
-                    }
-                }
-            }
+            tc_level_g<RP, ADJ, RT>(*tc, s - 1, G >> 1, rt, ncol, sm, dsm + (size_t)(s - 1) * (G >> 1) * DS);
             __syncthreads();
         }
+    } else {
+        fused_levels<Real, RP, ADJ, KIND, RT>(C, k, rt, ncol, sm, dsm);
     }
 
     // ---------------------------------------------------------------- store
@@ -638,6 +668,22 @@ __global__ void __launch_bounds__(FusedTraits<Real>::kThreads, FusedTraits<Real>
     fused_body<Real, RP, ADJ, KIND, RT>(c_eo<Real, RP>, P.d, blockIdx.x, smraw);
 }
 
+// Single-transform launch with the G-form levels on the tensor cores (FP32
+// tiles of 32 columns, 128 threads, 128 columns of tensor memory per CTA).
+// The set-up and tear-down bracket the whole block; status receives 1 if a
+// wait for the tensor cores expired.
+template <int RP, bool ADJ, int KIND>
+__global__ void __launch_bounds__(kTcThreads, 4)
+    k_fused_tc(const __grid_constant__ FusedParams<float, RP> P, const __grid_constant__ TcOps B, int* status,
+               int tail)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    TcCtx tc;
+    tc_setup(tc, B, smraw + tail, status);
+    fused_body<float, RP, ADJ, KIND, 32, false, true>(c_eo<float, RP>, P.d, blockIdx.x, smraw, &tc);
+    tc_teardown(tc);
+}
+
 // Batched launch: CTA blocks [start[b], start[b+1]) run descriptor b, so one
 // launch covers one fused chunk of many transforms of a batch whatever their
 // sizes (all descriptors of a launch share the level kind and tile width).
@@ -790,11 +836,39 @@ static void set_smem_attr()
     }
 }
 
+// shared memory of a tensor-core CTA: the fused tile and tables, then (at a
+// 128-byte boundary) the B operands, the barrier and the tensor-memory address
+inline size_t tc_tail_offset(int k, int RP) { return (fused_smem_bytes(k, 32, RP, sizeof(float2)) + 127) & ~(size_t)127; }
+inline size_t tc_smem_bytes(int k, int RP) { return tc_tail_offset(k, RP) + sizeof(TcOps) + 16; }
+
+template <int RP, bool ADJ, int KIND>
+static void launch_tc(const FusedParams<float, RP>& P, const TcOps& B, int* status, int64_t blocks, cudaStream_t st)
+{
+    static bool attr_done[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !attr_done[dev]) {
+        int optin = 0;
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaFuncSetAttribute(k_fused_tc<RP, ADJ, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        if (dev >= 0 && dev < 64) attr_done[dev] = true;
+    }
+    k_fused_tc<RP, ADJ, KIND><<<(unsigned)blocks, kTcThreads, tc_smem_bytes(P.d.k, RP), st>>>(
+        P, B, status, (int)tc_tail_offset(P.d.k, RP));
+}
+
 template <typename Real, int RP, bool ADJ, int KIND>
-static int launch_one(const FusedParams<Real, RP>& P, int64_t ngroups, cudaStream_t st)
+static int launch_one(const FusedParams<Real, RP>& P, int64_t ngroups, cudaStream_t st, const TcOps* tcb = nullptr,
+                      int* tcstatus = nullptr)
 {
     typedef typename CT<Real>::T cx;
     const int G = 1 << P.d.k;
+    if constexpr (sizeof(Real) == 4 && ((!ADJ && KIND == 1) || (ADJ && KIND == 0))) {
+        if (tcb && P.d.rt == 32) {
+            launch_tc<RP, ADJ, KIND>(P, *tcb, tcstatus, ngroups * ((P.d.nc + 31) / 32), st);
+            return IBF_OK;
+        }
+    }
     size_t smem = fused_smem_bytes(P.d.k, P.d.rt, RP, sizeof(cx));
     int ntile = (P.d.nc + P.d.rt - 1) / P.d.rt;
     int threads = std::min(FusedTraits<Real>::kThreads, std::max(32, (G / 2) * P.d.rt));
@@ -829,6 +903,9 @@ static int fused_run(ibf_plan* p, const void* vin, void* vout, int nrhs, bool ad
     P.d.N = p->N;
     P.d.L = p->L;
     const int64_t N = p->N;
+    TcOps tcb;
+    const bool use_tc = sizeof(Real) == 4 && p->dtype == IBF_C64_TF32X3;
+    if (use_tc) tc_build_ops(p->T[0], p->T[1], RP, tcb);
     for (int c0 = 0; c0 < nrhs; c0 += p->max_nrhs) {
         const int nc = std::min(p->max_nrhs, nrhs - c0);
         const int rt = std::min(p->rtile, pow2ceil(nc));
@@ -861,12 +938,13 @@ static int fused_run(ibf_plan* p, const void* vin, void* vout, int nrhs, bool ad
             P.d.out = bufs[cur ^ 1];
             const int64_t ngroups = 1LL << (p->L - P.d.k);
             int rc;
+            const TcOps* tb = use_tc ? &tcb : nullptr;
             if (!adj)
-                rc = ch.kind == 0 ? launch_one<Real, RP, false, 0>(P, ngroups, st)
-                                  : launch_one<Real, RP, false, 1>(P, ngroups, st);
+                rc = ch.kind == 0 ? launch_one<Real, RP, false, 0>(P, ngroups, st, tb, p->d_tcstatus)
+                                  : launch_one<Real, RP, false, 1>(P, ngroups, st, tb, p->d_tcstatus);
             else
-                rc = ch.kind == 0 ? launch_one<Real, RP, true, 0>(P, ngroups, st)
-                                  : launch_one<Real, RP, true, 1>(P, ngroups, st);
+                rc = ch.kind == 0 ? launch_one<Real, RP, true, 0>(P, ngroups, st, tb, p->d_tcstatus)
+                                  : launch_one<Real, RP, true, 1>(P, ngroups, st, tb, p->d_tcstatus);
             if (rc) return rc;
             prof_mark(p, st, ch.kind == 0 ? IBF_K_FUSED_H : IBF_K_FUSED_G);
             cur ^= 1;

@@ -484,7 +484,7 @@ extern "C" int ibf_plan_create_ex(int phase_id, int d, int64_t N, int r, int dty
     if (N < 4 || N > (1LL << 24) || (N & (N - 1)))
         return set_error(IBF_ERR_INVALID, "N must be a power of two in [4, 2^24]");
     if (r < 3 || r > kMaxR) return set_error(IBF_ERR_INVALID, "r must be in [3, 16]");
-    if (dtype != IBF_C128 && dtype != IBF_C64_FP32 && dtype != IBF_C64_BF16X3)
+    if (dtype != IBF_C128 && dtype != IBF_C64_FP32 && dtype != IBF_C64_BF16X3 && dtype != IBF_C64_TF32X3)
         return set_error(IBF_ERR_INVALID, "unknown dtype");
     ibf_options o;
     memset(&o, 0, sizeof(o));
@@ -503,7 +503,9 @@ extern "C" int ibf_plan_create_ex(int phase_id, int d, int64_t N, int r, int dty
     if (form == IBF_FORM_EXPLICIT && dtype != IBF_C128 && dtype != IBF_C64_FP32)
         return set_error(IBF_ERR_UNSUPPORTED, "the explicit form is FP64 or FP32");
     if (dtype == IBF_C64_BF16X3)
-        return set_error(IBF_ERR_UNSUPPORTED, "split-BF16 tensor-core apply is not built yet");
+        return set_error(IBF_ERR_UNSUPPORTED, "split-BF16 tensor-core apply is not built (IBF_C64_TF32X3 is)");
+    if (dtype == IBF_C64_TF32X3 && form != IBF_FORM_STRUCTURED)
+        return set_error(IBF_ERR_UNSUPPORTED, "IBF_C64_TF32X3 is the structured form only");
     if (form == IBF_FORM_STRUCTURED && !fused_supports_r(r))
         return set_error(IBF_ERR_UNSUPPORTED, "structured form supports r in {5, 7, 9, 11}");
 
@@ -592,6 +594,14 @@ extern "C" int ibf_plan_create_ex(int phase_id, int d, int64_t N, int r, int dty
             return rc;
         }
     p->ws_bytes = 2 * wsb;
+    if (dtype == IBF_C64_TF32X3) {
+        // status word of the tensor-core waits (ibf_plan_status)
+        if ((rc = dalloc(p, (void**)&p->d_tcstatus, sizeof(int), false))) {
+            free_plan(p);
+            return rc;
+        }
+        cudaMemset(p->d_tcstatus, 0, sizeof(int));
+    }
     if (form == IBF_FORM_STRUCTURED) {
         fused_choose_shape(p);
         // commit the static-scratch array on this device now, while the
@@ -651,6 +661,16 @@ extern "C" int ibf_apply_adjoint(ibf_plan* p, const void* y, void* g, int nrhs, 
 extern "C" int ibf_plan_status(ibf_plan* p)
 {
     if (!p) return set_error(IBF_ERR_INVALID, "plan is NULL");
+    if (p->d_tcstatus) {
+        // tensor-core plans: a bounded wait that expired on the device
+        int dev = 0;
+        if (cudaMemcpy(&dev, p->d_tcstatus, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return set_error(IBF_ERR_CUDA, "plan status: reading the device status word failed");
+        if (dev) {
+            cudaMemset(p->d_tcstatus, 0, sizeof(int));
+            plan_note(p, IBF_ERR_TIMEOUT);
+        }
+    }
     const int st = p->sticky;
     p->sticky = IBF_OK;
     if (st != IBF_OK) return set_error(st, "sticky status of the plan: an earlier apply failed or its batch timed out");

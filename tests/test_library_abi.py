@@ -89,3 +89,21 @@ def test_form_options_validated_without_gpu(lib):
         assert create(form, r=13, rank=6) == 4                       # r above 12
         assert create(form, dtype=ibf.C64_BF16X3) == 4               # no split-BF16 form
         assert create(form, d=2, phase=ibf.PHASE_FIO2D, N=64 * 64) == 4   # 1D only
+
+
+def test_tensor_core_dtype_validated_without_gpu(lib):
+    """IBF_C64_TF32X3 is the 1D structured form only; the split-BF16 dtype is
+    not built.  Both are refused before any CUDA call."""
+    import paper_1605_03616_gb300 as ibf
+
+    def create(form, dtype, d=1, phase=ibf.PHASE_FIO1D, N=1024, r=9):
+        o = ibf.Options()
+        o.form, o.rank = form, 4
+        out = ctypes.c_void_p()
+        return lib.ibf_plan_create_ex(phase, d, N, r, dtype, None, ctypes.byref(o), ctypes.byref(out))
+
+    assert create(ibf.FORM_EXPLICIT, ibf.C64_TF32X3) == 4
+    assert create(ibf.FORM_OPTIMAL, ibf.C64_TF32X3) == 4
+    assert create(ibf.FORM_STRUCTURED, ibf.C64_TF32X3, d=2, phase=ibf.PHASE_FIO2D, N=64 * 64, r=7) == 4
+    assert create(ibf.FORM_STRUCTURED, ibf.C64_BF16X3) == 4
+    assert create(ibf.FORM_STRUCTURED, 4) == 1                       # unknown dtype
