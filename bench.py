@@ -42,14 +42,14 @@ FP32_LANES_PER_SM = 128
 # this benchmark at N = 2^20, r = 9, nrhs = 64, 4 levels per launch, tile 32
 # (the ncu DRAM capture of the fused kernels).  Keyed by the launch's level
 # range; valid only while the kernel sources hash to KERNEL_SRC_SHA.
-KERNEL_SRC_SHA = "fecf3fff897107d4"
+KERNEL_SRC_SHA = "74e333fcf127a63e"
 TRAFFIC_N20_R9_NRHS64_K4 = {
-    (0, 4, "H"): 1216440576 + 4771523840,
-    (4, 7, "H"): 5285107968 + 4778114048,
-    (7, 10, "H"): 5964420352 + 4782394624,
-    (10, 14, "G"): 5435983104 + 4779323904,
-    (14, 17, "G"): 5284954112 + 4779703040,
-    (17, 20, "G"): 5370062336 + 527404288,
+    (0, 4, "H"): 1216754944 + 4775659264,
+    (4, 7, "H"): 5285108736 + 4780080640,
+    (7, 10, "H"): 5965724160 + 4785707008,
+    (10, 14, "G"): 5436101120 + 4782749952,
+    (14, 17, "G"): 5284958208 + 4782261504,
+    (17, 20, "G"): 5369652736 + 528164608,
 }
 
 
@@ -529,6 +529,113 @@ def structured_flops(kind_levels, r, N, nc, pro, epi, kind_g):
     return f
 
 
+def fused_schedule(L, h, kfuse):
+    """Level ranges (lo, hi, kind) of the structured apply's fused launches in
+    launch order: levels 1..h and h+1..L split into balanced chunks of at most
+    kfuse levels (the library's schedule)."""
+    sched = []
+
+    def split(lo, hi, kind):
+        n = hi - lo
+        nch = (n + kfuse - 1) // kfuse
+        for c in range(nch):
+            ln = n // nch + (1 if c < n % nch else 0)
+            sched.append((lo, lo + ln, kind))
+            lo += ln
+    split(0, h, "H")
+    split(h, L, "G")
+    return sched
+
+
+def dominant_roofline(prof, L, h, kfuse, r, N, nrhs, fp32_peak, hbm_peak):
+    """Roofline of the launch with the largest total time in a per-launch
+    profile (list of (kind, ms) in launch order, whole applies): algorithmic
+    flops (structured_flops) and bytes (Lambda or g/u in and out, the phase
+    tables, the switch blocks) per launch over its mean CUDA-event time."""
+    sched = fused_schedule(L, h, kfuse)
+    per_launch = {}
+    for idx, (_, t_ms) in enumerate(prof):
+        per_launch.setdefault(sched[idx % len(sched)], []).append(t_ms)
+    tot = {k: sum(v) for k, v in per_launch.items()}
+    lo, hi, kd = max(tot, key=tot.get)
+    pro = "V" if lo == 0 else None
+    epi = "U" if hi == L else ("switch" if hi == h else None)
+    avg_ms = statistics.mean(per_launch[(lo, hi, kd)])
+    flops = structured_flops(hi - lo, r, N, nrhs, pro, epi, kd == "G")
+    esz = 8
+    bytes_alg = (N * nrhs * esz) if pro == "V" else (N * r * nrhs * esz)
+    bytes_alg += (N * nrhs * esz) if epi == "U" else (N * r * nrhs * esz)
+    bytes_alg += (hi - lo) * 2 * N * r * esz
+    if epi == "switch":
+        bytes_alg += N * r * r * esz
+    ach_tf = flops / (avg_ms / 1e3) / 1e12
+    ach_gb = bytes_alg / (avg_ms / 1e3) / 1e9
+    return {"lo": lo, "hi": hi, "kind": kd, "pro": pro, "epi": epi, "avg_ms": avg_ms, "n": len(per_launch[(lo, hi, kd)]),
+            "flops": flops, "bytes": bytes_alg, "tflops": ach_tf, "gbs": ach_gb, "alu_frac": ach_tf / fp32_peak,
+            "hbm_frac": ach_gb / hbm_peak,
+            "launch_ms": {"%s %d..%d" % (kk, a0 + 1, b0): round(statistics.mean(v), 4)
+                          for (a0, b0, kk), v in per_launch.items()}}
+
+
+def run_config2_sweep(ibf, torch, fp32_peak, hbm_peak, Ns=(1 << 16, 1 << 18, 1 << 20), nrhss=(1, 16, 64), reps=5):
+    """1D FIO grid N x nrhs: the FP32 structured apply in its autotuned launch
+    shape (vectors/s, the dominant launch's roofline fraction) against the
+    plain FP64 explicit single-vector form on the same GPU (vectors/s, and the
+    FP32 result's relative L2 difference from it on the first column)."""
+    s = torch.cuda.current_stream().cuda_stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pts = []
+    for N in Ns:
+        g = torch.from_numpy(W.complex_normal((max(nrhss), N), W.rng(workload=2), dtype=np.complex64)).cuda()
+        p64 = ibf.Plan(ibf.PHASE_FIO1D, N, 9, ibf.C128, max_nrhs=1)
+        g64 = g[0:1].to(torch.complex128).contiguous()
+        u64 = torch.empty_like(g64)
+        for _ in range(2):
+            p64.apply_raw(g64.data_ptr(), u64.data_ptr(), 1, s)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(3):
+            p64.apply_raw(g64.data_ptr(), u64.data_ptr(), 1, s)
+        e1.record()
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) / 3
+        p64.close()
+        for nrhs in nrhss:
+            plan = ibf.Plan(ibf.PHASE_FIO1D, N, 9, ibf.C64_FP32, max_nrhs=nrhs)
+            k, rt, _ = plan.autotune(nrhs)
+            gg = g[:nrhs].contiguous()
+            u = torch.empty_like(gg)
+            for _ in range(2):
+                plan.apply_raw(gg.data_ptr(), u.data_ptr(), nrhs, s)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                plan.apply_raw(gg.data_ptr(), u.data_ptr(), nrhs, s)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            plan.profile_begin(4 * plan.query(ibf.Q_LAUNCHES) + 8)
+            for _ in range(3):
+                plan.apply_raw(gg.data_ptr(), u.data_ptr(), nrhs, s)
+            prof = plan.profile_end()
+            dom = dominant_roofline(prof, plan.L, plan.h, plan.query(ibf.Q_LEVELS_PER_LAUNCH), 9, N, nrhs,
+                                    fp32_peak, hbm_peak)
+            err = float(torch.linalg.vector_norm(u[0].to(torch.complex128) - u64[0]) /
+                        torch.linalg.vector_norm(u64[0]))
+            v32 = nrhs / ms * 1e3
+            pts.append({"N": N, "nrhs": nrhs, "vectors_per_s": v32, "ms_per_apply": ms, "levels_per_launch": k,
+                        "rhs_tile": rt, "launches": plan.query(ibf.Q_LAUNCHES),
+                        "dominant_launch": "%s %d..%d" % (dom["kind"], dom["lo"] + 1, dom["hi"]),
+                        "dominant_ms": dom["avg_ms"], "alu_frac": dom["alu_frac"], "hbm_frac": dom["hbm_frac"],
+                        "fp64_plain_vectors_per_s": 1e3 / t64, "speedup_vs_fp64_plain": v32 / (1e3 / t64),
+                        "rel_err_vs_fp64": err})
+            plan.close()
+        del g
+    return {"workload": "1D FIO Phi=x*xi+c(x)|xi| r=9 complex64 (FP32 structured, autotuned per point) vs "
+                        "plain FP64 explicit single-vector form", "fp32_peak_tflops": fp32_peak,
+            "hbm_peak_gbs": hbm_peak, "points": pts}
+
+
 def run_gpu(a):
     import torch
     import torch.distributed as dist
@@ -658,8 +765,10 @@ def run_gpu(a):
     uh = torch.empty_like(gh).pin_memory()
 
     def e2e_step():
-        # ibf_apply_host: chunked copies in and out overlap the apply
-        plan.apply_host(gh, uh, stream=stream)
+        # ibf_apply_host: chunked copies in and out overlap the apply; the
+        # inputs are host-written, so a step's copy-in may overlap the
+        # previous step's last apply (IBF_HOST_PIPELINE)
+        plan.apply_host(gh, uh, stream=stream, pipeline=True)
 
     for _ in range(max(1, a.warmup)):
         e2e_step()
@@ -673,7 +782,7 @@ def run_gpu(a):
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dist if world > 1 else None, dev)
     e2e = {"value": job_throughput(nrhs, a.steps, world, e2e_ms), "unit": "vectors/s",
            "h2d_bytes_per_step": int(gh.numel() * 8), "d2h_bytes_per_step": int(uh.numel() * 8),
-           "api": "ibf_apply_host (page-locked host buffers, copies overlapped with the apply)"}
+           "api": "ibf_apply_host (page-locked host buffers, copies overlapped with the apply, IBF_HOST_PIPELINE)"}
 
     # ---- plain FP64 explicit single-vector form on the same GPU, and accuracy
     fp64 = None
@@ -742,6 +851,10 @@ def run_gpu(a):
     if rank == 0 and not a.skip_tc:
         tensorcore = run_tensorcore(ibf, torch, N=N, nrhs=nrhs)
 
+    sweep = None
+    if rank == 0 and not a.skip_sweep:
+        sweep = run_config2_sweep(ibf, torch, fp32_peak, float(pk["hbm_gbs"]))
+
     # ---- CPU oracle on the host cores (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not a.skip_cpu:
@@ -767,7 +880,7 @@ def run_gpu(a):
                            "parallelism": "independent rhs batches per GPU (dp%d)" % world},
                 "clocks": clk, "e2e": e2e, "gpu_launches": a.steps * launches, "roofline": roof,
                 "fp64_plain": fp64, "construction": construction, "batch256": batch, "autograd": grad5, "optimal_ibf": optimal, "nufft1024_latency": nufft,
-                "amplitude": amplitude, "tensorcore": tensorcore,
+                "amplitude": amplitude, "tensorcore": tensorcore, "config2_sweep": sweep,
                 "fio2d": fio2d, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     plan.close()
@@ -804,12 +917,14 @@ def main():
                     help="profiling aid: one warm-up and one timed apply of an FP32 and a TF32X3 plan at size N "
                          "(--nrhs columns, --levels-per-launch levels, default 4)")
     ap.add_argument("--skip-tc", action="store_true")
+    ap.add_argument("--skip-sweep", action="store_true")
+    ap.add_argument("--only-sweep", action="store_true", help="profiling aid: run only the config-2 grid")
     a = ap.parse_args()
     if a.warmup < 3 and a.impl == "ibf":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if a.impl == "reference":
         return run_reference(a)
-    if a.only_2d or a.only_batch or a.only_optimal or a.only_amplitude or a.only_tc:
+    if a.only_2d or a.only_batch or a.only_optimal or a.only_amplitude or a.only_tc or a.only_sweep:
         import torch
         import paper_1605_03616_gb300 as ibf
         if a.only_2d:
@@ -819,6 +934,11 @@ def main():
         elif a.only_optimal:
             name, rec = "optimal_ibf", run_optimal(ibf, torch, N=a.only_optimal,
                                                    variants=[(12, ibf.FORM_OPTIMAL_IN, 9, ibf.C64_FP32)])
+        elif a.only_sweep:
+            pk, _ = peaks()
+            nsm = torch.cuda.get_device_properties(0).multi_processor_count
+            fp32_peak = nsm * FP32_LANES_PER_SM * 2 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+            name, rec = "config2_sweep", run_config2_sweep(ibf, torch, fp32_peak, float(pk["hbm_gbs"]))
         elif a.only_tc:
             name, rec = "tensorcore", run_tensorcore(ibf, torch, N=a.only_tc, nrhs=a.nrhs,
                                                      k=a.levels_per_launch or 4, reps=1, profile=False)

@@ -195,7 +195,7 @@ int ibf_apply(ibf_plan* plan, const void* g, void* u, int nrhs, ibf_stream_t str
 int ibf_apply_adjoint(ibf_plan* plan, const void* y, void* g, int nrhs, ibf_stream_t stream);
 
 /*
- * ibf_apply_host -- u = K g (adjoint = 0) or g = K^* y (adjoint = 1) with
+ * ibf_apply_host -- u = K g or g = K^* y (bit 0 of `flags`, IBF_HOST_ADJOINT) with
  * both vectors in host memory (same column-major layouts as ibf_apply and
  * ibf_apply_adjoint).  The paper applies the factors to resident vectors; this
  * is the transfer-overlapped form of the same apply for data that lives on
@@ -211,9 +211,20 @@ int ibf_apply_adjoint(ibf_plan* plan, const void* y, void* g, int nrhs, ibf_stre
  * the device), copy streams and events: make it outside stream capture.
  * Returns once the work is queued; out_host is complete when `stream` is.
  * Calls on one plan must be ordered on `stream`.  Errors as ibf_apply;
- * IBF_ERR_OOM if the staging buffers cannot be allocated.
+ * IBF_ERR_OOM if the staging buffers cannot be allocated, IBF_ERR_INVALID
+ * for unknown flag bits.
+ *   flags : IBF_HOST_ADJOINT (1) applies K^*; IBF_HOST_PIPELINE (2) declares
+ *          that in_host is written only by the host (no earlier work queued
+ *          on `stream` produces it).  Without it the first copy-in waits for
+ *          all earlier work on `stream`; with it the copy-in waits only until
+ *          the plan's staging buffers are free (the previous call's applies
+ *          that read them, and its copy-outs when that call's out_host
+ *          overlaps this call's in_host), so back-to-back calls overlap the
+ *          copy-in of one with the last apply of the other.  `stream` still
+ *          completes only after every copy-out of the call.
  */
-int ibf_apply_host(ibf_plan* plan, const void* in_host, void* out_host, int nrhs, int adjoint,
+enum { IBF_HOST_ADJOINT = 1, IBF_HOST_PIPELINE = 2 };
+int ibf_apply_host(ibf_plan* plan, const void* in_host, void* out_host, int nrhs, int flags,
                    ibf_stream_t stream);
 
 /*

@@ -27,6 +27,8 @@ C64_FP32 = 1
 C64_BF16X3 = 2
 C64_TF32X3 = 3             # tensor-core G-form levels (tcgen05 kind::tf32, two-term splits)
 
+HOST_ADJOINT, HOST_PIPELINE = 1, 2   # ibf_apply_host flags
+
 FORM_AUTO = 0
 FORM_EXPLICIT = 1
 FORM_STRUCTURED = 2
@@ -246,12 +248,14 @@ class Plan:
         _check(self._lib.ibf_apply_adjoint(self._p, ctypes.c_void_p(y_ptr), ctypes.c_void_p(g_ptr), nrhs,
                                            ctypes.c_void_p(stream_ptr)))
 
-    def apply_host(self, src, dst, adjoint: bool = False, stream=None) -> None:
+    def apply_host(self, src, dst, adjoint: bool = False, stream=None, pipeline: bool = False) -> None:
         """ibf_apply_host: `src` and `dst` are CPU tensors (or numpy arrays) of
         shape (nrhs, N), complex64 or complex128 to match the plan; page-locked
         tensors (`pin_memory()`) overlap the copies with the apply.  Queued on
         `stream` (default: the current CUDA stream); synchronise it before
-        reading `dst`."""
+        reading `dst`.  pipeline=True (IBF_HOST_PIPELINE) declares that `src`
+        is written only by the host, so the copy-in may overlap the previous
+        call's last apply."""
         torch = _torch()
 
         def ptr(a):
@@ -260,7 +264,8 @@ class Plan:
         nrhs = int(src.shape[0]) if len(src.shape) == 2 else 1
         s = (stream or torch.cuda.current_stream()).cuda_stream
         _check(self._lib.ibf_apply_host(self._p, ctypes.c_void_p(ptr(src)), ctypes.c_void_p(ptr(dst)), nrhs,
-                                        1 if adjoint else 0, ctypes.c_void_p(s)))
+                                        (HOST_ADJOINT if adjoint else 0) | (HOST_PIPELINE if pipeline else 0),
+                                        ctypes.c_void_p(s)))
 
     def apply_amplitude(self, v, alpha, beta, adjoint: bool = False, out=None, work=None, stream=None):
         """u = A g (or g = A^* y with adjoint=True) for the amplitude

@@ -404,7 +404,7 @@ extern "C" int ibf_batch_create(ibf_plan* const* plans, int count, const int* nr
                 start.push_back(blocks);
                 const int64_t ntile = (nrhs[b] + rt[b] - 1) / rt[b];
                 blocks += (1LL << (p->L - d.k)) * ntile;
-                smem = std::max(smem, fused_smem_bytes(d.k, rt[b], p->r, esz));
+                smem = std::max(smem, fused_smem_bytes(d.k, rt[b], p->r, esz, d.pro));
                 threads = std::max(threads, std::min(cap, (1 << (d.k - 1)) * rt[b]));
             }
             if (descs.empty()) continue;
@@ -490,7 +490,7 @@ extern "C" int ibf_batch_create(ibf_plan* const* plans, int count, const int* nr
                 descs.push_back(d);
                 start.push_back(total);
                 total += blocks;
-                smem = std::max(smem, fused_smem_bytes(d.k, 32, p->r, esz));
+                smem = std::max(smem, fused_smem_bytes(d.k, 32, p->r, esz, d.pro));
             }
         B->p_n = (int)descs.size();
         B->p_total = total;

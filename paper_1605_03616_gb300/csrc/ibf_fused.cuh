@@ -226,6 +226,36 @@ __device__ __forceinline__ double2 p2fma(double2 w, double2 x, double2 acc)
 
 namespace ibf {
 
+// Asynchronous copies of the phase tables of a fused block into dsm: every
+// unit of every fused level, [s-1][u][a][c][RP] with per-unit stride 4r+1 (the
+// CTA reads each entry once from global memory); one thread per (level, unit,
+// a, c) row of r contiguous entries.  Completed by cp_async_wait().
+template <typename Real, int RP>
+__device__ __forceinline__ void fused_stage_tables(const FusedDesc& P, int64_t i0, int64_t jb, int k,
+                                                   typename CT<Real>::T* dsm)
+{
+    typedef typename CT<Real>::T cx;
+    constexpr int DS = 4 * RP + 1;
+    const int L = P.L, l0 = P.l0;
+    const int nunit = (1 << k) >> 1;
+    const int rows_per_level = nunit * 4;
+    for (int row = threadIdx.x; row < k * rows_per_level; row += blockDim.x) {
+        const int st1 = row / rows_per_level;          // level s = st1 + 1 of the launch
+        const int rr = row - st1 * rows_per_level;
+        const int u = rr >> 2, ac = rr & 3;             // ac = a * 2 + c
+        const int s = st1 + 1, bit = st1;
+        const int p0 = ((u >> bit) << (bit + 1)) | (u & ((1 << bit) - 1));
+        const int low = p0 & ((1 << bit) - 1);
+        const int64_t ia = (i0 << s) + ((int64_t)brevk(low, bit) << 1) + (ac >> 1);
+        const int64_t C = (((jb << (k - s)) + (p0 >> s)) << 1) + (ac & 1);
+        const int64_t ldC = 1LL << (L - l0 - s + 1);
+        const cx* src = (const cx*)P.D[st1] + (ia * ldC + C) * RP;
+        cx* dst = dsm + (st1 * nunit + u) * DS + ac * RP;
+#pragma unroll
+        for (int t = 0; t < RP; ++t) cp_async_elem(dst + t, src + t, true);
+    }
+}
+
 // The k butterfly levels of one block, in place in shared memory: sm holds
 // the 2^k positions of the Lambda tile (stride PS = r rt + 1), dsm the staged
 // phase tables [s-1][u][a][c][RP] (per-unit stride 4r+1).  Every level ends
@@ -384,19 +414,34 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
     const int64_t jb = grp & ((1LL << nbj) - 1);
     const int64_t N = P.N;
 
+    constexpr int DS = 4 * RP + 1;   // per-unit stride of the staged tables, padded against bank conflicts
+    cx* dsm = sm + (size_t)G * PS;
+    // a Lambda tile read through asynchronous copies: the table copies go out
+    // with it, one wait and one barrier for both
+    // (g and the V^0 rows, read only, go the same way in every mode)
+    const bool early = (P.pro == PRO_LAMBDA && !COH) || P.pro == PRO_V;
+    if (early) fused_stage_tables<Real, RP>(P, i0, jb, k, dsm);
+
     // ---------------------------------------------------------------- load
     if (P.pro == PRO_V) {
-        // forward, l0 = 0: Lambda^0_{0,j} = V^0-expansion of g(xi_j), j = jb 2^k + pos
-        const cx* g = (const cx*)P.vin;
-        // the CTA's V^0 rows are contiguous: stage them after the Lambda tile
-        cx* vs = sm + (size_t)G * PS;
+        // forward, l0 = 0: Lambda^0_{0,j} = V^0-expansion of g(xi_j), j = jb 2^k + pos.
+        // The block's g values ([c][pos]) and its V^0 rows (contiguous) are
+        // staged after the table region, with the table copies in flight.
+        cx* gt = dsm + fused_region_elems(k, RP);
+        cx* vs = gt + (size_t)G * rt;
+        const cx* g = (const cx*)P.vin + (jb << k);
+        for (int e = threadIdx.x; e < G * rt; e += blockDim.x) {
+            const int pos = e & (G - 1), c = e >> k;
+            const bool on = c < ncol;
+            cp_async_elem(gt + e, g + pos + N * (int64_t)(col0 + (on ? c : 0)), on);
+        }
         const cx* Vg = (const cx*)P.Vs + (jb << k) * RP;
-        for (int e = threadIdx.x; e < G * RP; e += blockDim.x) vs[e] = Vg[e];
+        for (int e = threadIdx.x; e < G * RP; e += blockDim.x) cp_async_elem(vs + e, Vg + e, true);
+        cp_async_wait();
         __syncthreads();
         for (int e = threadIdx.x; e < G * rt; e += blockDim.x) {
             const int pos = e & (G - 1), c = e >> k;
-            const int64_t kx = (jb << k) + pos;
-            cx gv = c < ncol ? g[kx + N * (col0 + c)] : cz<cx>();
+            const cx gv = gt[e];
 #pragma unroll
             for (int t = 0; t < RP; ++t) sm[pos * PS + t * rt + c] = cmul(vs[pos * RP + t], gv);
         }
@@ -460,35 +505,16 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
             }
         }
     }
+    if (early) cp_async_wait();
     __syncthreads();
 
     // ------------------------------------------------- stage phase tables
-    // D entries of every unit of every fused level, [s-1][u][a][c][RP]; the
-    // CTA reads each once from global memory.
-    constexpr int DS = 4 * RP + 1;   // per-unit stride, padded against bank conflicts
-    cx* dsm = sm + (size_t)G * PS;
-    {
-        // one thread per (level, unit, a, c) row of r contiguous table entries
-        const int nunit = G >> 1;
-        const int rows_per_level = nunit * 4;
-        for (int row = threadIdx.x; row < k * rows_per_level; row += blockDim.x) {
-            const int st1 = row / rows_per_level;          // level s = st1 + 1 of the launch
-            const int rr = row - st1 * rows_per_level;
-            const int u = rr >> 2, ac = rr & 3;             // ac = a * 2 + c
-            const int s = st1 + 1, bit = st1;
-            const int p0 = ((u >> bit) << (bit + 1)) | (u & ((1 << bit) - 1));
-            const int low = p0 & ((1 << bit) - 1);
-            const int64_t ia = (i0 << s) + ((int64_t)brevk(low, bit) << 1) + (ac >> 1);
-            const int64_t C = (((jb << (k - s)) + (p0 >> s)) << 1) + (ac & 1);
-            const int64_t ldC = 1LL << (L - l0 - s + 1);
-            const cx* src = (const cx*)P.D[st1] + (ia * ldC + C) * RP;
-            cx* dst = dsm + (st1 * nunit + u) * DS + ac * RP;
-#pragma unroll
-            for (int t = 0; t < RP; ++t) cp_async_elem(dst + t, src + t, true);
-        }
+    // (issued above together with the Lambda tile when the input is a tile)
+    if (!early) {
+        fused_stage_tables<Real, RP>(P, i0, jb, k, dsm);
         cp_async_wait();
+        __syncthreads();
     }
-    __syncthreads();
 
     if constexpr (TCL) {
         // tensor-core G-form levels (forward G, adjoint H), FP32 only
@@ -806,11 +832,13 @@ static int fused_upload_consts(const ibf_plan* p)
 }
 
 // dynamic shared memory of one fused CTA: the Lambda tile plus the staged
-// phase tables of its k levels (padded per-unit stride 4r+1)
-inline size_t fused_smem_bytes(int k, int rt, int RP, size_t esz)
+// phase tables of its k levels (padded per-unit stride 4r+1); a launch with
+// the V^0 prologue also stages its g values and V^0 rows
+inline size_t fused_smem_bytes(int k, int rt, int RP, size_t esz, int pro = PRO_LAMBDA)
 {
     const size_t G = (size_t)1 << k;
-    return (G * ((size_t)RP * rt + 1) + fused_region_elems(k, RP)) * esz;
+    const size_t extra = pro == PRO_V ? G * ((size_t)rt + RP) : 0;
+    return (G * ((size_t)RP * rt + 1) + fused_region_elems(k, RP) + extra) * esz;
 }
 
 // largest fusion depth whose CTA fits the shared-memory budget that keeps
@@ -869,7 +897,7 @@ static int launch_one(const FusedParams<Real, RP>& P, int64_t ngroups, cudaStrea
             return IBF_OK;
         }
     }
-    size_t smem = fused_smem_bytes(P.d.k, P.d.rt, RP, sizeof(cx));
+    size_t smem = fused_smem_bytes(P.d.k, P.d.rt, RP, sizeof(cx), P.d.pro);
     int ntile = (P.d.nc + P.d.rt - 1) / P.d.rt;
     int threads = std::min(FusedTraits<Real>::kThreads, std::max(32, (G / 2) * P.d.rt));
     threads = (threads + 31) / 32 * 32;

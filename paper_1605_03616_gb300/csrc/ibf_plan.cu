@@ -706,11 +706,13 @@ static int host_setup(ibf_plan* p)
     return IBF_OK;
 }
 
-extern "C" int ibf_apply_host(ibf_plan* p, const void* hin, void* hout, int nrhs, int adjoint, ibf_stream_t stream)
+extern "C" int ibf_apply_host(ibf_plan* p, const void* hin, void* hout, int nrhs, int flags, ibf_stream_t stream)
 {
     if (!p) return set_error(IBF_ERR_INVALID, "plan is NULL");
     if (!hin || !hout) return set_error(IBF_ERR_INVALID, "NULL vector pointer");
     if (nrhs < 1) return set_error(IBF_ERR_INVALID, "nrhs must be >= 1");
+    if (flags & ~(IBF_HOST_ADJOINT | IBF_HOST_PIPELINE)) return set_error(IBF_ERR_INVALID, "unknown flag bits");
+    const bool adjoint = flags & IBF_HOST_ADJOINT;
     const size_t esz = p->dtype == IBF_C128 ? 16 : 8;
     if (((uintptr_t)hin % esz) || ((uintptr_t)hout % esz)) return set_error(IBF_ERR_INVALID, "misaligned vector pointer");
     int rc = host_setup(p);
@@ -722,10 +724,28 @@ extern "C" int ibf_apply_host(ibf_plan* p, const void* hin, void* hout, int nrhs
     char* slot_out[2] = {(char*)p->hst_buf + 2 * col * ch, (char*)p->hst_buf + 3 * col * ch};
     cudaEvent_t ev0 = p->hst_ev[0], *h2d = p->hst_ev + 1, *app = p->hst_ev + 3, *d2h = p->hst_ev + 5;
     cudaError_t e;
-    // earlier work on `stream` (a previous call's applies) comes first
-    if ((e = cudaEventRecord(ev0, st)) != cudaSuccess) return cuda_error(e, "host apply: event");
-    cudaStreamWaitEvent(p->hst_in, ev0, 0);
-    cudaStreamWaitEvent(p->hst_out, ev0, 0);
+    const size_t total = col * (size_t)nrhs;
+    const bool first = p->hst_prev_out == nullptr;
+    if ((flags & IBF_HOST_PIPELINE) && !first) {
+        // the copy-in waits only for the staging slots: the previous call's
+        // applies read them; if that call's output overlaps this input, its
+        // copy-outs too
+        cudaStreamWaitEvent(p->hst_in, app[0], 0);
+        cudaStreamWaitEvent(p->hst_in, app[1], 0);
+        const char* po = (const char*)p->hst_prev_out;
+        const char* ci = (const char*)hin;
+        if (ci < po + p->hst_prev_bytes && po < ci + total) {
+            cudaStreamWaitEvent(p->hst_in, d2h[0], 0);
+            cudaStreamWaitEvent(p->hst_in, d2h[1], 0);
+        }
+    } else {
+        // earlier work on `stream` (a previous call's applies) comes first
+        if ((e = cudaEventRecord(ev0, st)) != cudaSuccess) return cuda_error(e, "host apply: event");
+        cudaStreamWaitEvent(p->hst_in, ev0, 0);
+        cudaStreamWaitEvent(p->hst_out, ev0, 0);
+    }
+    p->hst_prev_out = hout;
+    p->hst_prev_bytes = total;
     const int nch = (nrhs + ch - 1) / ch;
     for (int j = 0; j < nch; ++j) {
         const int s = j & 1, c0 = j * ch, nc = std::min(ch, nrhs - c0);

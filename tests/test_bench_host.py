@@ -91,3 +91,20 @@ def test_reference_arm_line(tmp_path):
     env = dict(os.environ, RANK="1")
     out = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=str(tmp_path), env=env)
     assert out.returncode == 0 and out.stdout.strip() == ""
+
+
+def test_fused_schedule_and_dominant_roofline():
+    """The bench's copy of the launch schedule (levels 1..h and h+1..L in
+    balanced chunks of at most k levels) and the dominant launch it picks
+    from a per-launch profile."""
+    import bench
+    assert bench.fused_schedule(20, 10, 4) == [(0, 4, "H"), (4, 7, "H"), (7, 10, "H"), (10, 14, "G"), (14, 17, "G"),
+                                               (17, 20, "G")]
+    assert bench.fused_schedule(11, 5, 4) == [(0, 3, "H"), (3, 5, "H"), (5, 8, "G"), (8, 11, "G")]
+    # two applies; the switch launch (7..10) is the longest in total
+    prof = [(4, 3.0), (4, 2.0), (4, 3.5), (5, 3.1), (5, 2.1), (5, 2.2)] * 2
+    d = bench.dominant_roofline(prof, 20, 10, 4, 9, 1 << 20, 64, 80.0, 6800.0)
+    assert (d["lo"], d["hi"], d["kind"], d["epi"], d["n"]) == (7, 10, "H", "switch", 2)
+    assert abs(d["avg_ms"] - 3.5) < 1e-12
+    assert d["flops"] == bench.structured_flops(3, 9, 1 << 20, 64, None, "switch", False)
+    assert abs(d["alu_frac"] - d["flops"] / 3.5e-3 / 1e12 / 80.0) < 1e-12

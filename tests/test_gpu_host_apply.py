@@ -74,3 +74,31 @@ def test_host_apply_2d_and_explicit(ibf):
     assert torch.equal(oe, _device(pe, ge))
     p2.close()
     pe.close()
+
+
+def test_host_apply_pipelined_calls(ibf):
+    """IBF_HOST_PIPELINE: back-to-back calls whose copy-in may overlap the
+    previous call's last apply give the device apply's results bit for bit,
+    also when one call's output is the next call's input (then the copy-in
+    waits for the previous copy-outs) and with an unflagged call in between."""
+    N, nrhs = 1 << 12, 70                      # chunks of 32, 32 and 6 columns
+    plan = ibf.Plan(ibf.PHASE_FIO1D, N, 9, ibf.C64_FP32, max_nrhs=64)
+    gs = [W.complex_normal((nrhs, N), W.rng(830 + i), dtype=np.complex64) for i in range(4)]
+    src = [torch.from_numpy(g).pin_memory() for g in gs]
+    dst = [torch.full_like(s, float("nan")).pin_memory() for s in src]
+    for i in range(4):
+        plan.apply_host(src[i], dst[i], pipeline=(i != 2))
+    # chained: the output of one call is the input of the next
+    c1 = torch.full_like(src[0], float("nan")).pin_memory()
+    c2 = torch.full_like(src[0], float("nan")).pin_memory()
+    plan.apply_host(src[0], c1, pipeline=True)
+    plan.apply_host(c1, c2, pipeline=True)
+    torch.cuda.current_stream().synchronize()
+    for g, d in zip(gs, dst):
+        assert torch.equal(d, _device(plan, g))
+    ref1 = _device(plan, gs[0])
+    assert torch.equal(c1, ref1)
+    assert torch.equal(c2, _device(plan, ref1.numpy()))
+    lib = ibf.load_library()
+    assert lib.ibf_apply_host(plan._p, src[0].data_ptr(), dst[0].data_ptr(), 1, 4, None) == 1   # unknown flag
+    plan.close()
