@@ -461,14 +461,48 @@ def run_batch(ibf, torch, reps=5, count=256, seed=4):
     perr = max(float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)) for a, b in zip(outs, ref))
     pstatus = batch.status()
     vec = int(nr.sum())
+    # algorithmic FP32 flops of the whole batch (independent of the fusion depth)
+    flops = sum(apply_flops(int(e), 9, 1 << int(e), int(k)) for e, k in zip(es, nr))
+    g_launches = batch.query(ibf.BQ_LAUNCHES)
+    batch.close()
+    # the graph again with every plan's launch shape picked by the autotuner
+    for p, k in zip(plans, nr):
+        p.autotune(int(k))
+    tbatch = ibf.Batch(plans, ins, outs)
+    with torch.cuda.stream(stream):
+        tbatch.apply(stream=stream)
+    stream.synchronize()
+    tgraph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(tgraph, stream=stream):
+        tbatch.apply(stream=stream)
+    for _ in range(2):
+        tgraph.replay()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        tgraph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    t_tuned = e0.elapsed_time(e1) / reps
+    terr = max(float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)) for a, b in zip(outs, ref))
+    t_launches = tbatch.query(ibf.BQ_LAUNCHES)
+    tbatch.close()
+    pk, _ = peaks()
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    fp32_peak = nsm * FP32_LANES_PER_SM * 2 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
     res = {"workload": "256 x 1D FIO, N=2^e e~U{10..16}, nrhs~U{1..64}, r=9, complex64",
            "vectors": vec, "graph_ms": t_graph, "loop_ms": t_loop,
            "graph_vectors_per_s": vec / (t_graph / 1e3), "loop_vectors_per_s": vec / (t_loop / 1e3),
-           "speedup_vs_loop": t_loop / t_graph, "launches_graph": batch.query(ibf.BQ_LAUNCHES),
+           "speedup_vs_loop": t_loop / t_graph, "launches_graph": g_launches,
            "launches_loop": sum(p.query(ibf.Q_LAUNCHES) for p in plans), "max_rel_diff_graph_vs_loop": err,
            "persistent_ms": t_pers, "persistent_vectors_per_s": vec / (t_pers / 1e3), "persistent_launches": 1,
-           "persistent_max_rel_diff": perr, "persistent_status": pstatus}
-    batch.close()
+           "persistent_max_rel_diff": perr, "persistent_status": pstatus,
+           "tuned_graph_ms": t_tuned, "tuned_graph_vectors_per_s": vec / (t_tuned / 1e3),
+           "tuned_launches_graph": t_launches, "tuned_max_rel_diff": terr,
+           "alg_gflop": flops / 1e9, "fp32_peak_tflops": fp32_peak,
+           "graph_alu_frac": flops / (t_graph / 1e3) / 1e12 / fp32_peak,
+           "tuned_graph_alu_frac": flops / (t_tuned / 1e3) / 1e12 / fp32_peak,
+           "persistent_alu_frac": flops / (t_pers / 1e3) / 1e12 / fp32_peak}
     for p in plans:
         p.close()
     return res
@@ -634,6 +668,14 @@ def run_config2_sweep(ibf, torch, fp32_peak, hbm_peak, Ns=(1 << 16, 1 << 18, 1 <
     return {"workload": "1D FIO Phi=x*xi+c(x)|xi| r=9 complex64 (FP32 structured, autotuned per point) vs "
                         "plain FP64 explicit single-vector form", "fp32_peak_tflops": fp32_peak,
             "hbm_peak_gbs": hbm_peak, "points": pts}
+
+
+def apply_flops(L, r, N, nc):
+    """Algorithmic FP32 flops of one structured apply (switch at h = L // 2):
+    h H levels, L - h G levels, the V^0 prologue, the switch and U^L."""
+    h = L // 2
+    return (structured_flops(h, r, N, nc, "V", "switch", False) +
+            structured_flops(L - h, r, N, nc, None, "U", True))
 
 
 def run_gpu(a):

@@ -66,6 +66,12 @@ enum ibf_phase {
                                    have 2D forms: x.xi and 0.75 sin(2 pi x1)
                                    cos(2 pi x2) + 0.125|xi| + 0.3 sin(0.1 xi1 -
                                    0.07 xi2).                                         */
+    IBF_PHASE_FIO1D_SERIES = 4, /* Phi = x xi + c(x)|xi| with a caller-given
+                                   coefficient c(x) = sum_{m<M} a_m cos(2 pi m x)
+                                   + b_m sin(2 pi m x) (ibf_options.phase_coef,
+                                   phase_ncoef): the 1D FIOs of Assumption 1.1
+                                   with a smooth periodic c; Sec. 6.2's phase is
+                                   a_0 = 1/4, b_1 = 1/8.  d = 1 only.              */
     IBF_PHASE_SEPARABLE = 100   /* test phase f(x) + h(xi), f = 0.75 sin 2 pi x,
                                    h = 0.125|xi| + 0.3 sin(0.1 xi); the remainder
                                    R^{AB} of eq. RAB vanishes, so the IBF is exact    */
@@ -128,6 +134,9 @@ typedef struct ibf_options {
                               power of two); <= 0 lets the autotuner choose        */
     int rank;              /* optimal form: rank r0 of every compressed block,
                               1..r (the paper's r0); ignored by the other forms    */
+    const double* phase_coef; /* IBF_PHASE_FIO1D_SERIES: 2 M host doubles, a_0..a_{M-1}
+                              then b_0..b_{M-1}; copied at creation              */
+    int phase_ncoef;       /* IBF_PHASE_FIO1D_SERIES: M, 1..16                     */
 } ibf_options;
 
 /*

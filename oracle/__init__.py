@@ -35,6 +35,7 @@ PHASE_NUFFT = 0
 PHASE_FIO1D = 1
 PHASE_FIO2D = 2
 PHASE_FIO2D_32 = 3      # the 2D FIO with the constants /32 printed in Sec. 6.3
+PHASE_FIO1D_SERIES = 4   # Phi = x xi + c(x)|xi|, c a trigonometric series (set_series)
 PHASE_SEPARABLE = 100
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -61,6 +62,8 @@ def _configure(lib):
     Ci = ctypes.c_int
     lib.orc_phi_1d.restype = ctypes.c_double
     lib.orc_phi_1d.argtypes = [Ci, ctypes.c_double, ctypes.c_double]
+    lib.orc_set_series.restype = Ci
+    lib.orc_set_series.argtypes = [Ci, P, P]
     lib.orc_phi_2d.restype = ctypes.c_double
     lib.orc_phi_2d.argtypes = [Ci] + [ctypes.c_double] * 4
     lib.orc_cheb_grid.argtypes = [Ci, P]
@@ -127,6 +130,16 @@ def _cols(g: np.ndarray, n: int) -> tuple[np.ndarray, int, bool]:
 def _uncols(buf: np.ndarray, n: int, nrhs: int, vec: bool) -> np.ndarray:
     out = buf.reshape(nrhs, n).T.copy()
     return out[:, 0] if vec else out
+
+
+def set_series(a, b) -> None:
+    """Coefficients of PHASE_FIO1D_SERIES: c(x) = sum_m a[m] cos(2 pi m x) +
+    b[m] sin(2 pi m x), m < len(a) (len(b) == len(a), 1..16 terms)."""
+    a = _f64(a)
+    b = _f64(b)
+    if a.shape != b.shape or not 1 <= a.size <= 16:
+        raise ValueError("a and b: the same length, 1..16")
+    assert _load().orc_set_series(a.size, _ptr(a), _ptr(b)) == 0
 
 
 def phi_1d(phase_id: int, x: float, xi: float) -> float:

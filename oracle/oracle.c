@@ -45,6 +45,7 @@ typedef double complex cplx;
 #define ORC_PHASE_FIO1D 1      /* Phi = x xi + c(x)|xi|, c = (2+sin 2 pi x)/8  */
 #define ORC_PHASE_FIO2D 2      /* Phi = x.xi + sqrt(c1^2 xi1^2 + c2^2 xi2^2), c /16 */
 #define ORC_PHASE_FIO2D_32 3   /* the same with the constants /32 of Sec. 6.3      */
+#define ORC_PHASE_FIO1D_SERIES 4 /* Phi = x xi + c(x)|xi|, c a trigonometric series */
 #define ORC_PHASE_SEPARABLE 100 /* test phase f(x) + h(xi): remainder R^{AB}=0 */
 
 /* ------------------------------------------------------------------ */
@@ -59,11 +60,38 @@ static cplx e2pi(double t)
     return cos(a) + I * sin(a);
 }
 
+/* Coefficient series of ORC_PHASE_FIO1D_SERIES: c(x) = sum_{m<M} a_m cos(2 pi m x)
+ * + b_m sin(2 pi m x) (the FIO class of Sec. 1, Assumption 1.1, in 1D with a
+ * smooth periodic c; Sec. 6.2's phase is a_0 = 1/4, b_1 = 1/8).  Set by
+ * orc_set_series before the phase is used; one series per process. */
+static int orc_nco = 0;
+static double orc_ca[16], orc_cb[16];
+
+int orc_set_series(int M, const double* a, const double* b)
+{
+    if (M < 1 || M > 16) return 1;
+    orc_nco = M;
+    for (int m = 0; m < M; ++m) {
+        orc_ca[m] = a[m];
+        orc_cb[m] = b[m];
+    }
+    return 0;
+}
+
 /* 1D phase functions: eq. 1D-FT (with the sign of the K = e(+x xi) reading),
- * eq. 1D-FIO-kernal, and the separable test phase. */
+ * eq. 1D-FIO-kernal, the FIO with a series coefficient, and the separable
+ * test phase. */
 double orc_phi_1d(int phase_id, double x, double xi)
 {
     switch (phase_id) {
+    case ORC_PHASE_FIO1D_SERIES: {
+        double c = 0.0;
+        for (int m = 0; m < orc_nco; ++m) {
+            double arg = 2.0 * M_PI * (double)m * x;
+            c += orc_ca[m] * cos(arg) + orc_cb[m] * sin(arg);
+        }
+        return x * xi + c * fabs(xi);
+    }
     case ORC_PHASE_NUFFT:
         return x * xi;
     case ORC_PHASE_FIO1D: {

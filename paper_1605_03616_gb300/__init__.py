@@ -20,6 +20,7 @@ from .build import LIB as _LIB_PATH
 PHASE_NUFFT = 0
 PHASE_FIO1D = 1
 PHASE_FIO2D = 2
+PHASE_FIO1D_SERIES = 4     # Phi = x xi + c(x)|xi|, c(x) a trigonometric series (coef=(a, b))
 PHASE_SEPARABLE = 100
 
 C128 = 0
@@ -62,7 +63,8 @@ class IBFError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int), ("h", ctypes.c_int), ("max_nrhs", ctypes.c_int),
-                ("levels_per_launch", ctypes.c_int), ("rhs_tile", ctypes.c_int), ("rank", ctypes.c_int)]
+                ("levels_per_launch", ctypes.c_int), ("rhs_tile", ctypes.c_int), ("rank", ctypes.c_int),
+                ("phase_coef", ctypes.c_void_p), ("phase_ncoef", ctypes.c_int)]
 
 
 _lib = None
@@ -133,7 +135,7 @@ class Plan:
 
     def __init__(self, phase: int, N: int, r: int = 9, dtype: int = C64_FP32, x=None, d: int = 1,
                  form: int = FORM_AUTO, h: int = 0, max_nrhs: int = 0, levels_per_launch: int = 0,
-                 rhs_tile: int = 0, rank: int = 0):
+                 rhs_tile: int = 0, rank: int = 0, coef=None):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("the IBF library runs on a CUDA GPU only; none is available")
@@ -141,6 +143,14 @@ class Plan:
         self._lib = load_library()
         self.N, self.r, self.dtype, self.phase = int(N), int(r), int(dtype), int(phase)
         opt = Options(form, h, max_nrhs, levels_per_launch, rhs_tile, rank)
+        if coef is not None:
+            # PHASE_FIO1D_SERIES: coef = (a, b), c(x) = sum_m a[m] cos(2 pi m x) + b[m] sin(2 pi m x)
+            a, b = (np.ascontiguousarray(v, dtype=np.float64).ravel() for v in coef)
+            if a.shape != b.shape:
+                raise ValueError("coef: a and b must have the same length")
+            self._coef = np.concatenate([a, b])
+            opt.phase_coef = self._coef.ctypes.data
+            opt.phase_ncoef = a.size
         xa = None
         if x is not None:
             xa = np.ascontiguousarray(x, dtype=np.float64)

@@ -74,10 +74,18 @@ struct PersistArgs {
 template <typename Real>
 struct PersistTraits {
     static constexpr int kThreads = 256;
-    // 2 CTAs per SM: the item body holds both level kinds and the epilogues,
-    // and spills under the 80-register budget of 3 CTAs per SM
-    static constexpr int kMinBlocks = sizeof(Real) == 4 ? 2 : 1;
+    // FP32: 4 CTAs per SM (64 registers); the two level kinds are separate
+    // functions (persist_item), so the kernel holds one kind's registers at a time
+    static constexpr int kMinBlocks = sizeof(Real) == 4 ? 4 : 1;
 };
+
+// One work item of one level kind, not inlined into the persistent loop: the
+// loop keeps only its own state live across the call.
+template <typename Real, int RP, bool ADJ, int KIND>
+__device__ __noinline__ void persist_item(const FusedDesc& d, int64_t blk, unsigned char* smraw)
+{
+    fused_body<Real, RP, ADJ, KIND, 32, true>(c_eo<Real, RP>, d, blk, smraw);
+}
 
 // Each CTA takes items from the shared counter in order (the next item is
 // claimed while the current one runs, hiding the atomic's latency).  An item
@@ -145,9 +153,9 @@ __global__ void __launch_bounds__(PersistTraits<Real>::kThreads, PersistTraits<R
         const int64_t blk = item - cur_lo;
         // every descriptor of the persistent form uses 32-column tiles
         if (d.kind == 0)
-            fused_body<Real, RP, ADJ, 0, 32, true>(c_eo<Real, RP>, d, blk, smraw);
+            persist_item<Real, RP, ADJ, 0>(d, blk, smraw);
         else
-            fused_body<Real, RP, ADJ, 1, 32, true>(c_eo<Real, RP>, d, blk, smraw);
+            persist_item<Real, RP, ADJ, 1>(d, blk, smraw);
         if (threadIdx.x == 0) ++pending;
         __syncthreads();   // shared memory and the claimed item change hands
     }

@@ -112,6 +112,179 @@ __global__ void kx_level_adj(const cd* blk, const cd* out, cd* in, int L, int l,
     in[e] = acc;
 }
 
+// Warp-per-pair forms of the two level kernels above (same arithmetic, same
+// outputs).  A level streams its blocks once (2 ro ri entries per pair) and
+// reads two contiguous input pairs, so it should run at the HBM rate; one
+// thread per output entry instead issues ri dependent loads per block row
+// and stays latency-bound.  Here one warp owns one output pair: it copies the
+// pair's blocks and, per tile of kXCT columns, its inputs into a shared-memory
+// slice with asynchronous copies (every lane several in flight), then each
+// lane computes outputs (t, col) of the tile from shared memory (block rows
+// read as broadcasts, inputs by consecutive columns) and stores them
+// coalesced.  Ranks up to kXRmax.
+constexpr int kXWarps = 8;     // warps (pairs) per CTA
+constexpr int kXCT = 8;        // columns per tile
+constexpr int kXRmax = 16;
+
+__device__ __forceinline__ void xcp(float2* d, const float2* s)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(d)), "l"(s)
+                 : "memory");
+}
+__device__ __forceinline__ void xcp(double2* d, const double2* s)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(d)), "l"(s)
+                 : "memory");
+}
+__device__ __forceinline__ void xcp_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// shared memory per warp: the two blocks (or the two gathered blocks of the
+// adjoint) and one tile of two input pairs
+template <typename cd>
+constexpr size_t xslice_elems() { return 2 * kXRmax * kXRmax + 2 * kXRmax * kXCT; }
+
+template <typename cd>
+__global__ void __launch_bounds__(kXWarps * 32) kx_level_w(const cd* blk, const cd* in, cd* out, int L, int l, int ro,
+                                                            int ri, int nc, int64_t N)
+{
+    extern __shared__ __align__(16) unsigned char xsm[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t p = (int64_t)blockIdx.x * kXWarps + w;
+    if (p >= N) return;
+    cd* sb = reinterpret_cast<cd*>(xsm) + w * xslice_elems<cd>();   // [c][t][s]
+    cd* sx = sb + 2 * kXRmax * kXRmax;                                // [c][s][col of tile]
+    const int64_t nj = 1LL << (L - l);
+    const int64_t i = p >> (L - l), j = p & (nj - 1);
+    const int64_t q0 = (i >> 1) * (2 * nj) + 2 * j;
+    const cd* bp = blk + p * 2 * ro * ri;
+    const int nb = 2 * ro * ri;
+    for (int e = lane; e < nb; e += 32) xcp(sb + e, bp + e);
+    for (int c0 = 0; c0 < nc; c0 += kXCT) {
+        const int nt = min(kXCT, nc - c0);
+        const cd* xin = in + q0 * ri * nc + c0;
+        for (int e = lane; e < 2 * ri * nt; e += 32) {
+            const int cs = e / nt, col = e - cs * nt;   // cs = c ri + s
+            xcp(sx + cs * kXCT + col, xin + (int64_t)cs * nc + col);
+        }
+        xcp_wait();
+        __syncwarp();
+        for (int o = lane; o < ro * nt; o += 32) {
+            const int t = o / nt, col = o - t * nt;
+            cd acc = cmk<cd>(0, 0);
+            for (int c = 0; c < 2; ++c) {
+                const cd* row = sb + (c * ro + t) * ri;
+                const cd* v = sx + c * ri * kXCT + col;
+#pragma unroll 4
+                for (int s2 = 0; s2 < ri; ++s2) cadd(acc, cmul(row[s2], v[s2 * kXCT]));
+            }
+            out[(p * ro + t) * nc + c0 + col] = acc;
+        }
+        __syncwarp();   // the tile's inputs are read before the next tile's copies
+    }
+}
+
+// Persistent, double-buffered form of kx_level_w for nc <= kXPipeCols: every
+// warp walks pairs w, w + W, w + 2W, ... (W = warps in the grid) with two
+// shared-memory slices sized to the level's ranks (2 ro ri + 2 ri nc
+// elements), and issues the copies of its next pair before computing the
+// current one, so copies stay in flight through the arithmetic.
+constexpr int kXPipeCols = 16;
+
+template <typename cd>
+__global__ void __launch_bounds__(kXWarps * 32) kx_level_wp(const cd* blk, const cd* in, cd* out, int L, int l, int ro,
+                                                             int ri, int nc, int64_t N, int slice)
+{
+    extern __shared__ __align__(16) unsigned char xsm[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t W = (int64_t)gridDim.x * kXWarps;
+    cd* s0 = reinterpret_cast<cd*>(xsm) + (size_t)w * 2 * slice;
+    cd* s1 = s0 + slice;
+    const int nb = 2 * ro * ri, nx = 2 * ri * nc;
+    const int64_t nj = 1LL << (L - l);
+    auto issue = [&](int64_t p, cd* sl) {
+        const int64_t i = p >> (L - l), j = p & (nj - 1);
+        const int64_t q0 = (i >> 1) * (2 * nj) + 2 * j;
+        const cd* bp = blk + p * nb;
+        const cd* xp = in + q0 * ri * nc;          // the two input pairs are contiguous
+        for (int e = lane; e < nb; e += 32) xcp(sl + e, bp + e);
+        for (int e = lane; e < nx; e += 32) xcp(sl + nb + e, xp + e);
+    };
+    int64_t p = (int64_t)blockIdx.x * kXWarps + w;
+    if (p < N) issue(p, s0);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    for (int it = 0; p < N; ++it, p += W) {
+        cd* cur = (it & 1) ? s1 : s0;
+        if (p + W < N) issue(p + W, (it & 1) ? s0 : s1);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        __syncwarp();
+        const cd* sx = cur + nb;                   // [c][s][col]
+        for (int o = lane; o < ro * nc; o += 32) {
+            const int t = o / nc, col = o - t * nc;
+            cd acc = cmk<cd>(0, 0);
+            for (int c = 0; c < 2; ++c) {
+                const cd* row = cur + (c * ro + t) * ri;
+                const cd* v = sx + c * ri * nc + col;
+#pragma unroll 4
+                for (int s2 = 0; s2 < ri; ++s2) cadd(acc, cmul(row[s2], v[s2 * nc]));
+            }
+            out[(p * ro + t) * nc + col] = acc;
+        }
+        __syncwarp();   // every lane is done with this slice before it is refilled
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// adjoint of level l, warp per input pair q = (i', C) of level l-1: it
+// gathers from the output pairs (2i'+a, C/2), a = 0, 1, through block c = C&1
+// of each, conjugate-transposed
+template <typename cd>
+__global__ void __launch_bounds__(kXWarps * 32) kx_level_adj_w(const cd* blk, const cd* out, cd* in, int L, int l,
+                                                                int ro, int ri, int nc, int64_t N)
+{
+    extern __shared__ __align__(16) unsigned char xsm[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t q = (int64_t)blockIdx.x * kXWarps + w;
+    if (q >= N) return;
+    cd* sb = reinterpret_cast<cd*>(xsm) + w * xslice_elems<cd>();   // [a][t][s]
+    cd* sy = sb + 2 * kXRmax * kXRmax;                                // [a][t][col of tile]
+    const int64_t nC = 1LL << (L - l + 1), nj = nC >> 1;
+    const int64_t ip = q >> (L - l + 1), C = q & (nC - 1);
+    const int64_t j = C >> 1;
+    const int c = (int)(C & 1);
+    const int nb = ro * ri;
+    for (int a = 0; a < 2; ++a) {
+        const int64_t pa = (2 * ip + a) * nj + j;
+        const cd* bp = blk + (pa * 2 + c) * nb;
+        for (int e = lane; e < nb; e += 32) xcp(sb + a * nb + e, bp + e);
+    }
+    for (int c0 = 0; c0 < nc; c0 += kXCT) {
+        const int nt = min(kXCT, nc - c0);
+        for (int a = 0; a < 2; ++a) {
+            const int64_t pa = (2 * ip + a) * nj + j;
+            const cd* yin = out + pa * ro * nc + c0;
+            for (int e = lane; e < ro * nt; e += 32) {
+                const int t = e / nt, col = e - t * nt;
+                xcp(sy + (a * ro + t) * kXCT + col, yin + (int64_t)t * nc + col);
+            }
+        }
+        xcp_wait();
+        __syncwarp();
+        for (int o = lane; o < ri * nt; o += 32) {
+            const int s2 = o / nt, col = o - s2 * nt;
+            cd acc = cmk<cd>(0, 0);
+            for (int a = 0; a < 2; ++a) {
+                const cd* bcol = sb + a * nb + s2;
+                const cd* v = sy + a * ro * kXCT + col;
+#pragma unroll 4
+                for (int t = 0; t < ro; ++t) cadd(acc, cmulc(bcol[t * ri], v[t * kXCT]));
+            }
+            in[(q * ri + s2) * nc + c0 + col] = acc;
+        }
+        __syncwarp();
+    }
+}
+
 // switch at level h: out_p = M~_p in_p (eq. switchlocM), M~_p of rows x cols
 // (rank after x rank before the switch), or its adjoint
 template <typename cd>
@@ -165,6 +338,23 @@ __global__ void kx_term_adj(const cd* U, const int32_t* off, const int32_t* perm
 
 static inline unsigned nb(int64_t n) { return (unsigned)((n + 255) / 256); }
 
+// the warp-per-pair level kernels use kXWarps slices of shared memory (96 KB
+// for complex128): raise their dynamic shared-memory limit once per device
+template <typename cd>
+static size_t xlevel_smem()
+{
+    static bool done[64] = {false};
+    const size_t bytes = kXWarps * xslice_elems<cd>() * sizeof(cd);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !done[dev]) {
+        cudaFuncSetAttribute(kx_level_w<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        cudaFuncSetAttribute(kx_level_adj_w<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (dev >= 0 && dev < 64) done[dev] = true;
+    }
+    return bytes;
+}
+
 // rank of Lambda^l before the switch (H side, l <= h) and after it (G side,
 // l >= h)
 static inline int rank_h(const ibf_plan* p, int l)
@@ -180,6 +370,34 @@ static inline int rank_out(const ibf_plan* p, int l) { return l <= p->h ? rank_h
 static inline int rank_in(const ibf_plan* p, int l) { return l <= p->h ? rank_h(p, l - 1) : rank_g(p, l - 1); }
 
 int explicit_launches(const ibf_plan* p) { return p->L + 3; }
+
+// persistent warp-per-pair level: as many CTAs as are resident at once;
+// false (nothing launched) if its slices do not fit one CTA's shared memory
+template <typename cd>
+static bool launch_level_wp(const cd* blk, const cd* in, cd* out, int L, int l, int ro, int ri, int nc, int64_t N,
+                            cudaStream_t st)
+{
+    const int slice = (2 * ro * ri + 2 * ri * nc + 1) & ~1;   // even: 16-byte aligned slices for complex64
+    const size_t smem = (size_t)kXWarps * 2 * slice * sizeof(cd);
+    int dev = 0, nsm = 0, occ = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (smem > (size_t)optin) return false;
+    static bool done[64] = {false};
+    if (dev < 0 || dev >= 64 || !done[dev]) {
+        cudaFuncSetAttribute(kx_level_wp<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        if (dev >= 0 && dev < 64) done[dev] = true;
+    }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kx_level_wp<cd>, kXWarps * 32, smem) != cudaSuccess ||
+        occ < 1) {
+        cudaGetLastError();
+        occ = 1;
+    }
+    const int64_t blocks = std::min<int64_t>((N + kXWarps - 1) / kXWarps, (int64_t)nsm * occ);
+    kx_level_wp<cd><<<(unsigned)blocks, kXWarps * 32, smem, st>>>(blk, in, out, L, l, ro, ri, nc, N, slice);
+    return true;
+}
 
 template <typename cd>
 static int explicit_apply_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cudaStream_t st)
@@ -198,7 +416,12 @@ static int explicit_apply_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cud
         prof_mark(p, st, IBF_K_EXPLICIT_INIT);
         for (int l = 1; l <= L; ++l) {
             const int ro = rank_out(p, l), ri = rank_in(p, l);
-            kx_level<<<nb(N * ro * nc), 256, 0, st>>>((const cd*)p->eblk[l], a, b, L, l, ro, ri, nc, N);
+            if (nc <= kXPipeCols && launch_level_wp<cd>((const cd*)p->eblk[l], a, b, L, l, ro, ri, nc, N, st)) {
+            } else if (ro <= kXRmax && ri <= kXRmax)
+                kx_level_w<cd><<<(unsigned)((N + kXWarps - 1) / kXWarps), kXWarps * 32, xlevel_smem<cd>(), st>>>(
+                    (const cd*)p->eblk[l], a, b, L, l, ro, ri, nc, N);
+            else
+                kx_level<<<nb(N * ro * nc), 256, 0, st>>>((const cd*)p->eblk[l], a, b, L, l, ro, ri, nc, N);
             prof_mark(p, st, IBF_K_EXPLICIT_LEVEL);
             std::swap(a, b);
             if (l == h) {
@@ -236,7 +459,11 @@ static int explicit_adjoint_t(ibf_plan* p, const void* yv, void* gv, int nrhs, c
                 std::swap(a, b);
             }
             const int ro = rank_out(p, l), ri = rank_in(p, l);
-            kx_level_adj<<<nb(N * ri * nc), 256, 0, st>>>((const cd*)p->eblk[l], a, b, L, l, ro, ri, nc, N);
+            if (ro <= kXRmax && ri <= kXRmax)
+                kx_level_adj_w<cd><<<(unsigned)((N + kXWarps - 1) / kXWarps), kXWarps * 32, xlevel_smem<cd>(), st>>>(
+                    (const cd*)p->eblk[l], a, b, L, l, ro, ri, nc, N);
+            else
+                kx_level_adj<<<nb(N * ri * nc), 256, 0, st>>>((const cd*)p->eblk[l], a, b, L, l, ro, ri, nc, N);
             prof_mark(p, st, IBF_K_EXPLICIT_LEVEL);
             std::swap(a, b);
         }

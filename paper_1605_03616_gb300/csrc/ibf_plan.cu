@@ -42,6 +42,8 @@ struct Geo {
     int64_t N;
     int L, r, phase;
     double z[kMaxR];
+    int nco;                       // IBF_PHASE_FIO1D_SERIES: terms of c(x)
+    double ca[kMaxCoef], cb[kMaxCoef];
 };
 
 __device__ __forceinline__ double pow2(int l) { return (double)(1LL << l); }
@@ -50,12 +52,23 @@ __device__ __forceinline__ double xw(int l) { return 1.0 / pow2(l); }
 __device__ __forceinline__ double ww(int64_t N, int l) { return (double)N / pow2(l); }
 __device__ __forceinline__ double wc(int64_t N, int l, int64_t j) { return -0.5 * (double)N + ((double)j + 0.5) * ww(N, l); }
 
-// Phase functions (Assumption 1.1; Sec. 6.1, 6.2 and a separable test phase).
-__device__ __forceinline__ double phi(int ph, double x, double xi)
+// Phase functions (Assumption 1.1; Sec. 6.1, 6.2, the 1D FIO with a series
+// coefficient, and a separable test phase).
+__device__ __forceinline__ double phi(const Geo& G, double x, double xi)
 {
+    const int ph = G.phase;
     if (ph == IBF_PHASE_NUFFT) return x * xi;
     if (ph == IBF_PHASE_FIO1D) {
         double c = (2.0 + sin(2.0 * 3.141592653589793 * x)) / 8.0;
+        return x * xi + c * fabs(xi);
+    }
+    if (ph == IBF_PHASE_FIO1D_SERIES) {
+        // c(x) = sum_m a_m cos(2 pi m x) + b_m sin(2 pi m x), summed in order of m
+        double c = 0.0;
+        for (int m = 0; m < G.nco; ++m) {
+            const double arg = 2.0 * 3.141592653589793 * (double)m * x;
+            c += G.ca[m] * cos(arg) + G.cb[m] * sin(arg);
+        }
         return x * xi + c * fabs(xi);
     }
     // IBF_PHASE_SEPARABLE
@@ -108,7 +121,7 @@ __global__ void kE_V(const Geo G, double2* V)
     int64_t k = e / G.r;
     double xi = (double)k - 0.5 * (double)G.N;
     double cA = xc(0, 0), wB = ww(G.N, G.L), cB = wc(G.N, G.L, k);
-    double2 v = cmul(e2pi(-phi(G.phase, cA, gp(cB, wB, G, t))), e2pi(phi(G.phase, cA, xi)));
+    double2 v = cmul(e2pi(-phi(G, cA, gp(cB, wB, G, t))), e2pi(phi(G, cA, xi)));
     V[e] = cscale(lag(G, t, (xi - cB) / wB), v);
 }
 
@@ -131,13 +144,13 @@ __global__ void kE_blk(const Geo G, int l, int h, double2* B)
         double cB = wc(G.N, G.L - l, j), wB = ww(G.N, G.L - l);
         double gCs = gp(cC, wC, G, s);
         v = cscale(lag(G, t, (gCs - cB) / wB),
-                   cmul(e2pi(-phi(G.phase, cA, gp(cB, wB, G, t))), e2pi(phi(G.phase, cA, gCs))));
+                   cmul(e2pi(-phi(G, cA, gp(cB, wB, G, t))), e2pi(phi(G, cA, gCs))));
     } else {
         double cA = xc(l, i), wA = xw(l);
         double cP = xc(l - 1, i / 2), wP = xw(l - 1);
         double gAt = gp(cA, wA, G, t);
         v = cscale(lag(G, s, (gAt - cP) / wP),
-                   cmul(e2pi(phi(G.phase, gAt, cC)), e2pi(-phi(G.phase, gp(cP, wP, G, s), cC))));
+                   cmul(e2pi(phi(G, gAt, cC)), e2pi(-phi(G, gp(cP, wP, G, s), cC))));
     }
     B[e] = v;
 }
@@ -153,7 +166,7 @@ __global__ void kE_M(const Geo G, int h, double2* M)
     int64_t p = e / (r * r);
     int64_t i = p >> (G.L - h), j = p & ((1LL << (G.L - h)) - 1);
     double cA = xc(h, i), wA = xw(h), cB = wc(G.N, G.L - h, j), wB = ww(G.N, G.L - h);
-    M[e] = e2pi(phi(G.phase, gp(cA, wA, G, t), gp(cB, wB, G, s)));
+    M[e] = e2pi(phi(G, gp(cA, wA, G, t), gp(cB, wB, G, s)));
 }
 
 // U^L rows for the sorted points (eq. PIBFbf3), B = root of T_Omega
@@ -165,7 +178,7 @@ __global__ void kE_U(const Geo G, const double* x, const int32_t* leaf, int64_t 
     int64_t n = e / G.r;
     double xn = x[n];
     double cB = wc(G.N, 0, 0), wA = xw(G.L), cA = xc(G.L, leaf[n]);
-    double2 v = cmul(e2pi(phi(G.phase, xn, cB)), e2pi(-phi(G.phase, gp(cA, wA, G, t), cB)));
+    double2 v = cmul(e2pi(phi(G, xn, cB)), e2pi(-phi(G, gp(cA, wA, G, t), cB)));
     U[e] = cscale(lag(G, t, (xn - cA) / wA), v);
 }
 
@@ -186,7 +199,7 @@ __global__ void kS_V(const Geo G, C* V)
     int64_t k = e / G.r;
     double xi = (double)k - 0.5 * (double)G.N;
     double cA = xc(0, 0), wB = ww(G.N, G.L), cB = wc(G.N, G.L, k);
-    store(V + e, cscale(lag(G, t, (xi - cB) / wB), e2pi(phi(G.phase, cA, xi))));
+    store(V + e, cscale(lag(G, t, (xi - cB) / wB), e2pi(phi(G, cA, xi))));
 }
 
 // H level l (1..h): D[i][C][s], i < 2^l, C < 2^(L-l+1)
@@ -201,7 +214,7 @@ __global__ void kS_Q(const Geo G, int l, C* D)
     int64_t q = e / r;
     int64_t i = q >> cb, Cc = q & ((1LL << cb) - 1);
     double g = gp(wc(G.N, cb, Cc), ww(G.N, cb), G, s);
-    double d = phi(G.phase, xc(l, i), g) - phi(G.phase, xc(l - 1, i / 2), g);
+    double d = phi(G, xc(l, i), g) - phi(G, xc(l - 1, i / 2), g);
     store(D + e, e2pi(d));
 }
 
@@ -217,7 +230,7 @@ __global__ void kS_L(const Geo G, int l, C* D)
     int64_t q = e / r;
     int64_t i = q >> cb, Cc = q & ((1LL << cb) - 1);
     double g = gp(xc(l, i), xw(l), G, t);
-    double d = phi(G.phase, g, wc(G.N, cb, Cc)) - phi(G.phase, g, wc(G.N, cb - 1, Cc / 2));
+    double d = phi(G, g, wc(G.N, cb, Cc)) - phi(G, g, wc(G.N, cb - 1, Cc / 2));
     store(D + e, e2pi(d));
 }
 
@@ -234,7 +247,7 @@ __global__ void kS_M(const Geo G, int h, C* M)
     int64_t i = p >> (G.L - h), j = p & ((1LL << (G.L - h)) - 1);
     double cA = xc(h, i), wA = xw(h), cB = wc(G.N, G.L - h, j), wB = ww(G.N, G.L - h);
     double gA = gp(cA, wA, G, t), gB = gp(cB, wB, G, s);
-    double d = phi(G.phase, gA, gB) - phi(G.phase, cA, gB) - phi(G.phase, gA, cB);
+    double d = phi(G, gA, gB) - phi(G, cA, gB) - phi(G, gA, cB);
     store(M + e, e2pi(d));
 }
 
@@ -247,7 +260,7 @@ __global__ void kS_U(const Geo G, const double* x, const int32_t* leaf, int64_t 
     int64_t n = e / G.r;
     double xn = x[n];
     double cA = xc(G.L, leaf[n]), wA = xw(G.L);
-    store(U + e, cscale(lag(G, t, (xn - cA) / wA), e2pi(phi(G.phase, xn, wc(G.N, 0, 0)))));
+    store(U + e, cscale(lag(G, t, (xn - cA) / wA), e2pi(phi(G, xn, wc(G.N, 0, 0)))));
 }
 
 // ---------------------------------------------------------------------------
@@ -258,6 +271,11 @@ static Geo make_geo(const ibf_plan* p)
     G.L = p->L;
     G.r = p->r;
     G.phase = p->phase_id;
+    G.nco = (int)p->coef.size() / 2;
+    for (int m = 0; m < kMaxCoef; ++m) {
+        G.ca[m] = m < G.nco ? p->coef[m] : 0.0;
+        G.cb[m] = m < G.nco ? p->coef[G.nco + m] : 0.0;
+    }
     for (int t = 0; t < kMaxR; ++t) G.z[t] = t < p->r ? p->z[t] : 0.0;
     return G;
 }
@@ -479,8 +497,17 @@ extern "C" int ibf_plan_create_ex(int phase_id, int d, int64_t N, int r, int dty
     *out = nullptr;
     if (d == 2) return create_2d(phase_id, N, r, dtype, x, opt, out);
     if (d != 1) return set_error(IBF_ERR_INVALID, "d must be 1 or 2");
-    if (phase_id != IBF_PHASE_NUFFT && phase_id != IBF_PHASE_FIO1D && phase_id != IBF_PHASE_SEPARABLE)
+    if (phase_id != IBF_PHASE_NUFFT && phase_id != IBF_PHASE_FIO1D && phase_id != IBF_PHASE_SEPARABLE &&
+        phase_id != IBF_PHASE_FIO1D_SERIES)
         return set_error(IBF_ERR_INVALID, "unknown 1D phase id " + std::to_string(phase_id));
+    std::vector<double> coef;
+    if (phase_id == IBF_PHASE_FIO1D_SERIES) {
+        if (!opt || !opt->phase_coef || opt->phase_ncoef < 1 || opt->phase_ncoef > kMaxCoef)
+            return set_error(IBF_ERR_INVALID, "IBF_PHASE_FIO1D_SERIES needs phase_coef and 1 <= phase_ncoef <= 16");
+        coef.assign(opt->phase_coef, opt->phase_coef + 2 * opt->phase_ncoef);
+        for (double v : coef)
+            if (!std::isfinite(v)) return set_error(IBF_ERR_INVALID, "phase_coef must be finite");
+    }
     if (N < 4 || N > (1LL << 24) || (N & (N - 1)))
         return set_error(IBF_ERR_INVALID, "N must be a power of two in [4, 2^24]");
     if (r < 3 || r > kMaxR) return set_error(IBF_ERR_INVALID, "r must be in [3, 16]");
@@ -540,6 +567,7 @@ extern "C" int ibf_plan_create_ex(int phase_id, int d, int64_t N, int r, int dty
 
     ibf_plan* p = new ibf_plan();
     p->phase_id = phase_id;
+    p->coef = coef;
     p->d = d;
     p->r = r;
     p->dtype = dtype;

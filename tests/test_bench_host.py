@@ -108,3 +108,17 @@ def test_fused_schedule_and_dominant_roofline():
     assert abs(d["avg_ms"] - 3.5) < 1e-12
     assert d["flops"] == bench.structured_flops(3, 9, 1 << 20, 64, None, "switch", False)
     assert abs(d["alu_frac"] - d["flops"] / 3.5e-3 / 1e12 / 80.0) < 1e-12
+
+
+def test_apply_flops_is_the_sum_over_launches():
+    """The whole-apply flop count used for the batch roofline equals the sum of
+    the per-launch counts over any fusion depth's schedule."""
+    import bench
+    for L, k, nc in ((20, 4, 64), (11, 5, 3), (16, 3, 17)):
+        h, N = L // 2, 1 << L
+        tot = 0
+        for lo, hi, kd in bench.fused_schedule(L, h, k):
+            pro = "V" if lo == 0 else None
+            epi = "U" if hi == L else ("switch" if hi == h else None)
+            tot += bench.structured_flops(hi - lo, 9, N, nc, pro, epi, kd == "G")
+        assert tot == bench.apply_flops(L, 9, N, nc)

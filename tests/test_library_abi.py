@@ -107,3 +107,29 @@ def test_tensor_core_dtype_validated_without_gpu(lib):
     assert create(ibf.FORM_STRUCTURED, ibf.C64_TF32X3, d=2, phase=ibf.PHASE_FIO2D, N=64 * 64, r=7) == 4
     assert create(ibf.FORM_STRUCTURED, ibf.C64_BF16X3) == 4
     assert create(ibf.FORM_STRUCTURED, 4) == 1                       # unknown dtype
+
+
+def test_series_phase_validated_without_gpu(lib):
+    """IBF_PHASE_FIO1D_SERIES needs 1..16 finite coefficients and is 1D only;
+    every refusal comes before a CUDA call."""
+    import numpy as np
+    import paper_1605_03616_gb300 as ibf
+
+    def create(coef, ncoef, d=1, N=1024, r=9):
+        o = ibf.Options()
+        o.form = ibf.FORM_STRUCTURED
+        if coef is not None:
+            o.phase_coef = coef.ctypes.data
+        o.phase_ncoef = ncoef
+        out = ctypes.c_void_p()
+        return lib.ibf_plan_create_ex(ibf.PHASE_FIO1D_SERIES, d, N, r, ibf.C64_FP32, None, ctypes.byref(o),
+                                      ctypes.byref(out))
+
+    ok = np.array([0.25, 0.0, 0.0, 0.125])
+    assert create(None, 2) == 1
+    assert create(ok, 0) == 1
+    assert create(ok, 17) == 1
+    assert create(np.array([0.25, np.nan, 0.0, 0.1]), 2) == 1
+    assert create(ok, 2, d=2, N=64 * 64, r=7) == 1          # no 2D form
+    out = ctypes.c_void_p()
+    assert lib.ibf_plan_create(ibf.PHASE_FIO1D_SERIES, 1, 1024, 9, ibf.C64_FP32, ctypes.byref(out)) == 1

@@ -48,18 +48,26 @@ def test_direct_2d_equals_dft_closed_form():
 
 
 # ------------------------------------------------------------- phase shapes
+# the series of tests/golden/phase_values.txt, kind 4
+SERIES_GOLDEN_A, SERIES_GOLDEN_B = [0.25, 0.0, 0.125], [0.0, 0.125, 0.0]
+# a smooth positive coefficient with five terms (|c - 1/4| <= 0.11)
+SERIES_SMOOTH_A = [0.25, 0.04, -0.02, 0.01, 0.005]
+SERIES_SMOOTH_B = [0.0, 0.03, 0.015, -0.01, 0.004]
+
+
 def test_phase_values_match_hand_computed():
     """The phases of Sec. 6 at points where they are exact rationals
     (tests/golden/phase_values.txt, each value worked out by hand): c(x) of
     the 1D FIO and c1, c2 of the 2D FIO at quarter and twelfth points, where
     sin and cos take the values 0, +-1/2, +-1.  A phase-shifted coefficient
     (cos for sin) or c1 and c2 exchanged moves several rows by >= 1."""
-    kinds = {0: O.PHASE_NUFFT, 1: O.PHASE_FIO1D, 2: O.PHASE_FIO2D, 3: O.PHASE_FIO2D_32}
+    kinds = {0: O.PHASE_NUFFT, 1: O.PHASE_FIO1D, 2: O.PHASE_FIO2D, 3: O.PHASE_FIO2D_32, 4: O.PHASE_FIO1D_SERIES}
+    O.set_series(SERIES_GOLDEN_A, SERIES_GOLDEN_B)
     rows = read_golden("phase_values.txt")
-    assert len(rows) >= 20
+    assert len(rows) >= 26
     for kind, x1, x2, k1, k2, want in rows:
         ph = kinds[int(kind)]
-        got = O.phi_1d(ph, x1, k1) if int(kind) <= 1 else O.phi_2d(ph, x1, x2, k1, k2)
+        got = O.phi_1d(ph, x1, k1) if int(kind) in (0, 1, 4) else O.phi_2d(ph, x1, x2, k1, k2)
         assert abs(got - want) <= 1e-12 * max(1.0, abs(want)), (kind, x1, x2, k1, k2, got, want)
 
 
@@ -276,3 +284,34 @@ def test_adjoint_matches_dense_conjugate_transpose():
     Ks = O.direct_1d(O.PHASE_SEPARABLE, x, W.omega_1d(N), np.eye(N))
     gs = O.ibf_adjoint_1d(O.PHASE_SEPARABLE, N, r, x, y)
     assert O.rel_l2(gs, Ks.conj().T @ y) < 1e-12
+
+
+# ------------------------------------------------- the series-coefficient FIO
+def test_series_phase_reduces_to_sec62_fio():
+    """With c(x) = 1/4 + sin(2 pi x)/8 the series phase is Sec. 6.2's: the
+    direct sums and the IBFs agree to rounding."""
+    O.set_series([0.25, 0.0], [0.0, 0.125])
+    N, r = 256, 9
+    x = W.uniform_x(N)
+    g = W.complex_normal((N, 2), W.rng(40))
+    a = O.ibf_apply_1d(O.PHASE_FIO1D_SERIES, N, r, x, g)
+    b = O.ibf_apply_1d(O.PHASE_FIO1D, N, r, x, g)
+    assert O.rel_l2(a, b) < 1e-13
+    xi = W.omega_1d(N)
+    assert O.rel_l2(O.direct_1d(O.PHASE_FIO1D_SERIES, x, xi, g), O.direct_1d(O.PHASE_FIO1D, x, xi, g)) < 1e-13
+
+
+def test_series_phase_ibf_converges_in_r():
+    """A five-term smooth coefficient: the IBF error against the direct sum
+    falls monotonically in r, to the FIO's level at r = 9, and stays flat in N."""
+    O.set_series(SERIES_SMOOTH_A, SERIES_SMOOTH_B)
+    errs = {}
+    for N in (256, 1024):
+        x = W.uniform_x(N)
+        g = W.complex_normal(N, W.rng(41))
+        ref = O.direct_1d(O.PHASE_FIO1D_SERIES, x, W.omega_1d(N), g)
+        errs[N] = [O.rel_l2(O.ibf_apply_1d(O.PHASE_FIO1D_SERIES, N, r, x, g), ref) for r in (5, 7, 9, 11)]
+    for N, e in errs.items():
+        assert all(e[i + 1] < e[i] for i in range(len(e) - 1)), (N, e)
+        assert e[2] < 1e-4, (N, e)
+    assert max(errs[1024][2], errs[256][2]) < 5 * min(errs[1024][2], errs[256][2])

@@ -2,8 +2,9 @@
 mistake in a copy of the oracle -- the C source recompiled with gcc, or a
 Python module re-executed from its edited source -- runs one of the real pin
 tests against the copy, and requires that pin to fail.  Mistakes: a sign of
-the phase factor, a phase-shifted 1D FIO coefficient, the 2D FIO coefficients
-exchanged, the Chebyshev grid, a dropped Lagrange factor, the child
+the phase factor, a phase-shifted 1D FIO coefficient, the sine terms of the
+series coefficient dropped, the 2D FIO coefficients exchanged, the Chebyshev
+grid, a dropped Lagrange factor, the child
 centre or a phase sign of a butterfly level, a transposed switch block, a
 wrong box width in U^L, a dropped phase factor in V^0, a skipped corona box
 in 2D, a dropped conjugate in an adjoint level, swapped amplitude factors, a missing conjugate in the amplitude
@@ -63,6 +64,9 @@ C_MUTATIONS = [
      lambda: T2.test_separable_2d_box_and_mibf_exact(32, 7)),
     ("1D FIO coefficient phase-shifted (cos for sin)",
      "double c = (2.0 + sin(2.0 * M_PI * x)) / 8.0;", "double c = (2.0 + cos(2.0 * M_PI * x)) / 8.0;",
+     T.test_phase_values_match_hand_computed),
+    ("series coefficient without its sine terms",
+     "c += orc_ca[m] * cos(arg) + orc_cb[m] * sin(arg);", "c += orc_ca[m] * cos(arg);",
      T.test_phase_values_match_hand_computed),
     ("2D FIO coefficients c1 and c2 exchanged",
      "double c1 = (2.0 + sin(2.0 * M_PI * x1) * sin(2.0 * M_PI * x2)) / den;\n"
