@@ -245,19 +245,22 @@ def run_optimal(ibf, torch, N=1 << 16, nrhs=8, reps=3, variants=None):
     g32 = g.to(torch.complex64)
     out, ref = [], None
     names = {ibf.FORM_EXPLICIT: "preliminary", ibf.FORM_OPTIMAL: "optimal (sweep-out)",
-             ibf.FORM_OPTIMAL_IN: "optimal (sweep-out + sweep-in)"}
+             ibf.FORM_OPTIMAL_IN: "optimal (sweep-out + sweep-in)",
+             ibf.FORM_STRUCTURED: "preliminary, structured (the fast FP32 form)"}
     C128, C64 = ibf.C128, ibf.C64_FP32
     variants = variants or [(12, ibf.FORM_EXPLICIT, 0, C128), (9, ibf.FORM_EXPLICIT, 0, C128),
                             (12, ibf.FORM_OPTIMAL, 9, C128), (12, ibf.FORM_OPTIMAL_IN, 9, C128),
                             (12, ibf.FORM_OPTIMAL, 7, C128), (12, ibf.FORM_OPTIMAL_IN, 7, C128),
                             (9, ibf.FORM_OPTIMAL, 7, C128),
                             (12, ibf.FORM_EXPLICIT, 0, C64), (12, ibf.FORM_OPTIMAL_IN, 9, C64),
-                            (12, ibf.FORM_OPTIMAL_IN, 7, C64)]
+                            (12, ibf.FORM_OPTIMAL_IN, 7, C64), (9, ibf.FORM_STRUCTURED, 0, C64)]
     for r, form, r0, dt in variants:
         gin = g if dt == C128 else g32
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         p = ibf.Plan(ibf.PHASE_FIO1D, N, r, dt, form=form, rank=r0, max_nrhs=nrhs)
+        if form == ibf.FORM_STRUCTURED:
+            p.autotune(nrhs)
         torch.cuda.synchronize()
         tc = (time.perf_counter() - t0) * 1e3
         u = p.apply(gin)
