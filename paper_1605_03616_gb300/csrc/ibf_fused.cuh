@@ -288,9 +288,9 @@ __device__ __forceinline__ void fused_levels(const FusedConsts<Real, RP>& C, int
                 if (c < ncol) {
                     const int p0 = ((u >> bit) << (bit + 1)) | (u & ((1 << bit) - 1));
                     const int p1 = p0 | (1 << bit);
-                    const cx* x0p = sm + (size_t)p0 * PS + c;
-                    const cx* x1p = sm + (size_t)p1 * PS + c;
-                    const cx* du = dl + (size_t)u * DS;
+                    const cx* x0p = sm + (p0 * PS + c);
+                    const cx* x1p = sm + (p1 * PS + c);
+                    const cx* du = dl + u * DS;
                     // output a uses D_{a,q} (forward H) or conj(D_{q,a}) (adjoint G)
                     const cx* d00 = du + (ADJ ? 0 : 0) * RP;
                     const cx* d01 = du + (ADJ ? 2 : 1) * RP;
@@ -323,8 +323,8 @@ __device__ __forceinline__ void fused_levels(const FusedConsts<Real, RP>& C, int
                             wo1[t] = p2fma(qm, mv1, wo1[t]);
                         }
                     }
-                    cx* o0 = sm + (size_t)p0 * PS + c;
-                    cx* o1 = sm + (size_t)p1 * PS + c;
+                    cx* o0 = sm + (p0 * PS + c);
+                    cx* o1 = sm + (p1 * PS + c);
 #pragma unroll
                     for (int t = 0; t < HQ; ++t) {
                         o0[t * rt] = p2add(we0[t], wo0[t]);
@@ -344,12 +344,12 @@ __device__ __forceinline__ void fused_levels(const FusedConsts<Real, RP>& C, int
                 if (c < ncol) {
                     const int p0 = ((u >> bit) << (bit + 1)) | (u & ((1 << bit) - 1));
                     const int p1 = p0 | (1 << bit);
-                    const cx* du = dl + (size_t)u * DS;
+                    const cx* du = dl + u * DS;
                     // even and odd parts of both inputs (all reads before any write)
                     cx xe[2][HR], xo[2][HQ > 0 ? HQ : 1];
 #pragma unroll
                     for (int q = 0; q < 2; ++q) {
-                        const cx* xp = sm + (size_t)(q ? p1 : p0) * PS + c;
+                        const cx* xp = sm + ((q ? p1 : p0) * PS + c);
 #pragma unroll
                         for (int s2 = 0; s2 < HQ; ++s2) {
                             const cx lo = xp[s2 * rt], hi = xp[(RP - 1 - s2) * rt];
@@ -358,8 +358,8 @@ __device__ __forceinline__ void fused_levels(const FusedConsts<Real, RP>& C, int
                         }
                         if (ODD) xe[q][HQ] = xp[HQ * rt];
                     }
-                    cx* o0 = sm + (size_t)p0 * PS + c;
-                    cx* o1 = sm + (size_t)p1 * PS + c;
+                    cx* o0 = sm + (p0 * PS + c);
+                    cx* o1 = sm + (p1 * PS + c);
 #pragma unroll
                     for (int t = 0; t < RP; ++t) {
                         cx a0 = cz<cx>(), a1 = cz<cx>();
@@ -478,11 +478,12 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
             for (int pos = threadIdx.x >> 5; pos < G; pos += nw) {
                 const int64_t pair = !ADJ ? (i0 << (L - l0)) + (jb << k) + pos
                                           : (((i0 << k) + brevk(pos, k)) << nbj) + jb;
-                const cx* src = in + pair * RP * P.nc + col0 + lane;
+                // lanes past the last column copy nothing from column col0's (valid) row addresses
+                const cx* src = in + pair * RP * P.nc + col0 + (on ? lane : 0);
                 cx* dst = sm + pos * PS + lane;
                 if (!COH) {
 #pragma unroll
-                    for (int t = 0; t < RP; ++t) cp_async_elem(dst + t * 32, on ? src + (int64_t)t * P.nc : src, on);
+                    for (int t = 0; t < RP; ++t, src += P.nc) cp_async_elem(dst + t * 32, src, on);
                 } else {
                     cx v[RP];
 #pragma unroll
@@ -540,7 +541,7 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
                     cx* dst = out + pair * RP * P.nc + col0 + lane;
                     const cx* srcs = sm + pos * PS + lane;
 #pragma unroll
-                    for (int t = 0; t < RP; ++t) dst[(int64_t)t * P.nc] = srcs[t * 32];
+                    for (int t = 0; t < RP; ++t, dst += P.nc) *dst = srcs[t * 32];
                 }
         } else {
             for (int e = threadIdx.x; e < G * RP * rt; e += blockDim.x) {
