@@ -189,6 +189,7 @@ __global__ void __launch_bounds__(kXWarps * 32) kx_level_w(const cd* blk, const 
 // elements), and issues the copies of its next pair before computing the
 // current one, so copies stay in flight through the arithmetic.
 constexpr int kXPipeCols = 16;
+constexpr int kXMinCols = 4;   // fewer columns leave most lanes of a pair's warp idle
 
 template <typename cd>
 __global__ void __launch_bounds__(kXWarps * 32) kx_level_wp(const cd* blk, const cd* in, cd* out, int L, int l, int ro,
@@ -416,8 +417,12 @@ static int explicit_apply_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cud
         prof_mark(p, st, IBF_K_EXPLICIT_INIT);
         for (int l = 1; l <= L; ++l) {
             const int ro = rank_out(p, l), ri = rank_in(p, l);
-            if (nc <= kXPipeCols && launch_level_wp<cd>((const cd*)p->eblk[l], a, b, L, l, ro, ri, nc, N, st)) {
-            } else if (ro <= kXRmax && ri <= kXRmax)
+            // warp per pair where the level is memory-bound (complex64) and the
+            // pair has enough outputs for a warp; FP64 levels are bound by the
+            // FP64 pipe and keep one thread per output entry
+            const bool warp = sizeof(cd) == sizeof(float2) && nc >= kXMinCols;
+            if (warp && nc <= kXPipeCols && launch_level_wp<cd>((const cd*)p->eblk[l], a, b, L, l, ro, ri, nc, N, st)) {
+            } else if (warp && ro <= kXRmax && ri <= kXRmax)
                 kx_level_w<cd><<<(unsigned)((N + kXWarps - 1) / kXWarps), kXWarps * 32, xlevel_smem<cd>(), st>>>(
                     (const cd*)p->eblk[l], a, b, L, l, ro, ri, nc, N);
             else
@@ -459,7 +464,7 @@ static int explicit_adjoint_t(ibf_plan* p, const void* yv, void* gv, int nrhs, c
                 std::swap(a, b);
             }
             const int ro = rank_out(p, l), ri = rank_in(p, l);
-            if (ro <= kXRmax && ri <= kXRmax)
+            if (sizeof(cd) == sizeof(float2) && nc >= kXMinCols && ro <= kXRmax && ri <= kXRmax)
                 kx_level_adj_w<cd><<<(unsigned)((N + kXWarps - 1) / kXWarps), kXWarps * 32, xlevel_smem<cd>(), st>>>(
                     (const cd*)p->eblk[l], a, b, L, l, ro, ri, nc, N);
             else
