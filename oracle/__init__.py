@@ -36,6 +36,7 @@ PHASE_FIO1D = 1
 PHASE_FIO2D = 2
 PHASE_FIO2D_32 = 3      # the 2D FIO with the constants /32 printed in Sec. 6.3
 PHASE_FIO1D_SERIES = 4   # Phi = x xi + c(x)|xi|, c a trigonometric series (set_series)
+PHASE_FIO2D_SERIES = 5   # Phi = x.xi + sqrt(c1^2 xi1^2 + c2^2 xi2^2), c1, c2 2D series (set_series2)
 PHASE_SEPARABLE = 100
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -64,6 +65,8 @@ def _configure(lib):
     lib.orc_phi_1d.argtypes = [Ci, ctypes.c_double, ctypes.c_double]
     lib.orc_set_series.restype = Ci
     lib.orc_set_series.argtypes = [Ci, P, P]
+    lib.orc_set_series2.restype = Ci
+    lib.orc_set_series2.argtypes = [Ci, P]
     lib.orc_phi_2d.restype = ctypes.c_double
     lib.orc_phi_2d.argtypes = [Ci] + [ctypes.c_double] * 4
     lib.orc_cheb_grid.argtypes = [Ci, P]
@@ -140,6 +143,17 @@ def set_series(a, b) -> None:
     if a.shape != b.shape or not 1 <= a.size <= 16:
         raise ValueError("a and b: the same length, 1..16")
     assert _load().orc_set_series(a.size, _ptr(a), _ptr(b)) == 0
+
+
+def set_series2(terms) -> None:
+    """Coefficients of PHASE_FIO2D_SERIES: rows (p, q, al1, be1, al2, be2),
+    1..16 of them; c_d(x) = sum_t al_d cos(2 pi (p x1 + q x2)) +
+    be_d sin(2 pi (p x1 + q x2))."""
+    t = _f64(terms)
+    if t.ndim != 2 or t.shape[1] != 6 or not 1 <= t.shape[0] <= 16:
+        raise ValueError("terms: 1..16 rows of 6")
+    t = np.ascontiguousarray(t)
+    assert _load().orc_set_series2(t.shape[0], _ptr(t)) == 0
 
 
 def phi_1d(phase_id: int, x: float, xi: float) -> float:

@@ -46,6 +46,7 @@ typedef double complex cplx;
 #define ORC_PHASE_FIO2D 2      /* Phi = x.xi + sqrt(c1^2 xi1^2 + c2^2 xi2^2), c /16 */
 #define ORC_PHASE_FIO2D_32 3   /* the same with the constants /32 of Sec. 6.3      */
 #define ORC_PHASE_FIO1D_SERIES 4 /* Phi = x xi + c(x)|xi|, c a trigonometric series */
+#define ORC_PHASE_FIO2D_SERIES 5 /* Phi = x.xi + sqrt(c1^2 xi1^2 + c2^2 xi2^2), c1, c2 2D series */
 #define ORC_PHASE_SEPARABLE 100 /* test phase f(x) + h(xi): remainder R^{AB}=0 */
 
 /* ------------------------------------------------------------------ */
@@ -76,6 +77,42 @@ int orc_set_series(int M, const double* a, const double* b)
         orc_cb[m] = b[m];
     }
     return 0;
+}
+
+/* Coefficient series of ORC_PHASE_FIO2D_SERIES: for d = 1, 2
+ *   c_d(x) = sum_{t<M} al[d][t] cos(2 pi (p_t x1 + q_t x2)) + be[d][t] sin(2 pi (p_t x1 + q_t x2)),
+ * the 2D FIO of Sec. 6.3's form x.xi + sqrt(c1^2 xi1^2 + c2^2 xi2^2) (the
+ * generalized-Radon form Sec. 1 names) with smooth periodic coefficients.
+ * Sec. 6.3's c1 = (2 + sin 2 pi x1 sin 2 pi x2)/16 is
+ * 1/8 + cos(2 pi (x1 - x2))/32 - cos(2 pi (x1 + x2))/32.  Terms are rows
+ * (p_t, q_t, al1_t, be1_t, al2_t, be2_t); one series per process. */
+static int orc_nco2 = 0;
+static double orc_pq[16][2], orc_al[2][16], orc_be[2][16];
+
+int orc_set_series2(int M, const double* terms)
+{
+    if (M < 1 || M > 16) return 1;
+    orc_nco2 = M;
+    for (int t = 0; t < M; ++t) {
+        const double* row = terms + 6 * t;
+        orc_pq[t][0] = row[0];
+        orc_pq[t][1] = row[1];
+        orc_al[0][t] = row[2];
+        orc_be[0][t] = row[3];
+        orc_al[1][t] = row[4];
+        orc_be[1][t] = row[5];
+    }
+    return 0;
+}
+
+static double orc_series2(int d, double x1, double x2)
+{
+    double c = 0.0;
+    for (int t = 0; t < orc_nco2; ++t) {
+        double arg = 2.0 * M_PI * (orc_pq[t][0] * x1 + orc_pq[t][1] * x2);
+        c += orc_al[d][t] * cos(arg) + orc_be[d][t] * sin(arg);
+    }
+    return c;
 }
 
 /* 1D phase functions: eq. 1D-FT (with the sign of the K = e(+x xi) reading),
@@ -118,6 +155,11 @@ double orc_phi_2d(int phase_id, double x1, double x2, double k1, double k2)
         double c2 = (2.0 + cos(2.0 * M_PI * x1) * cos(2.0 * M_PI * x2)) / den;
         double a = c1 * k1;
         double b = c2 * k2;
+        return (x1 * k1 + x2 * k2) + sqrt(a * a + b * b);
+    }
+    case ORC_PHASE_FIO2D_SERIES: {
+        double a = orc_series2(0, x1, x2) * k1;
+        double b = orc_series2(1, x1, x2) * k2;
         return (x1 * k1 + x2 * k2) + sqrt(a * a + b * b);
     }
     case ORC_PHASE_NUFFT:

@@ -50,6 +50,14 @@ def test_direct_2d_equals_dft_closed_form():
 # ------------------------------------------------------------- phase shapes
 # the series of tests/golden/phase_values.txt, kind 4
 SERIES_GOLDEN_A, SERIES_GOLDEN_B = [0.25, 0.0, 0.125], [0.0, 0.125, 0.0]
+# the 2D series of tests/golden/phase_values.txt, kind 5: rows (p, q, al1, be1, al2, be2)
+SERIES2_GOLDEN = [[0, 0, 0.25, 0, 0.125, 0], [1, 0, 0, 0.125, 0, 0], [1, 1, 0.0625, 0, 0, 0],
+                  [0, 1, 0, 0, 0.0625, 0], [1, -1, 0, 0, 0, 0.03125]]
+# Sec. 6.3's coefficients (constants /16) as a series: sin a sin b = (cos(a-b) - cos(a+b))/2
+SERIES2_SEC63 = [[0, 0, 0.125, 0, 0.125, 0], [1, -1, 1 / 32, 0, 1 / 32, 0], [1, 1, -1 / 32, 0, 1 / 32, 0]]
+# smooth positive coefficients with six terms (c1 >= 0.14, c2 >= 0.08)
+SERIES2_SMOOTH = [[0, 0, 0.2, 0, 0.12, 0], [1, 0, 0.02, 0.015, 0, 0.01], [0, 1, -0.01, 0, 0.015, -0.005],
+                  [1, 1, 0, 0.01, 0.005, 0], [1, -1, 0.005, 0, 0, 0.008], [2, 1, 0, -0.004, 0.003, 0.002]]
 # a smooth positive coefficient with five terms (|c - 1/4| <= 0.11)
 SERIES_SMOOTH_A = [0.25, 0.04, -0.02, 0.01, 0.005]
 SERIES_SMOOTH_B = [0.0, 0.03, 0.015, -0.01, 0.004]
@@ -61,10 +69,12 @@ def test_phase_values_match_hand_computed():
     the 1D FIO and c1, c2 of the 2D FIO at quarter and twelfth points, where
     sin and cos take the values 0, +-1/2, +-1.  A phase-shifted coefficient
     (cos for sin) or c1 and c2 exchanged moves several rows by >= 1."""
-    kinds = {0: O.PHASE_NUFFT, 1: O.PHASE_FIO1D, 2: O.PHASE_FIO2D, 3: O.PHASE_FIO2D_32, 4: O.PHASE_FIO1D_SERIES}
+    kinds = {0: O.PHASE_NUFFT, 1: O.PHASE_FIO1D, 2: O.PHASE_FIO2D, 3: O.PHASE_FIO2D_32, 4: O.PHASE_FIO1D_SERIES,
+             5: O.PHASE_FIO2D_SERIES}
     O.set_series(SERIES_GOLDEN_A, SERIES_GOLDEN_B)
+    O.set_series2(SERIES2_GOLDEN)
     rows = read_golden("phase_values.txt")
-    assert len(rows) >= 26
+    assert len(rows) >= 37
     for kind, x1, x2, k1, k2, want in rows:
         ph = kinds[int(kind)]
         got = O.phi_1d(ph, x1, k1) if int(kind) in (0, 1, 4) else O.phi_2d(ph, x1, x2, k1, k2)

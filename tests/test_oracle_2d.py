@@ -89,3 +89,41 @@ def test_2d_adjoint_dot_product_identity_and_separable_exactness():
     row0 = np.exp(2j * np.pi * np.array([ph(x[0], b) for b in xi]))
     exact = np.conj(row0) * np.exp(2j * np.pi * ph(x[0], xi[0])) * np.vdot(col0, y)
     assert O.rel_l2(ga, exact) < 1e-12
+
+
+def test_series2_phase_reduces_to_sec63_fio():
+    """With c1 = 1/8 + (cos 2 pi (x1 - x2) - cos 2 pi (x1 + x2))/32 and
+    c2 = 1/8 + (cos 2 pi (x1 - x2) + cos 2 pi (x1 + x2))/32 the series phase is
+    Sec. 6.3's (constants /16): phases, direct sums and MIBFs agree to
+    rounding."""
+    from test_oracle import SERIES2_SEC63
+
+    O.set_series2(SERIES2_SEC63)
+    gen = W.rng(510)
+    for _ in range(50):
+        x1, x2 = gen.random(2)
+        k1, k2 = gen.uniform(-64, 64, 2)
+        a = O.phi_2d(O.PHASE_FIO2D_SERIES, x1, x2, k1, k2)
+        b = O.phi_2d(O.PHASE_FIO2D, x1, x2, k1, k2)
+        assert abs(a - b) < 1e-13 * max(1.0, abs(b))
+    n, r = 32, 7
+    x = W.grid_x_2d(n)
+    g = W.complex_normal((n * n, 2), W.rng(511))
+    ua = O.mibf_apply_2d(O.PHASE_FIO2D_SERIES, n, r, x, g)
+    ub = O.mibf_apply_2d(O.PHASE_FIO2D, n, r, x, g)
+    assert O.rel_l2(ua, ub) < 1e-12
+
+
+def test_series2_phase_mibf_converges_in_r():
+    """Six-term smooth coefficients: the MIBF error against the direct sum
+    falls by a factor > 3 per step of r and reaches the workload FIO's level."""
+    from test_oracle import SERIES2_SMOOTH
+
+    O.set_series2(SERIES2_SMOOTH)
+    n = 32
+    x = W.grid_x_2d(n)
+    g = W.complex_normal(n * n, W.rng(512))
+    ud = O.direct_2d(O.PHASE_FIO2D_SERIES, x, W.omega_2d(n), g)
+    errs = [O.rel_l2(O.mibf_apply_2d(O.PHASE_FIO2D_SERIES, n, r, x, g), ud) for r in (5, 7, 9)]
+    assert errs[0] > 3 * errs[1] > 9 * errs[2], errs
+    assert errs[1] < 1e-3, errs
