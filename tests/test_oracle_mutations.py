@@ -3,7 +3,8 @@ mistake in a copy of the oracle -- the C source recompiled with gcc, or a
 Python module re-executed from its edited source -- runs one of the real pin
 tests against the copy, and requires that pin to fail.  Mistakes: a sign of
 the phase factor, a phase-shifted 1D FIO coefficient, the sine terms of the
-series coefficient dropped, the 2D FIO coefficients exchanged, the Chebyshev
+series coefficient dropped, the 2D FIO coefficients exchanged, the 2D
+series' frequencies exchanged, its sine terms dropped or c2 used for c1, the Chebyshev
 grid, a dropped Lagrange factor, the child
 centre or a phase sign of a butterfly level, a transposed switch block, a
 wrong box width in U^L, a dropped phase factor in V^0, a skipped corona box
@@ -73,6 +74,16 @@ C_MUTATIONS = [
      "        double c2 = (2.0 + cos(2.0 * M_PI * x1) * cos(2.0 * M_PI * x2)) / den;",
      "double c2 = (2.0 + sin(2.0 * M_PI * x1) * sin(2.0 * M_PI * x2)) / den;\n"
      "        double c1 = (2.0 + cos(2.0 * M_PI * x1) * cos(2.0 * M_PI * x2)) / den;",
+     T.test_phase_values_match_hand_computed),
+    ("2D series: p and q exchanged",
+     "double arg = 2.0 * M_PI * (orc_pq[t][0] * x1 + orc_pq[t][1] * x2);",
+     "double arg = 2.0 * M_PI * (orc_pq[t][1] * x1 + orc_pq[t][0] * x2);",
+     T.test_phase_values_match_hand_computed),
+    ("2D series: sine terms dropped",
+     "c += orc_al[d][t] * cos(arg) + orc_be[d][t] * sin(arg);", "c += orc_al[d][t] * cos(arg);",
+     T.test_phase_values_match_hand_computed),
+    ("2D series: c2 used in place of c1",
+     "double a = orc_series2(0, x1, x2) * k1;", "double a = orc_series2(1, x1, x2) * k1;",
      T.test_phase_values_match_hand_computed),
     ("adjoint conjugate dropped", "                                 e2pi(-orc_phi_1d(ph, gPs, cC));\n"
      "                        acc += conj(w) * ln[t];",
