@@ -614,6 +614,55 @@ def dominant_roofline(prof, L, h, kfuse, r, N, nrhs, fp32_peak, hbm_peak):
                           for (a0, b0, kk), v in per_launch.items()}}
 
 
+# Series coefficients of the phases with caller-given coefficients: 1D,
+# c(x) = sum_m a_m cos(2 pi m x) + b_m sin(2 pi m x) (Sec. 6.2's c plus three
+# harmonics); 2D, rows (p, q, al1, be1, al2, be2) of c1, c2 (Sec. 6.3's form).
+SERIES1D = ([0.25, 0.01, -0.02, 0.01], [0.0, 0.125, 0.015, -0.01])
+SERIES2D = [[0, 0, 0.2, 0, 0.12, 0], [1, 0, 0.02, 0.015, 0, 0.01], [0, 1, -0.01, 0, 0.015, -0.005],
+            [1, 1, 0, 0.01, 0.005, 0], [1, -1, 0.005, 0, 0, 0.008], [2, 1, 0, -0.004, 0.003, 0.002]]
+
+
+def run_series(ibf, torch, reps=5):
+    """The FIOs with series coefficients: plan construction (wall clock) and
+    FP32 apply at the workload sizes -- 1D N=2^20, r=9, 64 columns (tile and
+    depth of the FIO1D workload) and 2D n=512, r=7, 32 columns -- beside the
+    fixed-coefficient phases of Sec. 6.2 / 6.3 at the same sizes."""
+    cs = torch.cuda.current_stream().cuda_stream
+    out = {"workload": "1D N=2^20 r=9 64 columns; 2D n=512 r=7 32 columns; complex64 structured",
+           "series1d_terms": len(SERIES1D[0]), "series2d_terms": len(SERIES2D)}
+
+    def timed(plan, nrhs, N):
+        g = torch.from_numpy(W.complex_normal((nrhs, N), W.rng(workload=7), dtype=np.complex64)).cuda()
+        u = torch.empty_like(g)
+        for _ in range(2):
+            plan.apply_raw(g.data_ptr(), u.data_ptr(), nrhs, cs)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            plan.apply_raw(g.data_ptr(), u.data_ptr(), nrhs, cs)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    for tag, phase, d, N, r, nrhs, kw in (
+            ("fio1d", ibf.PHASE_FIO1D, 1, 1 << 20, 9, 64, {}),
+            ("series1d", ibf.PHASE_FIO1D_SERIES, 1, 1 << 20, 9, 64, {"coef": SERIES1D}),
+            ("fio2d", ibf.PHASE_FIO2D, 2, 512 * 512, 7, 32, {}),
+            ("series2d", ibf.PHASE_FIO2D_SERIES, 2, 512 * 512, 7, 32, {"coef": SERIES2D})):
+        extra = {"levels_per_launch": 4, "rhs_tile": 32} if d == 1 else {}
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan = ibf.Plan(phase, N, r, ibf.C64_FP32, d=d, max_nrhs=nrhs, **extra, **kw)
+        torch.cuda.synchronize()
+        t_build = (time.perf_counter() - t0) * 1e3
+        ms = timed(plan, nrhs, N)
+        out[tag] = {"construct_ms": t_build, "apply_ms": ms, "vectors_per_s": nrhs * 1e3 / ms}
+        plan.close()
+    return out
+
+
 def run_config2_sweep(ibf, torch, fp32_peak, hbm_peak, Ns=(1 << 16, 1 << 18, 1 << 20), nrhss=(1, 16, 64), reps=5):
     """1D FIO grid N x nrhs: the FP32 structured apply in its autotuned launch
     shape (vectors/s, the dominant launch's roofline fraction) against the
@@ -892,6 +941,10 @@ def run_gpu(a):
     if rank == 0 and not a.skip_2d:
         fio2d = run_2d(ibf, torch)
 
+    series = None
+    if rank == 0 and not a.skip_2d:
+        series = run_series(ibf, torch)
+
     tensorcore = None
     if rank == 0 and not a.skip_tc:
         tensorcore = run_tensorcore(ibf, torch, N=N, nrhs=nrhs)
@@ -926,7 +979,7 @@ def run_gpu(a):
                 "clocks": clk, "e2e": e2e, "gpu_launches": a.steps * launches, "roofline": roof,
                 "fp64_plain": fp64, "construction": construction, "batch256": batch, "autograd": grad5, "optimal_ibf": optimal, "nufft1024_latency": nufft,
                 "amplitude": amplitude, "tensorcore": tensorcore, "config2_sweep": sweep,
-                "fio2d": fio2d, "cpu_baseline": cpu}
+                "fio2d": fio2d, "series_phases": series, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:
@@ -962,6 +1015,8 @@ def main():
                     help="profiling aid: one warm-up and one timed apply of an FP32 and a TF32X3 plan at size N "
                          "(--nrhs columns, --levels-per-launch levels, default 4)")
     ap.add_argument("--skip-tc", action="store_true")
+    ap.add_argument("--only-series", action="store_true",
+                    help="profiling aid: construction and apply of the series-coefficient phases only")
     ap.add_argument("--skip-sweep", action="store_true")
     ap.add_argument("--only-sweep", action="store_true", help="profiling aid: run only the config-2 grid")
     a = ap.parse_args()
@@ -969,11 +1024,13 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if a.impl == "reference":
         return run_reference(a)
-    if a.only_2d or a.only_batch or a.only_optimal or a.only_amplitude or a.only_tc or a.only_sweep:
+    if a.only_2d or a.only_batch or a.only_optimal or a.only_amplitude or a.only_tc or a.only_sweep or a.only_series:
         import torch
         import paper_1605_03616_gb300 as ibf
         if a.only_2d:
             name, rec = "fio2d", run_2d(ibf, torch, n=a.only_2d)
+        elif a.only_series:
+            name, rec = "series_phases", run_series(ibf, torch)
         elif a.only_batch:
             name, rec = "batch256", run_batch(ibf, torch)
         elif a.only_optimal:

@@ -72,6 +72,20 @@ enum ibf_phase {
                                    phase_ncoef): the 1D FIOs of Assumption 1.1
                                    with a smooth periodic c; Sec. 6.2's phase is
                                    a_0 = 1/4, b_1 = 1/8.  d = 1 only.              */
+    IBF_PHASE_FIO2D_SERIES = 5, /* Phi = x.xi + sqrt(c1^2 xi1^2 + c2^2 xi2^2), the
+                                   generalized-Radon form of Sec. 6.3 (Sec. 1 names
+                                   the class), with caller-given coefficients
+                                   c_d(x) = sum_{t<M} al_{d,t} cos(2 pi (p_t x1 + q_t x2))
+                                   + be_{d,t} sin(2 pi (p_t x1 + q_t x2)), d = 1, 2
+                                   (ibf_options.phase_coef, phase_ncoef).  Each c_d
+                                   must be bounded away from zero by its terms: the
+                                   sum of al_{d,t} over the terms with p_t = q_t = 0
+                                   must exceed the sum of |al_{d,t}| + |be_{d,t}|
+                                   over the others (then Phi is smooth in xi away
+                                   from 0, Assumption 1.1), else IBF_ERR_INVALID.
+                                   Sec. 6.3's c1, c2 (constants /16) are the rows
+                                   (0, 0, 1/8, 0, 1/8, 0), (1, -1, 1/32, 0, 1/32, 0),
+                                   (1, 1, -1/32, 0, 1/32, 0).  d = 2 only.        */
     IBF_PHASE_SEPARABLE = 100   /* test phase f(x) + h(xi), f = 0.75 sin 2 pi x,
                                    h = 0.125|xi| + 0.3 sin(0.1 xi); the remainder
                                    R^{AB} of eq. RAB vanishes, so the IBF is exact    */
@@ -135,8 +149,10 @@ typedef struct ibf_options {
     int rank;              /* optimal form: rank r0 of every compressed block,
                               1..r (the paper's r0); ignored by the other forms    */
     const double* phase_coef; /* IBF_PHASE_FIO1D_SERIES: 2 M host doubles, a_0..a_{M-1}
-                              then b_0..b_{M-1}; copied at creation              */
-    int phase_ncoef;       /* IBF_PHASE_FIO1D_SERIES: M, 1..16                     */
+                              then b_0..b_{M-1}.  IBF_PHASE_FIO2D_SERIES: 6 M host
+                              doubles, rows (p_t, q_t, al_{1,t}, be_{1,t}, al_{2,t},
+                              be_{2,t}).  Copied at creation; all finite.         */
+    int phase_ncoef;       /* the series phases: M, 1..16                          */
 } ibf_options;
 
 /*

@@ -21,6 +21,7 @@ PHASE_NUFFT = 0
 PHASE_FIO1D = 1
 PHASE_FIO2D = 2
 PHASE_FIO1D_SERIES = 4     # Phi = x xi + c(x)|xi|, c(x) a trigonometric series (coef=(a, b))
+PHASE_FIO2D_SERIES = 5     # Phi = x.xi + sqrt(c1^2 xi1^2 + c2^2 xi2^2), c1, c2 2D series (coef=rows of 6)
 PHASE_SEPARABLE = 100
 
 C128 = 0
@@ -143,7 +144,14 @@ class Plan:
         self._lib = load_library()
         self.N, self.r, self.dtype, self.phase = int(N), int(r), int(dtype), int(phase)
         opt = Options(form, h, max_nrhs, levels_per_launch, rhs_tile, rank)
-        if coef is not None:
+        if coef is not None and self.phase == PHASE_FIO2D_SERIES:
+            # rows (p, q, al1, be1, al2, be2): c_d(x) = sum_t al_d cos(2 pi (p x1 + q x2)) + be_d sin(...)
+            self._coef = np.ascontiguousarray(coef, dtype=np.float64)
+            if self._coef.ndim != 2 or self._coef.shape[1] != 6:
+                raise ValueError("coef: rows of (p, q, al1, be1, al2, be2)")
+            opt.phase_coef = self._coef.ctypes.data
+            opt.phase_ncoef = self._coef.shape[0]
+        elif coef is not None:
             # PHASE_FIO1D_SERIES: coef = (a, b), c(x) = sum_m a[m] cos(2 pi m x) + b[m] sin(2 pi m x)
             a, b = (np.ascontiguousarray(v, dtype=np.float64).ravel() for v in coef)
             if a.shape != b.shape:

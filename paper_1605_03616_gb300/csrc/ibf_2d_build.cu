@@ -18,13 +18,33 @@ struct Geo2 {
     int n, r, phase, Lq;
     double m;
     double z[kMaxR];
+    // IBF_PHASE_FIO2D_SERIES: frequencies (p_t, q_t) and coefficients of c1, c2
+    int nco;
+    double pq[kMaxCoef][2], al[2][kMaxCoef], be[2][kMaxCoef];
 };
 
 __device__ __forceinline__ double p2(int l) { return (double)(1LL << l); }
 
-__device__ __forceinline__ double phi2d(int ph, double x1, double x2, double k1, double k2)
+// c_d(x) of IBF_PHASE_FIO2D_SERIES: sum_t al cos(2 pi (p x1 + q x2)) + be sin(2 pi (p x1 + q x2))
+__device__ __forceinline__ double series2(const Geo2& G, int d, double x1, double x2)
+{
+    double c = 0.0;
+    for (int t = 0; t < G.nco; ++t) {
+        const double arg = 2.0 * 3.141592653589793 * (G.pq[t][0] * x1 + G.pq[t][1] * x2);
+        c += G.al[d][t] * cos(arg) + G.be[d][t] * sin(arg);
+    }
+    return c;
+}
+
+__device__ __forceinline__ double phi2d(const Geo2& G, double x1, double x2, double k1, double k2)
 {
     const double tp = 2.0 * 3.141592653589793;
+    const int ph = G.phase;
+    if (ph == IBF_PHASE_FIO2D_SERIES) {
+        const double a = series2(G, 0, x1, x2) * k1;
+        const double b = series2(G, 1, x1, x2) * k2;
+        return (x1 * k1 + x2 * k2) + sqrt(a * a + b * b);
+    }
     if (ph == IBF_PHASE_FIO2D) {
         double c1 = (2.0 + sin(tp * x1) * sin(tp * x2)) / 16.0;
         double c2 = (2.0 + cos(tp * x1) * cos(tp * x2)) / 16.0;
@@ -104,7 +124,7 @@ __global__ void k2b_V(const Geo2 G, const Boxes Bx, C* V)
     wb(G, Bx.q1[b], Bx.q2[b], G.Lq, j, cB1, cB2, wB);
     const double k1 = Bx.q1[b] + (double)(j >> G.Lq), k2 = Bx.q2[b] + (double)(j & ((1LL << G.Lq) - 1));
     const double w = lag1(G, t / G.r, (k1 - cB1) / wB) * lag1(G, t % G.r, (k2 - cB2) / wB);
-    double2 v = e2(phi2d(G.phase, 0.5, 0.5, k1, k2));
+    double2 v = e2(phi2d(G, 0.5, 0.5, k1, k2));
     put(V + e, make_double2(w * v.x, w * v.y));
 }
 
@@ -129,14 +149,14 @@ __global__ void k2b_D(const Geo2 G, const Boxes Bx, int l, int hq, C* D)
         const double g1 = cC1 + wC * G.z[s / G.r], g2 = cC2 + wC * G.z[s % G.r];
         xb(l, i, cA1, cA2, wA);
         xb(l - 1, parent2(l, i), cP1, cP2, wP);
-        d = phi2d(G.phase, cA1, cA2, g1, g2) - phi2d(G.phase, cP1, cP2, g1, g2);
+        d = phi2d(G, cA1, cA2, g1, g2) - phi2d(G, cP1, cP2, g1, g2);
     } else {
         double cA1, cA2, wA, cC1, cC2, wC, cR1, cR2, wR;
         xb(l, i, cA1, cA2, wA);
         const double g1 = cA1 + wA * G.z[s / G.r], g2 = cA2 + wA * G.z[s % G.r];
         wb(G, Bx.q1[b], Bx.q2[b], cl, Cc, cC1, cC2, wC);
         wb(G, Bx.q1[b], Bx.q2[b], cl - 1, parent2(cl, Cc), cR1, cR2, wR);
-        d = phi2d(G.phase, g1, g2, cC1, cC2) - phi2d(G.phase, g1, g2, cR1, cR2);
+        d = phi2d(G, g1, g2, cC1, cC2) - phi2d(G, g1, g2, cR1, cR2);
     }
     put(D + e, e2(d));
 }
@@ -160,8 +180,8 @@ __global__ void k2b_M(const Geo2 G, const Boxes Bx, int hq, C* M)
     wb(G, Bx.q1[b], Bx.q2[b], G.Lq - hq, j, cB1, cB2, wB);
     const double a1 = cA1 + wA * G.z[t / G.r], a2 = cA2 + wA * G.z[t % G.r];
     const double b1 = cB1 + wB * G.z[s / G.r], b2 = cB2 + wB * G.z[s % G.r];
-    const double d = phi2d(G.phase, a1, a2, b1, b2) - phi2d(G.phase, cA1, cA2, b1, b2) -
-                     phi2d(G.phase, a1, a2, cB1, cB2);
+    const double d = phi2d(G, a1, a2, b1, b2) - phi2d(G, cA1, cA2, b1, b2) -
+                     phi2d(G, a1, a2, cB1, cB2);
     put(M + e, e2(d));
 }
 
@@ -176,7 +196,7 @@ __global__ void k2b_U(const Geo2 G, const Boxes Bx, C* U)
     const int b = (int)(e / nx);
     const double x1 = (double)(pt / G.n) / (double)G.n, x2 = (double)(pt % G.n) / (double)G.n;
     const double c1 = Bx.q1[b] + 0.5 * G.m, c2 = Bx.q2[b] + 0.5 * G.m;
-    put(U + e, e2(phi2d(G.phase, x1, x2, c1, c2)));
+    put(U + e, e2(phi2d(G, x1, x2, c1, c2)));
 }
 
 // lw[o][t] = M_t((o - K/2)/K): Lagrange weight of a grid point at offset o in
@@ -202,7 +222,7 @@ __global__ void k2b_KC(const Geo2 G, int csd, C* KC)
     const int64_t k = e % cc, pt = e / cc;
     const double x1 = (double)(pt / G.n) / (double)G.n, x2 = (double)(pt % G.n) / (double)G.n;
     const double k1 = -0.5 * csd + (double)(k / csd), k2 = -0.5 * csd + (double)(k % csd);
-    put(KC + e, e2(phi2d(G.phase, x1, x2, k1, k2)));
+    put(KC + e, e2(phi2d(G, x1, x2, k1, k2)));
 }
 
 static inline unsigned nb2(int64_t n) { return (unsigned)((n + 255) / 256); }
@@ -233,6 +253,16 @@ static int build_2d_t(ibf_plan* p)
     G.r = r;
     G.phase = p->phase_id;
     for (int t = 0; t < r; ++t) G.z[t] = p->z[t];
+    G.nco = (int)p->coef.size() / 6;
+    for (int t = 0; t < G.nco; ++t) {
+        const double* row = &p->coef[6 * t];
+        G.pq[t][0] = row[0];
+        G.pq[t][1] = row[1];
+        for (int d = 0; d < 2; ++d) {
+            G.al[d][t] = row[2 + 2 * d];
+            G.be[d][t] = row[3 + 2 * d];
+        }
+    }
     int64_t nnz = 0;
     // rings: S_t = [-n/2^(t+1), n/2^(t+1))^2 while its side exceeds the centre
     for (int side = n; side > P->center; side /= 2) {

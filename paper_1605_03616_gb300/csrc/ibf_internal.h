@@ -14,7 +14,7 @@ namespace ibf {
 
 constexpr int kMaxR = 16;       // Chebyshev points per box
 constexpr int kMaxFuse = 10;    // butterfly levels fused in one structured kernel
-constexpr int kMaxCoef = 16;    // terms of the coefficient series of IBF_PHASE_FIO1D_SERIES
+constexpr int kMaxCoef = 16;    // terms of the coefficient series of the series phases
 
 // Host-side record of the last error of the calling thread.
 int set_error(int code, const std::string& msg);
@@ -24,7 +24,7 @@ int cuda_error(cudaError_t e, const char* what);
 
 struct ibf_plan {
     int phase_id = 0, d = 1, r = 0, dtype = 0, form = 0;
-    std::vector<double> coef;   // IBF_PHASE_FIO1D_SERIES: a_0..a_{M-1}, b_0..b_{M-1}
+    std::vector<double> coef;   // series phases: a_0..a_{M-1}, b_0..b_{M-1} (1D) or M rows of 6 (2D)
     int L = 0, h = 0;
     int64_t N = 0, nx = 0;
     int max_nrhs = 0;

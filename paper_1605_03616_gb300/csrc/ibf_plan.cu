@@ -438,8 +438,31 @@ extern "C" int ibf_plan_create(int phase_id, int d, int64_t N, int r, int dtype,
 static int create_2d(int phase_id, int64_t N, int r, int dtype, const double* x, const ibf_options* opt,
                      ibf_plan** out)
 {
-    if (phase_id != IBF_PHASE_FIO2D && phase_id != IBF_PHASE_NUFFT && phase_id != IBF_PHASE_SEPARABLE)
+    if (phase_id != IBF_PHASE_FIO2D && phase_id != IBF_PHASE_NUFFT && phase_id != IBF_PHASE_SEPARABLE &&
+        phase_id != IBF_PHASE_FIO2D_SERIES)
         return set_error(IBF_ERR_INVALID, "unknown 2D phase id " + std::to_string(phase_id));
+    std::vector<double> coef;
+    if (phase_id == IBF_PHASE_FIO2D_SERIES) {
+        if (!opt || !opt->phase_coef || opt->phase_ncoef < 1 || opt->phase_ncoef > kMaxCoef)
+            return set_error(IBF_ERR_INVALID, "IBF_PHASE_FIO2D_SERIES needs phase_coef and 1 <= phase_ncoef <= 16");
+        coef.assign(opt->phase_coef, opt->phase_coef + 6 * opt->phase_ncoef);
+        for (double v : coef)
+            if (!std::isfinite(v)) return set_error(IBF_ERR_INVALID, "phase_coef must be finite");
+        // c_d >= (constant terms) - (sum of the other terms' |al| + |be|) must be > 0
+        for (int d = 0; d < 2; ++d) {
+            double c0 = 0.0, rest = 0.0;
+            for (int t = 0; t < opt->phase_ncoef; ++t) {
+                const double* row = &coef[6 * t];
+                if (row[0] == 0.0 && row[1] == 0.0)
+                    c0 += row[2 + 2 * d];
+                else
+                    rest += std::fabs(row[2 + 2 * d]) + std::fabs(row[3 + 2 * d]);
+            }
+            if (!(c0 > rest))
+                return set_error(IBF_ERR_INVALID, "IBF_PHASE_FIO2D_SERIES: c" + std::to_string(d + 1) +
+                                                      " is not bounded away from zero by its terms");
+        }
+    }
     int n = 1;
     while ((int64_t)n * n < N && n < (1 << 12)) n *= 2;
     if ((int64_t)n * n != N || n < 32 || n > 2048)
@@ -454,6 +477,7 @@ static int create_2d(int phase_id, int64_t N, int r, int dtype, const double* x,
         return set_error(IBF_ERR_UNSUPPORTED, "2D: structured form only");
     ibf_plan* p = new ibf_plan();
     p->phase_id = phase_id;
+    p->coef = coef;
     p->d = 2;
     p->r = r;
     p->dtype = dtype;

@@ -133,3 +133,33 @@ def test_series_phase_validated_without_gpu(lib):
     assert create(ok, 2, d=2, N=64 * 64, r=7) == 1          # no 2D form
     out = ctypes.c_void_p()
     assert lib.ibf_plan_create(ibf.PHASE_FIO1D_SERIES, 1, 1024, 9, ibf.C64_FP32, ctypes.byref(out)) == 1
+
+
+def test_series2_phase_validated_without_gpu(lib):
+    """IBF_PHASE_FIO2D_SERIES needs 1..16 finite rows of 6 whose constant
+    terms bound each coefficient away from zero, and is 2D only; every
+    refusal comes before a CUDA call."""
+    import numpy as np
+    import paper_1605_03616_gb300 as ibf
+
+    def create(rows, nrows, d=2, N=64 * 64, r=7):
+        o = ibf.Options()
+        o.form = ibf.FORM_STRUCTURED
+        if rows is not None:
+            rows = np.ascontiguousarray(rows, dtype=np.float64)
+            o.phase_coef = rows.ctypes.data
+        o.phase_ncoef = nrows
+        out = ctypes.c_void_p()
+        return lib.ibf_plan_create_ex(ibf.PHASE_FIO2D_SERIES, d, N, r, ibf.C64_FP32, None, ctypes.byref(o),
+                                      ctypes.byref(out))
+
+    ok = [[0, 0, 0.125, 0, 0.125, 0], [1, -1, 1 / 32, 0, 1 / 32, 0], [1, 1, -1 / 32, 0, 1 / 32, 0]]
+    assert create(None, 3) == 1
+    assert create(ok, 0) == 1
+    assert create(ok, 17) == 1
+    assert create([[0, 0, 0.125, 0, 0.125, np.inf]], 1) == 1
+    assert create([[0, 0, 0.05, 0, 0.125, 0], [1, 0, 0.03, 0.02, 0, 0]], 2) == 1     # c1 may vanish
+    assert create([[0, 0, 0.125, 0, 0.05, 0], [0, 1, 0, 0, 0.05, 0]], 2) == 1        # c2 may vanish
+    assert create([[0, 0, 0.125, 0, -0.125, 0]], 1) == 1                             # c2 < 0
+    assert create(ok, 3, d=1, N=1024, r=9) == 1                                      # no 1D form
+

@@ -55,7 +55,7 @@ SERIES2_GOLDEN = [[0, 0, 0.25, 0, 0.125, 0], [1, 0, 0, 0.125, 0, 0], [1, 1, 0.06
                   [0, 1, 0, 0, 0.0625, 0], [1, -1, 0, 0, 0, 0.03125]]
 # Sec. 6.3's coefficients (constants /16) as a series: sin a sin b = (cos(a-b) - cos(a+b))/2
 SERIES2_SEC63 = [[0, 0, 0.125, 0, 0.125, 0], [1, -1, 1 / 32, 0, 1 / 32, 0], [1, 1, -1 / 32, 0, 1 / 32, 0]]
-# smooth positive coefficients with six terms (c1 >= 0.14, c2 >= 0.08)
+# smooth positive coefficients with six terms (c1 >= 0.136, c2 >= 0.072)
 SERIES2_SMOOTH = [[0, 0, 0.2, 0, 0.12, 0], [1, 0, 0.02, 0.015, 0, 0.01], [0, 1, -0.01, 0, 0.015, -0.005],
                   [1, 1, 0, 0.01, 0.005, 0], [1, -1, 0.005, 0, 0, 0.008], [2, 1, 0, -0.004, 0.003, 0.002]]
 # a smooth positive coefficient with five terms (|c - 1/4| <= 0.11)
