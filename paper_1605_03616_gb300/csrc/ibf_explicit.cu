@@ -11,6 +11,7 @@
 // at every level after the sweep-out stage, and after the sweep-in stage a
 // rank per level (r_out x r_in blocks, an r_g x r_h middle factor).
 #include <algorithm>
+#include <type_traits>
 
 #include "ibf_internal.h"
 
@@ -125,6 +126,7 @@ __global__ void kx_level_adj(const cd* blk, const cd* out, cd* in, int L, int l,
 constexpr int kXWarps = 8;     // warps (pairs) per CTA
 constexpr int kXCT = 8;        // columns per tile
 constexpr int kXRmax = 16;
+constexpr int kXMinCols = 4;   // fewer columns leave most lanes of a pair's warp idle
 
 __device__ __forceinline__ void xcp(float2* d, const float2* s)
 {
@@ -181,59 +183,6 @@ __global__ void __launch_bounds__(kXWarps * 32) kx_level_w(const cd* blk, const 
         }
         __syncwarp();   // the tile's inputs are read before the next tile's copies
     }
-}
-
-// Persistent, double-buffered form of kx_level_w for nc <= kXPipeCols: every
-// warp walks pairs w, w + W, w + 2W, ... (W = warps in the grid) with two
-// shared-memory slices sized to the level's ranks (2 ro ri + 2 ri nc
-// elements), and issues the copies of its next pair before computing the
-// current one, so copies stay in flight through the arithmetic.
-constexpr int kXPipeCols = 16;
-constexpr int kXMinCols = 4;   // fewer columns leave most lanes of a pair's warp idle
-
-template <typename cd>
-__global__ void __launch_bounds__(kXWarps * 32) kx_level_wp(const cd* blk, const cd* in, cd* out, int L, int l, int ro,
-                                                             int ri, int nc, int64_t N, int slice)
-{
-    extern __shared__ __align__(16) unsigned char xsm[];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t W = (int64_t)gridDim.x * kXWarps;
-    cd* s0 = reinterpret_cast<cd*>(xsm) + (size_t)w * 2 * slice;
-    cd* s1 = s0 + slice;
-    const int nb = 2 * ro * ri, nx = 2 * ri * nc;
-    const int64_t nj = 1LL << (L - l);
-    auto issue = [&](int64_t p, cd* sl) {
-        const int64_t i = p >> (L - l), j = p & (nj - 1);
-        const int64_t q0 = (i >> 1) * (2 * nj) + 2 * j;
-        const cd* bp = blk + p * nb;
-        const cd* xp = in + q0 * ri * nc;          // the two input pairs are contiguous
-        for (int e = lane; e < nb; e += 32) xcp(sl + e, bp + e);
-        for (int e = lane; e < nx; e += 32) xcp(sl + nb + e, xp + e);
-    };
-    int64_t p = (int64_t)blockIdx.x * kXWarps + w;
-    if (p < N) issue(p, s0);
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    for (int it = 0; p < N; ++it, p += W) {
-        cd* cur = (it & 1) ? s1 : s0;
-        if (p + W < N) issue(p + W, (it & 1) ? s0 : s1);
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-        __syncwarp();
-        const cd* sx = cur + nb;                   // [c][s][col]
-        for (int o = lane; o < ro * nc; o += 32) {
-            const int t = o / nc, col = o - t * nc;
-            cd acc = cmk<cd>(0, 0);
-            for (int c = 0; c < 2; ++c) {
-                const cd* row = cur + (c * ro + t) * ri;
-                const cd* v = sx + c * ri * nc + col;
-#pragma unroll 4
-                for (int s2 = 0; s2 < ri; ++s2) cadd(acc, cmul(row[s2], v[s2 * nc]));
-            }
-            out[(p * ro + t) * nc + col] = acc;
-        }
-        __syncwarp();   // every lane is done with this slice before it is refilled
-    }
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
 // adjoint of level l, warp per input pair q = (i', C) of level l-1: it
@@ -374,30 +323,311 @@ int explicit_launches(const ibf_plan* p) { return p->L + 3; }
 
 // persistent warp-per-pair level: as many CTAs as are resident at once;
 // false (nothing launched) if its slices do not fit one CTA's shared memory
-template <typename cd>
-static bool launch_level_wp(const cd* blk, const cd* in, cd* out, int L, int l, int ro, int ri, int nc, int64_t N,
-                            cudaStream_t st)
+
+// Bulk-copy pipeline form of the forward levels and the forward switch for
+// complex64 plans with 4, 8, 12 or 16 columns.  A level streams every block
+// once and reads each input pair twice (the two output pairs of a unit share
+// it), so it is bound by HBM once enough bytes are in flight.  A persistent
+// CTA (one per SM) walks chunks of B consecutive output pairs: their blocks
+// are one contiguous run, and so are their input pairs (one run of pairs
+// (i/2, 2j + c) per row, and rows 2i' and 2i'+1 share theirs; the switch
+// reads pair p itself).  One producer lane copies each chunk with two
+// cp.async.bulk transfers into a ring of shared-memory stages, completed on
+// the stage's "full" mbarrier.  The consumer warps form groups of Gw warps,
+// enough lanes for the chunk's B ro output rows; group g computes chunks g,
+// g + ngroups, ... (one output row, all columns, per lane) and releases each
+// stage on its "empty" mbarrier.  Each group owns sg stages of the ring and
+// uses them in turn, so a stage has one consumer that sees its phases in
+// order (a parity wait cannot tell phase n from phase n - 2), and the next
+// chunk of every group is in flight while the group computes.  Every wait
+// is bounded: when one expires the kernel sets *status, stops issuing copies,
+// waits (bounded) for the copies it issued and returns.
+constexpr int kXbWarps = 16;           // consumer warps per CTA
+constexpr int kXbMaxStages = 16;
+constexpr int kXbMaxPairs = 512;       // pairs per chunk
+constexpr int kXbMaxGroupWarps = 4;    // warps per group: at least four groups
+constexpr int kXbChunkBytes = 32 << 10;
+constexpr int kXbSmemBudget = 200 << 10;
+
+// Waits poll the barrier and sleep between polls, so that a waiting warp
+// (the producer is usually ahead and waits for a free stage) takes few issue
+// slots from the computing warps; at most kXbPolls polls, about 1 s in all
+// before a wait counts as expired.
+constexpr int kXbPolls = 1 << 22;
+constexpr unsigned kXbSleepNs = 256;
+
+__device__ __forceinline__ unsigned xb_smem(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool xb_wait(unsigned mbar, unsigned parity)
 {
-    const int slice = (2 * ro * ri + 2 * ri * nc + 1) & ~1;   // even: 16-byte aligned slices for complex64
-    const size_t smem = (size_t)kXWarps * 2 * slice * sizeof(cd);
-    int dev = 0, nsm = 0, occ = 0, optin = 0;
+    for (int i = 0; i < kXbPolls; ++i) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        __nanosleep(kXbSleepNs);
+    }
+    return false;
+}
+
+// one non-blocking check of a barrier phase
+__device__ __forceinline__ bool xb_test(unsigned mbar, unsigned parity)
+{
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// first input pair of output pair p: (i/2, 2j) of level l-1 for a level, p
+// itself for the switch
+template <bool SW>
+__device__ __forceinline__ int64_t xb_q0(int64_t p, int L, int l)
+{
+    if (SW) return p;
+    const int64_t nj = 1LL << (L - l);
+    return ((p >> (L - l)) >> 1) * (2 * nj) + 2 * (p & (nj - 1));
+}
+
+// One lane's outputs t = tq + m TQ (m < M, the last one stored only while
+// t < ro) of one output pair in one column: bp points at row tq of block
+// c = 0, xp at the lane's column of input pair c = 0 (inputs [c][s][col]), op
+// at output (tq, col).  NC blocks per pair (2 for a level, 1 for the switch).
+// Rows t >= ro of the last output read past the pair's blocks, at most TQ - 1
+// rows, which stay inside the stage (its input run follows the blocks): the
+// arithmetic runs unguarded and only the store is skipped.
+// One output column (pair p, column col, all RO rows) of a level (NC = 2
+// blocks) or the switch (NC = 1): u[t][col] = sum_c sum_s B_c[t][s] x_c[s][col].
+// br points at block c = 0 of the pair ([c][t][s], blocks of RO x ri), xr at
+// the lane's column of input pair c = 0 ([c][s][col], rows of nc columns),
+// op at output (0, col).  The nc lanes of a pair read the same block entries
+// (broadcasts) and consecutive input columns.
+template <int RO, int NC>
+__device__ __forceinline__ void xb_col(const float2* br, const float2* xr, float2* op, int ri, int nc)
+{
+    float2 acc[RO];
+#pragma unroll
+    for (int t = 0; t < RO; ++t) acc[t] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const float2* b = br + c * RO * ri;
+        const float2* x = xr + c * ri * nc;
+#pragma unroll 3
+        for (int s2 = 0; s2 < ri; ++s2, ++b, x += nc) {
+            const float2 xv = *x;
+#pragma unroll
+            for (int t = 0; t < RO; ++t) {
+                const float2 bv = b[t * ri];
+                acc[t].x = fmaf(bv.x, xv.x, acc[t].x);
+                acc[t].x = fmaf(-bv.y, xv.y, acc[t].x);
+                acc[t].y = fmaf(bv.x, xv.y, acc[t].y);
+                acc[t].y = fmaf(bv.y, xv.x, acc[t].y);
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < RO; ++t) op[(int64_t)t * nc] = acc[t];
+}
+
+// blk: NC RO x ri blocks per output pair, nc columns (2..32); chunks of B
+// pairs; ngroups groups of Gw consumer warps (ngroups Gw <= kXbWarps) with sg
+// stages each.  Chunk it of this CTA goes to group it % ngroups, as its chunk
+// j = it / ngroups, in stage (it % ngroups) sg + j % sg, phase j / sg.
+template <int RO, bool SW>
+__global__ void __launch_bounds__((kXbWarps + 1) * 32, 1)
+    kx_level_bulk(const float2* blk, const float2* in, float2* out, int L, int l, int ri, int nc, int64_t N, int B,
+                  int Gw, int ngroups, int sg, int* status)
+{
+    constexpr int NC = SW ? 1 : 2;
+    extern __shared__ __align__(16) unsigned char xsm[];
+    __shared__ __align__(8) unsigned long long full[kXbMaxStages], empty[kXbMaxStages];
+    __shared__ int s_abort;
+    __shared__ long long s_nxt[kXbWarps];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nb = NC * RO * ri;                                 // block entries per pair
+    const size_t stage_elems = (size_t)B * nb + (size_t)NC * B * ri * nc;
+    const int64_t nchunks = (N + B - 1) / B;
+    const int stages = ngroups * sg;
+    float2* sbase = reinterpret_cast<float2*>(xsm);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(xb_smem(&full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(xb_smem(&empty[s])), "r"(Gw));
+        }
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    if (w == 0) {
+        // producer: one lane issues the copies.  Each group's chunks go in the
+        // group's order, but the groups are served independently: a round
+        // visits every group and issues its next chunk if the stage it needs
+        // is free, so a slow group does not hold up the others' copies.
+        if (lane == 0) {
+            long long* nxt = s_nxt;                     // next chunk (j) of each group
+            for (int g = 0; g < ngroups; ++g) nxt[g] = 0;
+            int idle = 0;
+            bool left = true;
+            while (left && !*(volatile int*)&s_abort) {
+                left = false;
+                bool issued = false;
+                for (int g = 0; g < ngroups; ++g) {
+                    const int64_t j = nxt[g];
+                    const int64_t c = blockIdx.x + ((int64_t)g + j * ngroups) * gridDim.x;
+                    if (c >= nchunks) continue;
+                    left = true;
+                    const int s = g * sg + (int)(j % sg);
+                    const unsigned n = (unsigned)(j / sg);
+                    if (n > 0 && !xb_test(xb_smem(&empty[s]), (n - 1) & 1)) continue;
+                    const int64_t p0 = c * B;
+                    const int64_t np = min((int64_t)B, N - p0);
+                    const int64_t qlo = xb_q0<SW>(p0, L, l), qhi = xb_q0<SW>(p0 + np - 1, L, l) + NC;
+                    const unsigned bb = (unsigned)(np * nb * sizeof(float2));
+                    const unsigned ib = (unsigned)((qhi - qlo) * ri * nc * sizeof(float2));
+                    float2* sb = sbase + (size_t)s * stage_elems;
+                    const unsigned fb = xb_smem(&full[s]);
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(bb + ib)
+                                 : "memory");
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::
+                            "r"(xb_smem(sb)),
+                        "l"(blk + p0 * nb), "r"(bb), "r"(fb)
+                        : "memory");
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::
+                            "r"(xb_smem(sb + (size_t)B * nb)),
+                        "l"(in + qlo * ri * nc), "r"(ib), "r"(fb)
+                        : "memory");
+                    nxt[g] = j + 1;
+                    issued = true;
+                }
+                if (left && !issued) {
+                    if (++idle > kXbPolls) {
+                        if (status) atomicExch(status, 1);
+                        atomicExch(&s_abort, 1);
+                        break;
+                    }
+                    __nanosleep(kXbSleepNs);
+                } else {
+                    idle = 0;
+                }
+            }
+            // the last copies of every stage land before the CTA may exit
+            for (int g = 0; g < ngroups; ++g)
+                for (int64_t j = nxt[g] > sg ? nxt[g] - sg : 0; j < nxt[g]; ++j)
+                    if (!xb_wait(xb_smem(&full[g * sg + (int)(j % sg)]), (unsigned)(j / sg) & 1) && status)
+                        atomicExch(status, 1);
+        }
+        return;
+    }
+    // consumers: group g = (w - 1) / Gw computes chunks g, g + ngroups, ...;
+    // a warp holds PW = 32 / nc pairs, nc lanes each (lane: one column); warp
+    // gw of the group computes pairs gw PW + k, gw PW + k + Gw PW, ...
+    const int g = (w - 1) / Gw, gw = (w - 1) - g * Gw;
+    if (g >= ngroups) return;
+    const int PW = 32 / nc, pk = lane / nc, col = lane - pk * nc;
+    for (int64_t it = g, j = 0;; it += ngroups, ++j) {
+        const int64_t c = blockIdx.x + it * gridDim.x;
+        if (c >= nchunks) break;
+        const int s = g * sg + (int)(j % sg);
+        const unsigned n = (unsigned)(j / sg);
+        if (!xb_wait(xb_smem(&full[s]), n & 1)) {
+            if (status) atomicExch(status, 1);
+            atomicExch(&s_abort, 1);
+            break;
+        }
+        const int64_t p0 = c * B;
+        const int64_t qlo = xb_q0<SW>(p0, L, l);
+        const float2* sb = sbase + (size_t)s * stage_elems;
+        const int np = (int)min((int64_t)B, N - p0);
+        if (pk < PW)
+            for (int b = gw * PW + pk; b < np; b += Gw * PW) {
+                const int64_t p = p0 + b;
+                xb_col<RO, NC>(sb + (size_t)b * nb, sb + (size_t)B * nb + (xb_q0<SW>(p, L, l) - qlo) * ri * nc + col,
+                               out + p * RO * nc + col, ri, nc);
+            }
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(xb_smem(&empty[s])) : "memory");
+        if (*(volatile int*)&s_abort) break;
+    }
+}
+
+template <int RO, bool SW>
+static bool launch_level_bulk_r(const float2* blk, const float2* in, float2* out, int L, int l, int ri, int nc,
+                                int64_t N, int B, int Gw, int ngroups, int sg, size_t smem, int* status,
+                                cudaStream_t st)
+{
+    int dev = 0, nsm = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (smem > (size_t)optin) return false;
-    static bool done[64] = {false};
-    if (dev < 0 || dev >= 64 || !done[dev]) {
-        cudaFuncSetAttribute(kx_level_wp<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-        if (dev >= 0 && dev < 64) done[dev] = true;
+    // the kernel's static shared memory (barriers, counters) is queried once per
+    // device, and the dynamic limit raised to what remains of the opt-in size
+    static size_t static_smem[64] = {0};
+    if (dev < 0 || dev >= 64) return false;
+    if (!static_smem[dev]) {
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, kx_level_bulk<RO, SW>) != cudaSuccess ||
+            cudaFuncSetAttribute(kx_level_bulk<RO, SW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        static_smem[dev] = fa.sharedSizeBytes > 0 ? fa.sharedSizeBytes : 1;
     }
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kx_level_wp<cd>, kXWarps * 32, smem) != cudaSuccess ||
-        occ < 1) {
-        cudaGetLastError();
-        occ = 1;
-    }
-    const int64_t blocks = std::min<int64_t>((N + kXWarps - 1) / kXWarps, (int64_t)nsm * occ);
-    kx_level_wp<cd><<<(unsigned)blocks, kXWarps * 32, smem, st>>>(blk, in, out, L, l, ro, ri, nc, N, slice);
+    if (smem + static_smem[dev] > (size_t)optin) return false;
+    const int64_t blocks = std::min<int64_t>((N + B - 1) / B, (int64_t)nsm);
+    kx_level_bulk<RO, SW><<<(unsigned)blocks, (kXbWarps + 1) * 32, smem, st>>>(blk, in, out, L, l, ri, nc, N, B, Gw,
+                                                                                ngroups, sg, status);
     return true;
+}
+
+// Launch of kx_level_bulk for a level (SW false: two ro x ri blocks per
+// output pair) or the forward switch (SW true: one block, input pair p), for
+// 2..32 columns and ranks up to 16.  Chunks of B pairs (a power of two, at
+// least 2, at most kXbMaxPairs) of at most kXbChunkBytes bytes; groups of
+// Gw = min(ceil(B / PW), kXbMaxGroupWarps) warps (PW = 32 / nc pairs per warp,
+// a lane loops over the chunk's pairs), each
+// with two stages, as many groups as the warps and kXbSmemBudget allow.  One
+// CTA per SM.  false when the shapes are outside its limits (then the caller
+// runs another kernel).
+template <bool SW>
+static bool launch_level_bulk(const float2* blk, const float2* in, float2* out, int L, int l, int ro, int ri, int nc,
+                              int64_t N, int* status, cudaStream_t st)
+{
+    if (nc < 2 || nc > 32 || ro < 1 || ri < 1 || ro > 16 || ri > 16 || N < 2) return false;
+    const int NC = SW ? 1 : 2;
+    const size_t pair_bytes = sizeof(float2) * ((size_t)NC * ro * ri + (size_t)NC * ri * nc);
+    const int PW = 32 / nc;
+    int B = 2;
+    while (2 * B * pair_bytes <= (size_t)kXbChunkBytes && 2 * B <= N && 2 * B <= kXbMaxPairs) B *= 2;
+    const int Gw = std::min((B + PW - 1) / PW, kXbMaxGroupWarps);
+    if (Gw > kXbWarps) return false;
+    const size_t stage_bytes = (size_t)B * pair_bytes;
+    const int sg = 2;
+    const int ngroups =
+        (int)std::min<size_t>(kXbWarps / Gw, std::min<size_t>(kXbMaxStages, kXbSmemBudget / stage_bytes) / sg);
+    if (ngroups < 1) return false;
+    const size_t smem = (size_t)ngroups * sg * stage_bytes;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (smem + 1024 > (size_t)optin) return false;   // the kernel's own barriers and counters
+#define XB_RO(R) \
+    case R: return launch_level_bulk_r<R, SW>(blk, in, out, L, l, ri, nc, N, B, Gw, ngroups, sg, smem, status, st);
+    switch (ro) {
+        XB_RO(1) XB_RO(2) XB_RO(3) XB_RO(4) XB_RO(5) XB_RO(6) XB_RO(7) XB_RO(8)
+        XB_RO(9) XB_RO(10) XB_RO(11) XB_RO(12) XB_RO(13) XB_RO(14) XB_RO(15) XB_RO(16)
+    default: return false;
+    }
+#undef XB_RO
 }
 
 template <typename cd>
@@ -417,11 +647,16 @@ static int explicit_apply_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cud
         prof_mark(p, st, IBF_K_EXPLICIT_INIT);
         for (int l = 1; l <= L; ++l) {
             const int ro = rank_out(p, l), ri = rank_in(p, l);
-            // warp per pair where the level is memory-bound (complex64) and the
-            // pair has enough outputs for a warp; FP64 levels are bound by the
-            // FP64 pipe and keep one thread per output entry
+            // complex64 levels are memory-bound: the bulk-copy pipeline (up to 32
+            // columns, ranks up to 16), else a warp per pair (more columns);
+            // FP64 levels are bound by the FP64 pipe and keep one thread per
+            // output entry, as do calls with fewer than kXMinCols columns
             const bool warp = sizeof(cd) == sizeof(float2) && nc >= kXMinCols;
-            if (warp && nc <= kXPipeCols && launch_level_wp<cd>((const cd*)p->eblk[l], a, b, L, l, ro, ri, nc, N, st)) {
+            bool bulk = false;
+            if constexpr (std::is_same<cd, float2>::value)
+                bulk = warp && launch_level_bulk<false>((const float2*)p->eblk[l], a, b, L, l, ro, ri, nc, N,
+                                                        p->d_status, st);
+            if (bulk) {
             } else if (warp && ro <= kXRmax && ri <= kXRmax)
                 kx_level_w<cd><<<(unsigned)((N + kXWarps - 1) / kXWarps), kXWarps * 32, xlevel_smem<cd>(), st>>>(
                     (const cd*)p->eblk[l], a, b, L, l, ro, ri, nc, N);
@@ -430,7 +665,11 @@ static int explicit_apply_t(ibf_plan* p, const void* gv, void* uv, int nrhs, cud
             prof_mark(p, st, IBF_K_EXPLICIT_LEVEL);
             std::swap(a, b);
             if (l == h) {
-                kx_switch<<<nb(N * mr * nc), 256, 0, st>>>((const cd*)p->eM, a, b, mr, mc, nc, N, 0);
+                bool bulk_sw = false;
+                if constexpr (std::is_same<cd, float2>::value)
+                    bulk_sw = nc >= kXMinCols && launch_level_bulk<true>((const float2*)p->eM, a, b, L, h, mr, mc, nc,
+                                                                         N, p->d_status, st);
+                if (!bulk_sw) kx_switch<<<nb(N * mr * nc), 256, 0, st>>>((const cd*)p->eM, a, b, mr, mc, nc, N, 0);
                 prof_mark(p, st, IBF_K_EXPLICIT_SWITCH);
                 std::swap(a, b);
             }

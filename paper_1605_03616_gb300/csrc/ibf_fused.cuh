@@ -969,11 +969,11 @@ static int fused_run(ibf_plan* p, const void* vin, void* vout, int nrhs, bool ad
             int rc;
             const TcOps* tb = use_tc ? &tcb : nullptr;
             if (!adj)
-                rc = ch.kind == 0 ? launch_one<Real, RP, false, 0>(P, ngroups, st, tb, p->d_tcstatus)
-                                  : launch_one<Real, RP, false, 1>(P, ngroups, st, tb, p->d_tcstatus);
+                rc = ch.kind == 0 ? launch_one<Real, RP, false, 0>(P, ngroups, st, tb, p->d_status)
+                                  : launch_one<Real, RP, false, 1>(P, ngroups, st, tb, p->d_status);
             else
-                rc = ch.kind == 0 ? launch_one<Real, RP, true, 0>(P, ngroups, st, tb, p->d_tcstatus)
-                                  : launch_one<Real, RP, true, 1>(P, ngroups, st, tb, p->d_tcstatus);
+                rc = ch.kind == 0 ? launch_one<Real, RP, true, 0>(P, ngroups, st, tb, p->d_status)
+                                  : launch_one<Real, RP, true, 1>(P, ngroups, st, tb, p->d_status);
             if (rc) return rc;
             prof_mark(p, st, ch.kind == 0 ? IBF_K_FUSED_H : IBF_K_FUSED_G);
             cur ^= 1;

@@ -39,7 +39,8 @@ struct ibf_plan {
     // plan after its arguments were accepted, or IBF_ERR_TIMEOUT from a
     // persistent batch holding the plan; read and cleared by ibf_plan_status
     mutable int sticky = 0;
-    int* d_tcstatus = nullptr;   // IBF_C64_TF32X3: device word set when a tensor-core wait expires
+    int* d_status = nullptr;   // device word set when a bounded wait expires (tensor-core levels of
+                               // IBF_C64_TF32X3, bulk-copy levels of complex64 explicit forms)
 
     // Chebyshev grid on [-1/2,1/2] and the two child-to-parent Lagrange
     // transfer matrices T_c[t][s] = M_t((2c-1)/4 + z_s/2)   (Sec. 2.1)

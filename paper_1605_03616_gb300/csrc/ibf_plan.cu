@@ -646,13 +646,13 @@ extern "C" int ibf_plan_create_ex(int phase_id, int d, int64_t N, int r, int dty
             return rc;
         }
     p->ws_bytes = 2 * wsb;
-    if (dtype == IBF_C64_TF32X3) {
-        // status word of the tensor-core waits (ibf_plan_status)
-        if ((rc = dalloc(p, (void**)&p->d_tcstatus, sizeof(int), false))) {
+    if (dtype == IBF_C64_TF32X3 || (dtype == IBF_C64_FP32 && form != IBF_FORM_STRUCTURED)) {
+        // status word of the bounded device-side waits (ibf_plan_status)
+        if ((rc = dalloc(p, (void**)&p->d_status, sizeof(int), false))) {
             free_plan(p);
             return rc;
         }
-        cudaMemset(p->d_tcstatus, 0, sizeof(int));
+        cudaMemset(p->d_status, 0, sizeof(int));
     }
     if (form == IBF_FORM_STRUCTURED) {
         fused_choose_shape(p);
@@ -713,13 +713,13 @@ extern "C" int ibf_apply_adjoint(ibf_plan* p, const void* y, void* g, int nrhs, 
 extern "C" int ibf_plan_status(ibf_plan* p)
 {
     if (!p) return set_error(IBF_ERR_INVALID, "plan is NULL");
-    if (p->d_tcstatus) {
-        // tensor-core plans: a bounded wait that expired on the device
+    if (p->d_status) {
+        // plans whose kernels wait on mbarriers: a bounded wait that expired
         int dev = 0;
-        if (cudaMemcpy(&dev, p->d_tcstatus, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        if (cudaMemcpy(&dev, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
             return set_error(IBF_ERR_CUDA, "plan status: reading the device status word failed");
         if (dev) {
-            cudaMemset(p->d_tcstatus, 0, sizeof(int));
+            cudaMemset(p->d_status, 0, sizeof(int));
             plan_note(p, IBF_ERR_TIMEOUT);
         }
     }

@@ -127,6 +127,15 @@ def test_sweep_in_matches_oracle_and_keeps_the_operator(ibf, phase, N, r, r0, nr
     ("optimal", O.PHASE_FIO1D, 2048, 12, 9, 2),
     ("explicit", O.PHASE_FIO1D, 1024, 9, 0, 5),
     ("explicit", O.PHASE_NUFFT, 512, 7, 0, 1),
+    # the bulk-copy level kernel (4..32 columns): partial chunks at N = 16,
+    # 8 / 12 / 16 / 24 columns, sweep-in ranks 1..9, and 40 columns (the
+    # warp-per-pair kernel)
+    ("explicit", O.PHASE_FIO1D, 16, 5, 0, 4),
+    ("optimal_in", O.PHASE_FIO1D, 2048, 12, 9, 8),
+    ("optimal", O.PHASE_FIO1D, 1024, 9, 6, 12),
+    ("explicit", O.PHASE_NUFFT, 1024, 9, 0, 16),
+    ("explicit", O.PHASE_FIO1D, 512, 7, 0, 24),
+    ("explicit", O.PHASE_FIO1D, 256, 7, 0, 40),
 ])
 def test_fp32_explicit_and_optimal_forms(ibf, form, phase, N, r, r0, nrhs):
     """FP32 plans of the explicit and optimal forms: factors built (and
@@ -157,5 +166,6 @@ def test_fp32_explicit_and_optimal_forms(ibf, form, phase, N, r, r0, nrhs):
           % (form, phase, N, r, r0, ef, ea, tol, O.rel_l2(u32, u64), O.rel_l2(g32, g64)))
     assert ef < tol and ea < tol
     assert O.rel_l2(u32, u64) < 1e-5 and O.rel_l2(g32, g64) < 1e-5
+    assert p32.status() == 0          # no bounded device-side wait expired
     p32.close()
     p64.close()
