@@ -414,14 +414,13 @@ int ibf_plan_query(const ibf_plan* plan, int what, int64_t* value);
  * ibf_apply_amplitude, ibf_apply_static_scratch) returned after its
  * arguments were accepted (CUDA launch or copy failures), and
  * IBF_ERR_TIMEOUT when ibf_batch_status finds an expired wait in a batch
- * holding the plan, or when a bounded wait of the tensor-core levels of an
- * IBF_C64_TF32X3 plan expired on the device.  Argument errors are returned
- * by the call itself and are not recorded.  Returns that status (IBF_OK if
- * none) and resets it to IBF_OK; IBF_ERR_INVALID for a NULL plan.  No CUDA
- * call except, for IBF_C64_TF32X3 plans, one synchronous read (and reset) of
- * the device status word.  This replaces the survey's device-side per-plan status:
- * the only device-side waits are those of the persistent batch, whose status
- * word belongs to the batch.
+ * holding the plan, or when a bounded device-side wait of the plan's own
+ * kernels expired (the tensor-core levels of an IBF_C64_TF32X3 plan, the
+ * bulk-copy levels of a complex64 explicit or optimal plan).  Argument
+ * errors are returned by the call itself and are not recorded.  Returns that
+ * status (IBF_OK if none) and resets it to IBF_OK; IBF_ERR_INVALID for a
+ * NULL plan.  No CUDA call except, for the plans named above, one
+ * synchronous read (and reset) of the device status word.
  */
 int ibf_plan_status(ibf_plan* plan);
 
