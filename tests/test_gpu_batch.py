@@ -141,6 +141,31 @@ def test_persistent_single_launch_matches_oracle(ibf, adjoint):
         assert e < 1e-5, N
 
 
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_persistent_packed_items_match_oracle(ibf, adjoint):
+    """Narrow and shallow plans: a persistent item runs several blocks side by
+    side (1, 2 and 3 columns: tiles of 1, 2 and 4 columns, groups of fewer
+    than 32 threads on a named barrier; N = 2^6 leaves items with spare
+    groups), next to a 40-column plan (two 32-column tiles, one block per
+    item).  Forward and adjoint against the oracle's preliminary IBF."""
+    Ns, nrhs = [1 << 6, 1 << 7, 1 << 9, 1 << 10], [1, 2, 3, 40]
+    rng = W.rng(730 + adjoint)
+    plans = [ibf.Plan(ibf.PHASE_FIO1D, N, 9, ibf.C64_FP32, max_nrhs=k) for N, k in zip(Ns, nrhs)]
+    ins = [torch.from_numpy(W.complex_normal((k, N), rng, dtype=np.complex64)).cuda() for N, k in zip(Ns, nrhs)]
+    outs = [torch.full_like(t, float("nan")) for t in ins]
+    batch = ibf.Batch(plans, ins, outs, adjoint=adjoint)
+    batch.apply_persistent()
+    torch.cuda.synchronize()
+    assert batch.status() == 0
+    fn = O.ibf_adjoint_1d if adjoint else O.ibf_apply_1d
+    for N, g, u in zip(Ns, ins, outs):
+        ref = fn(O.PHASE_FIO1D, N, 9, W.uniform_x(N), g.cpu().numpy().T.astype(np.complex128))
+        e = O.rel_l2(u.cpu().numpy().T, ref)
+        print("\npersistent packed %s N=%d nrhs=%d: %.3e vs oracle" % ("adjoint" if adjoint else "forward", N,
+                                                                       g.shape[0], e))
+        assert e < 1e-5, N
+
+
 def test_persistent_wait_expires_without_hanging(ibf):
     """A dependency that is never satisfied (test hook) makes the bounded waits
     run out: the kernel returns, the batch reports IBF_ERR_TIMEOUT, and the
