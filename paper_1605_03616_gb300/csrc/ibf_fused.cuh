@@ -419,7 +419,9 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
     // a Lambda tile read through asynchronous copies: the table copies go out
     // with it, one wait and one barrier for both
     // (g and the V^0 rows, read only, go the same way in every mode)
-    const bool early = (P.pro == PRO_LAMBDA && !COH) || P.pro == PRO_V;
+    // (the tables are read-only during a launch, so the persistent form, whose
+    // tile loads bypass L1, issues them early too)
+    const bool early = P.pro == PRO_LAMBDA || P.pro == PRO_V;
     if (early) fused_stage_tables<Real, RP>(P, i0, jb, k, dsm);
 
     // ---------------------------------------------------------------- load
