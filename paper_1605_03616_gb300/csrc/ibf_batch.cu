@@ -71,6 +71,10 @@ struct PersistArgs {
 
 // Persistent form: 256 threads per CTA (fusion depth at most 4 with 32-column
 // tiles), as many CTAs as fit on the device at once.
+// items a CTA claims at a time: consecutive items mostly share a descriptor,
+// so the lookup, publish and dependency check run once per run of items
+constexpr int kPersistRun = 8;
+
 template <typename Real>
 struct PersistTraits {
     static constexpr int kThreads = 256;
@@ -87,8 +91,9 @@ __device__ __noinline__ void persist_item(const FusedDesc& d, int64_t blk, unsig
     fused_body<Real, RP, ADJ, KIND, 32, true>(c_eo<Real, RP>, d, blk, smraw);
 }
 
-// Each CTA takes items from the shared counter in order (the next item is
-// claimed while the current one runs, hiding the atomic's latency).  An item
+// Each CTA takes runs of kPersistRun consecutive items from the shared counter
+// in order (the next run is claimed while the current one runs, hiding the
+// atomic's latency).  An item
 // of a descriptor with a dependency may start once every item of that
 // dependency is done; a CTA checks this once per run of items of the same
 // descriptor.  Finished items are published (fence, then one atomic add per
@@ -105,59 +110,67 @@ __global__ void __launch_bounds__(PersistTraits<Real>::kThreads, PersistTraits<R
     int cur = -1;                       // descriptor of the current run of items
     int64_t cur_lo = 0, cur_hi = 0;     // its item range
     int pending = 0;                    // thread 0: finished items of cur not yet published
-    if (threadIdx.x == 0) s_item[0] = (long long)atomicAdd(A.next, 1ULL);
+    if (threadIdx.x == 0) s_item[0] = (long long)atomicAdd(A.next, (unsigned long long)kPersistRun);
     __syncthreads();
-    for (int it = 0;; ++it) {
-        const long long item = s_item[it & 1];
-        if (item >= A.total) break;
-        if (item < cur_lo || item >= cur_hi) {
-            if (cur >= 0) {
-                __threadfence();   // this thread's outputs are visible device-wide ...
-                __syncthreads();   // ... for every thread of the block ...
-                if (threadIdx.x == 0 && pending) atomicAdd(A.done + cur, pending);   // ... then counted
-                pending = 0;
-            }
-            int lo = 0, hi = A.n - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (A.start[mid] <= item)
-                    lo = mid;
-                else
-                    hi = mid - 1;
-            }
-            cur = lo;
-            cur_lo = A.start[lo];
-            cur_hi = lo + 1 < A.n ? A.start[lo + 1] : A.total;
-            const int dep = A.dep[lo];
-            if (dep >= 0) {
-                if (threadIdx.x == 0) {
-                    long long spins = 0;
-                    int ok = 1;
-                    while (atomicAdd(A.done + dep, 0) < A.need[lo]) {
-                        if (++spins > A.max_spin || *(volatile int*)A.status) {
-                            ok = 0;
-                            break;
-                        }
-                        __nanosleep(200);
-                    }
-                    if (!ok) atomicExch(A.status, 1);
-                    __threadfence();
-                    s_stop = !ok;
+    bool stop = false;
+    for (int it = 0; !stop; ++it) {
+        const long long base = s_item[it & 1];
+        if (base >= A.total) break;
+        // claim the next run while this one runs
+        if (threadIdx.x == 0) s_item[(it + 1) & 1] = (long long)atomicAdd(A.next, (unsigned long long)kPersistRun);
+        const long long end = min(base + (long long)kPersistRun, (long long)A.total);
+        for (long long item = base; item < end; ++item) {
+            if (item < cur_lo || item >= cur_hi) {
+                if (cur >= 0) {
+                    __threadfence();   // this thread's outputs are visible device-wide ...
+                    __syncthreads();   // ... for every thread of the block ...
+                    if (threadIdx.x == 0 && pending) atomicAdd(A.done + cur, pending);   // ... then counted
+                    pending = 0;
                 }
-                __syncthreads();
-                if (s_stop) break;
+                int lo = cur > 0 ? cur : 0, hi = A.n - 1;   // items only increase
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (A.start[mid] <= item)
+                        lo = mid;
+                    else
+                        hi = mid - 1;
+                }
+                cur = lo;
+                cur_lo = A.start[lo];
+                cur_hi = lo + 1 < A.n ? A.start[lo + 1] : A.total;
+                const int dep = A.dep[lo];
+                if (dep >= 0) {
+                    if (threadIdx.x == 0) {
+                        long long spins = 0;
+                        int ok = 1;
+                        while (atomicAdd(A.done + dep, 0) < A.need[lo]) {
+                            if (++spins > A.max_spin || *(volatile int*)A.status) {
+                                ok = 0;
+                                break;
+                            }
+                            __nanosleep(200);
+                        }
+                        if (!ok) atomicExch(A.status, 1);
+                        __threadfence();
+                        s_stop = !ok;
+                    }
+                    __syncthreads();
+                    if (s_stop) {
+                        stop = true;
+                        break;
+                    }
+                }
             }
+            const FusedDesc& d = A.descs[cur];
+            const int64_t blk = item - cur_lo;
+            // every descriptor of the persistent form uses 32-column tiles
+            if (d.kind == 0)
+                persist_item<Real, RP, ADJ, 0>(d, blk, smraw);
+            else
+                persist_item<Real, RP, ADJ, 1>(d, blk, smraw);
+            if (threadIdx.x == 0) ++pending;
+            __syncthreads();   // shared memory and the claimed items change hands
         }
-        if (threadIdx.x == 0) s_item[(it + 1) & 1] = (long long)atomicAdd(A.next, 1ULL);
-        const FusedDesc& d = A.descs[cur];
-        const int64_t blk = item - cur_lo;
-        // every descriptor of the persistent form uses 32-column tiles
-        if (d.kind == 0)
-            persist_item<Real, RP, ADJ, 0>(d, blk, smraw);
-        else
-            persist_item<Real, RP, ADJ, 1>(d, blk, smraw);
-        if (threadIdx.x == 0) ++pending;
-        __syncthreads();   // shared memory and the claimed item change hands
     }
     __threadfence();
     __syncthreads();
