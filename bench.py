@@ -861,22 +861,27 @@ def run_gpu(a):
     def e2e_step():
         # ibf_apply_host: chunked copies in and out overlap the apply; the
         # inputs are host-written, so a step's copy-in may overlap the
-        # previous step's last apply (IBF_HOST_PIPELINE)
-        plan.apply_host(gh, uh, stream=stream, pipeline=True)
+        # previous step's last apply (IBF_HOST_PIPELINE), and a step's last
+        # copy-out runs under the next step's applies (IBF_HOST_DEFER; the
+        # flush after the last step orders the stream after every copy-out)
+        plan.apply_host(gh, uh, stream=stream, pipeline=True, defer=True)
 
     for _ in range(max(1, a.warmup)):
         e2e_step()
+    plan.host_flush(stream)
     torch.cuda.synchronize()
     barrier()
     e0.record(stream)
     for _ in range(a.steps):
         e2e_step()
+    plan.host_flush(stream)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dist if world > 1 else None, dev)
     e2e = {"value": job_throughput(nrhs, a.steps, world, e2e_ms), "unit": "vectors/s",
            "h2d_bytes_per_step": int(gh.numel() * 8), "d2h_bytes_per_step": int(uh.numel() * 8),
-           "api": "ibf_apply_host (page-locked host buffers, copies overlapped with the apply, IBF_HOST_PIPELINE)"}
+           "api": "ibf_apply_host (page-locked host buffers, copies overlapped with the apply, IBF_HOST_PIPELINE | "
+                  "IBF_HOST_DEFER, ibf_host_flush after the last step)"}
 
     # ---- plain FP64 explicit single-vector form on the same GPU, and accuracy
     fp64 = None

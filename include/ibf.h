@@ -241,16 +241,30 @@ int ibf_apply_adjoint(ibf_plan* plan, const void* y, void* g, int nrhs, ibf_stre
  *   flags : IBF_HOST_ADJOINT (1) applies K^*; IBF_HOST_PIPELINE (2) declares
  *          that in_host is written only by the host (no earlier work queued
  *          on `stream` produces it).  Without it the first copy-in waits for
- *          all earlier work on `stream`; with it the copy-in waits only until
- *          the plan's staging buffers are free (the previous call's applies
- *          that read them, and its copy-outs when that call's out_host
+ *          all earlier work on `stream`; with it the copy-in of a chunk waits
+ *          only until its staging buffer is free (the previous call's last
+ *          apply that read it, and that call's copy-outs when its out_host
  *          overlaps this call's in_host), so back-to-back calls overlap the
  *          copy-in of one with the last apply of the other.  `stream` still
  *          completes only after every copy-out of the call.
+ *          IBF_HOST_DEFER (4), for a stream of calls: `stream` is not made to
+ *          wait for this call's copy-outs, so the last chunk's copy-out runs
+ *          under the next call's applies.  out_host is then complete once
+ *          `stream` has completed after a later call on the plan without the
+ *          flag, or after ibf_host_flush; a later call's applies wait for the
+ *          copy-outs still reading the staging buffer they write.
  */
-enum { IBF_HOST_ADJOINT = 1, IBF_HOST_PIPELINE = 2 };
+enum { IBF_HOST_ADJOINT = 1, IBF_HOST_PIPELINE = 2, IBF_HOST_DEFER = 4 };
 int ibf_apply_host(ibf_plan* plan, const void* in_host, void* out_host, int nrhs, int flags,
                    ibf_stream_t stream);
+
+/*
+ * ibf_host_flush -- orders `stream` after every copy-out of the plan's
+ * host applies still outstanding (those of calls made with IBF_HOST_DEFER):
+ * their out_host arrays are complete once `stream` has completed.  No effect
+ * when nothing is outstanding.  IBF_ERR_INVALID for a NULL plan.
+ */
+int ibf_host_flush(ibf_plan* plan, ibf_stream_t stream);
 
 /*
  * ibf_apply_amplitude -- u = A g (adjoint = 0) or g = A^* y (adjoint = 1) for

@@ -29,7 +29,7 @@ C64_FP32 = 1
 C64_BF16X3 = 2
 C64_TF32X3 = 3             # tensor-core G-form levels (tcgen05 kind::tf32, two-term splits)
 
-HOST_ADJOINT, HOST_PIPELINE = 1, 2   # ibf_apply_host flags
+HOST_ADJOINT, HOST_PIPELINE, HOST_DEFER = 1, 2, 4   # ibf_apply_host flags
 
 FORM_AUTO = 0
 FORM_EXPLICIT = 1
@@ -49,7 +49,7 @@ EXPORTS = ("ibf_plan_create", "ibf_plan_create_ex", "ibf_apply", "ibf_apply_adjo
            "ibf_apply_static_scratch", "ibf_batch_create", "ibf_batch_apply", "ibf_batch_query",
            "ibf_batch_destroy", "ibf_plan_autotune", "ibf_batch_apply_persistent", "ibf_batch_status",
            "ibf_batch_set_wait_limit", "ibf_batch_test_withhold", "ibf_apply_host", "ibf_apply_amplitude",
-           "ibf_plan_status")
+           "ibf_plan_status", "ibf_host_flush")
 
 BQ_LAUNCHES, BQ_WORKSPACE_BYTES, BQ_COUNT, BQ_PERSIST_ITEMS = range(4)
 
@@ -108,6 +108,7 @@ def load_library(path: str | None = None):
     L.ibf_apply_amplitude.argtypes = [P, P, P, I, P, P, I, I, P, I64, P]
     L.ibf_plan_profile_end.argtypes = [P, P, P, I, ctypes.POINTER(I)]
     L.ibf_plan_status.argtypes = [P]
+    L.ibf_host_flush.argtypes = [P, P]
     for nm in EXPORTS:
         getattr(L, nm).restype = I
     if path is None:
@@ -266,14 +267,17 @@ class Plan:
         _check(self._lib.ibf_apply_adjoint(self._p, ctypes.c_void_p(y_ptr), ctypes.c_void_p(g_ptr), nrhs,
                                            ctypes.c_void_p(stream_ptr)))
 
-    def apply_host(self, src, dst, adjoint: bool = False, stream=None, pipeline: bool = False) -> None:
+    def apply_host(self, src, dst, adjoint: bool = False, stream=None, pipeline: bool = False,
+                   defer: bool = False) -> None:
         """ibf_apply_host: `src` and `dst` are CPU tensors (or numpy arrays) of
         shape (nrhs, N), complex64 or complex128 to match the plan; page-locked
         tensors (`pin_memory()`) overlap the copies with the apply.  Queued on
         `stream` (default: the current CUDA stream); synchronise it before
         reading `dst`.  pipeline=True (IBF_HOST_PIPELINE) declares that `src`
         is written only by the host, so the copy-in may overlap the previous
-        call's last apply."""
+        call's last apply.  defer=True (IBF_HOST_DEFER) leaves the copy-outs
+        unordered with `stream` until a later call without it or
+        `host_flush`, so the last copy-out overlaps the next call's applies."""
         torch = _torch()
 
         def ptr(a):
@@ -282,8 +286,15 @@ class Plan:
         nrhs = int(src.shape[0]) if len(src.shape) == 2 else 1
         s = (stream or torch.cuda.current_stream()).cuda_stream
         _check(self._lib.ibf_apply_host(self._p, ctypes.c_void_p(ptr(src)), ctypes.c_void_p(ptr(dst)), nrhs,
-                                        (HOST_ADJOINT if adjoint else 0) | (HOST_PIPELINE if pipeline else 0),
-                                        ctypes.c_void_p(s)))
+                                        (HOST_ADJOINT if adjoint else 0) | (HOST_PIPELINE if pipeline else 0) |
+                                        (HOST_DEFER if defer else 0), ctypes.c_void_p(s)))
+
+    def host_flush(self, stream=None) -> None:
+        """ibf_host_flush: orders `stream` after the copy-outs of earlier
+        deferred host applies (their `dst` is complete once `stream` is)."""
+        torch = _torch()
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        _check(self._lib.ibf_host_flush(self._p, ctypes.c_void_p(s)))
 
     def apply_amplitude(self, v, alpha, beta, adjoint: bool = False, out=None, work=None, stream=None):
         """u = A g (or g = A^* y with adjoint=True) for the amplitude

@@ -84,6 +84,7 @@ struct ibf_plan {
     cudaEvent_t hst_ev[7] = {};   // start, h2d[2], apply[2], d2h[2]
     const void* hst_prev_out = nullptr;   // out_host of the previous call (IBF_HOST_PIPELINE)
     size_t hst_prev_bytes = 0;
+    bool hst_deferred = false;            // copy-outs not yet ordered before `stream` (IBF_HOST_DEFER)
     size_t factor_bytes = 0, ws_bytes = 0;
     int64_t nnz = 0;
     std::vector<void*> allocations;

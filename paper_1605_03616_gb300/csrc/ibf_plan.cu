@@ -763,7 +763,8 @@ extern "C" int ibf_apply_host(ibf_plan* p, const void* hin, void* hout, int nrhs
     if (!p) return set_error(IBF_ERR_INVALID, "plan is NULL");
     if (!hin || !hout) return set_error(IBF_ERR_INVALID, "NULL vector pointer");
     if (nrhs < 1) return set_error(IBF_ERR_INVALID, "nrhs must be >= 1");
-    if (flags & ~(IBF_HOST_ADJOINT | IBF_HOST_PIPELINE)) return set_error(IBF_ERR_INVALID, "unknown flag bits");
+    if (flags & ~(IBF_HOST_ADJOINT | IBF_HOST_PIPELINE | IBF_HOST_DEFER))
+        return set_error(IBF_ERR_INVALID, "unknown flag bits");
     const bool adjoint = flags & IBF_HOST_ADJOINT;
     const size_t esz = p->dtype == IBF_C128 ? 16 : 8;
     if (((uintptr_t)hin % esz) || ((uintptr_t)hout % esz)) return set_error(IBF_ERR_INVALID, "misaligned vector pointer");
@@ -778,12 +779,12 @@ extern "C" int ibf_apply_host(ibf_plan* p, const void* hin, void* hout, int nrhs
     cudaError_t e;
     const size_t total = col * (size_t)nrhs;
     const bool first = p->hst_prev_out == nullptr;
-    if ((flags & IBF_HOST_PIPELINE) && !first) {
-        // the copy-in waits only for the staging slots: the previous call's
-        // applies read them; if that call's output overlaps this input, its
-        // copy-outs too
-        cudaStreamWaitEvent(p->hst_in, app[0], 0);
-        cudaStreamWaitEvent(p->hst_in, app[1], 0);
+    const bool pipelined = (flags & IBF_HOST_PIPELINE) && !first;
+    if (pipelined) {
+        // the copy-in into slot s waits only for the previous call's last
+        // apply that read slot s (in the loop below), so the first chunk's
+        // copy-in runs under the previous call's last apply; if that call's
+        // output overlaps this input, it waits for its copy-outs too
         const char* po = (const char*)p->hst_prev_out;
         const char* ci = (const char*)hin;
         if (ci < po + p->hst_prev_bytes && po < ci + total) {
@@ -798,16 +799,19 @@ extern "C" int ibf_apply_host(ibf_plan* p, const void* hin, void* hout, int nrhs
     }
     p->hst_prev_out = hout;
     p->hst_prev_bytes = total;
+    // copy-outs of an earlier deferred call may still read the staging slots
+    // this call's first applies write
+    const bool after_deferred = p->hst_deferred;
     const int nch = (nrhs + ch - 1) / ch;
     for (int j = 0; j < nch; ++j) {
         const int s = j & 1, c0 = j * ch, nc = std::min(ch, nrhs - c0);
-        if (j >= 2) cudaStreamWaitEvent(p->hst_in, app[s], 0);
+        if (j >= 2 || pipelined) cudaStreamWaitEvent(p->hst_in, app[s], 0);
         if ((e = cudaMemcpyAsync(slot_in[s], (const char*)hin + col * c0, col * nc, cudaMemcpyHostToDevice,
                                  p->hst_in)) != cudaSuccess)
             return plan_note(p, cuda_error(e, "host apply: copy in"));
         cudaEventRecord(h2d[s], p->hst_in);
         cudaStreamWaitEvent(st, h2d[s], 0);
-        if (j >= 2) cudaStreamWaitEvent(st, d2h[s], 0);
+        if (j >= 2 || after_deferred) cudaStreamWaitEvent(st, d2h[s], 0);
         rc = adjoint ? ibf_apply_adjoint(p, slot_in[s], slot_out[s], nc, stream)
                      : ibf_apply(p, slot_in[s], slot_out[s], nc, stream);
         if (rc) return rc;
@@ -818,11 +822,31 @@ extern "C" int ibf_apply_host(ibf_plan* p, const void* hin, void* hout, int nrhs
             return plan_note(p, cuda_error(e, "host apply: copy out"));
         cudaEventRecord(d2h[s], p->hst_out);
     }
-    // `stream` completes only after every copy-out
-    cudaStreamWaitEvent(st, d2h[0], 0);
-    if (nch > 1) cudaStreamWaitEvent(st, d2h[1], 0);
+    if (flags & IBF_HOST_DEFER) {
+        // the copy-outs stay on the copy stream: the next call or
+        // ibf_host_flush orders `stream` after them
+        p->hst_deferred = true;
+    } else {
+        // `stream` completes only after every copy-out, earlier deferred ones
+        // included (both slots' latest copy-outs)
+        cudaStreamWaitEvent(st, d2h[0], 0);
+        cudaStreamWaitEvent(st, d2h[1], 0);
+        p->hst_deferred = false;
+    }
     e = cudaGetLastError();
     return e == cudaSuccess ? IBF_OK : plan_note(p, cuda_error(e, "host apply"));
+}
+
+extern "C" int ibf_host_flush(ibf_plan* p, ibf_stream_t stream)
+{
+    if (!p) return set_error(IBF_ERR_INVALID, "plan is NULL");
+    if (!p->hst_buf || !p->hst_deferred) return IBF_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStreamWaitEvent(st, p->hst_ev[5], 0);   // d2h of slot 0
+    cudaStreamWaitEvent(st, p->hst_ev[6], 0);   // d2h of slot 1
+    p->hst_deferred = false;
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? IBF_OK : plan_note(p, cuda_error(e, "host flush"));
 }
 
 extern "C" int ibf_plan_profile_begin(ibf_plan* p, int cap)

@@ -100,5 +100,44 @@ def test_host_apply_pipelined_calls(ibf):
     assert torch.equal(c1, ref1)
     assert torch.equal(c2, _device(plan, ref1.numpy()))
     lib = ibf.load_library()
-    assert lib.ibf_apply_host(plan._p, src[0].data_ptr(), dst[0].data_ptr(), 1, 4, None) == 1   # unknown flag
+    assert lib.ibf_apply_host(plan._p, src[0].data_ptr(), dst[0].data_ptr(), 1, 8, None) == 1   # unknown flag
+    plan.close()
+
+
+def test_host_apply_deferred_copy_outs(ibf):
+    """IBF_HOST_DEFER: a stream of calls whose last copy-outs are ordered with
+    the stream only by a later unflagged call or ibf_host_flush gives the
+    device apply's results bit for bit: separate outputs (3 chunks per call,
+    so both staging slots are reused across calls), a chain where one call's
+    output is the next call's input, an adjoint call, and both ways of
+    closing the stream."""
+    N, nrhs = 1 << 12, 70                      # chunks of 32, 32 and 6 columns
+    plan = ibf.Plan(ibf.PHASE_FIO1D, N, 9, ibf.C64_FP32, max_nrhs=64)
+    gs = [W.complex_normal((nrhs, N), W.rng(850 + i), dtype=np.complex64) for i in range(4)]
+    src = [torch.from_numpy(g).pin_memory() for g in gs]
+    dst = [torch.full_like(s, float("nan")).pin_memory() for s in src]
+    for i in range(4):
+        plan.apply_host(src[i], dst[i], pipeline=True, defer=True)
+    plan.host_flush()
+    torch.cuda.current_stream().synchronize()
+    for g, d in zip(gs, dst):
+        assert torch.equal(d, _device(plan, g))
+    # chain and adjoint under deferral, closed by an unflagged call
+    c1 = torch.full_like(src[0], float("nan")).pin_memory()
+    c2 = torch.full_like(src[0], float("nan")).pin_memory()
+    a1 = torch.full_like(src[0], float("nan")).pin_memory()
+    last = torch.full_like(src[0], float("nan")).pin_memory()
+    plan.apply_host(src[0], c1, pipeline=True, defer=True)
+    plan.apply_host(c1, c2, pipeline=True, defer=True)
+    plan.apply_host(src[1], a1, adjoint=True, pipeline=True, defer=True)
+    plan.apply_host(src[2], last, pipeline=True)
+    torch.cuda.current_stream().synchronize()
+    ref1 = _device(plan, gs[0])
+    assert torch.equal(c1, ref1)
+    assert torch.equal(c2, _device(plan, ref1.numpy()))
+    assert torch.equal(last, _device(plan, gs[2]))
+    assert torch.equal(a1, _device(plan, gs[1], adjoint=True))
+    lib = ibf.load_library()
+    assert lib.ibf_host_flush(None, None) == 1
+    assert lib.ibf_host_flush(plan._p, None) == 0      # nothing outstanding
     plan.close()

@@ -66,6 +66,7 @@ def test_argument_validation_without_gpu(lib):
     assert lib.ibf_apply(None, None, None, 1, None) == 1
     assert lib.ibf_apply_adjoint(None, None, None, 1, None) == 1
     assert lib.ibf_apply_host(None, None, None, 1, 0, None) == 1
+    assert lib.ibf_host_flush(None, None) == 1                                 # NULL plan, no CUDA call
     assert lib.ibf_apply_amplitude(None, None, None, 1, None, None, 1, 0, None, 0, None) == 1
     assert lib.ibf_plan_destroy(None) == 0
     v = ctypes.c_int64()
