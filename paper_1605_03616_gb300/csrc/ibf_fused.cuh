@@ -118,13 +118,13 @@ struct FusedParams {
 };
 
 // Elements of the shared-memory region after the Lambda tile: the staged
-// phase tables of the k levels (padded per-unit stride 4r+1), reused by the
-// epilogues for the switch blocks (padded stride r^2+1) and U^L rows, and by
-// the prologue for the V^0 rows.
+// phase tables of the k levels (per-unit stride 4r), reused by the epilogues
+// for the switch blocks (padded stride r^2+1) and U^L rows, and by the
+// prologue for the V^0 rows.
 __host__ __device__ __forceinline__ size_t fused_region_elems(int k, int RP)
 {
     const size_t G = (size_t)1 << k;
-    const size_t tables = (size_t)k * (G / 2) * (4 * RP + 1);
+    const size_t tables = (size_t)k * (G / 2) * (4 * RP);
     const size_t mblocks = G * ((size_t)RP * RP + 1);
     return tables > mblocks ? tables : mblocks;
 }
@@ -206,6 +206,35 @@ __device__ __forceinline__ void cp_async_elem(double2* dst, const double2* src, 
 }
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Layout of a unit's staged phase table (4r elements).  The unit's four
+// diagonals D_{a,c} (row ac = 2a + c) are stored as two interleaved pairs,
+// [p][t][w], so that one 16-byte shared load returns the two entries that a
+// level step uses together:
+//   H levels (KIND 0): pairs (D_00, D_10) and (D_01, D_11)
+//   G levels (KIND 1): pairs (D_00, D_01) and (D_10, D_11)
+// In both kinds the forward and the adjoint steps then read pair 0 at index t
+// and pair 1 at index r-1-t.  The unit stride 4r and every pair offset are
+// even, so with a 16-byte aligned table region every pair is 16-byte aligned.
+template <int RP, int KIND>
+__host__ __device__ __forceinline__ int tab_off(int ac, int t)
+{
+    const int p = KIND == 0 ? (ac & 1) : (ac >> 1);
+    const int w = KIND == 0 ? (ac >> 1) : (ac & 1);
+    return p * 2 * RP + 2 * t + w;
+}
+// the pair at q: q[0] and q[1] (one 16-byte load in single precision)
+__device__ __forceinline__ void ld_pair(const float2* q, float2& a, float2& b)
+{
+    const float4 v = *reinterpret_cast<const float4*>(q);
+    a = make_float2(v.x, v.y);
+    b = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void ld_pair(const double2* q, double2& a, double2& b)
+{
+    a = q[0];
+    b = q[1];
+}
+
 // Two-lane arithmetic on (re, im) pairs: Blackwell's packed FP32 instructions
 // (one issue slot for both lanes) in single precision, per-component double
 // operations otherwise.  Rounding is that of the per-component operations:
@@ -227,15 +256,16 @@ __device__ __forceinline__ double2 p2fma(double2 w, double2 x, double2 acc)
 namespace ibf {
 
 // Asynchronous copies of the phase tables of a fused block into dsm: every
-// unit of every fused level, [s-1][u][a][c][RP] with per-unit stride 4r+1 (the
-// CTA reads each entry once from global memory); one thread per (level, unit,
-// a, c) row of r contiguous entries.  Completed by cp_async_wait().
-template <typename Real, int RP>
+// unit of every fused level, [s-1][u] with per-unit stride 4r in the pair
+// layout of tab_off (the CTA reads each entry once from global memory); one
+// thread per (level, unit, a, c) row of r contiguous entries.  Completed by
+// cp_async_wait().
+template <typename Real, int RP, int KIND>
 __device__ __forceinline__ void fused_stage_tables(const FusedDesc& P, int64_t i0, int64_t jb, int k,
                                                    typename CT<Real>::T* dsm)
 {
     typedef typename CT<Real>::T cx;
-    constexpr int DS = 4 * RP + 1;
+    constexpr int DS = 4 * RP;
     const int L = P.L, l0 = P.l0;
     const int nunit = (1 << k) >> 1;
     const int rows_per_level = nunit * 4;
@@ -250,16 +280,16 @@ __device__ __forceinline__ void fused_stage_tables(const FusedDesc& P, int64_t i
         const int64_t C = (((jb << (k - s)) + (p0 >> s)) << 1) + (ac & 1);
         const int64_t ldC = 1LL << (L - l0 - s + 1);
         const cx* src = (const cx*)P.D[st1] + (ia * ldC + C) * RP;
-        cx* dst = dsm + (st1 * nunit + u) * DS + ac * RP;
+        cx* dst = dsm + (st1 * nunit + u) * DS + tab_off<RP, KIND>(ac, 0);
 #pragma unroll
-        for (int t = 0; t < RP; ++t) cp_async_elem(dst + t, src + t, true);
+        for (int t = 0; t < RP; ++t) cp_async_elem(dst + 2 * t, src + t, true);
     }
 }
 
 // The k butterfly levels of one block, in place in shared memory: sm holds
 // the 2^k positions of the Lambda tile (stride PS = r rt + 1), dsm the staged
-// phase tables [s-1][u][a][c][RP] (per-unit stride 4r+1).  Every level ends
-// with a barrier.
+// phase tables [s-1][u] (per-unit stride 4r, pair layout of tab_off).  Every
+// level ends with a barrier.
 template <typename Real, int RP, bool ADJ, int KIND, int RT>
 __device__ __forceinline__ void fused_levels(const FusedConsts<Real, RP>& C, int k, int rt_run, int ncol,
                                              typename CT<Real>::T* sm, const typename CT<Real>::T* dsm)
@@ -268,7 +298,7 @@ __device__ __forceinline__ void fused_levels(const FusedConsts<Real, RP>& C, int
     const int rt = RT ? RT : rt_run;
     const int PS = RP * rt + 1;
     const int G = 1 << k;
-    constexpr int DS = 4 * RP + 1;
+    constexpr int DS = 4 * RP;
     constexpr int HR = EO<RP>::HR, HQ = EO<RP>::HQ;
     constexpr bool ODD = RP & 1;
     const int nunit = G >> 1;
@@ -291,11 +321,12 @@ __device__ __forceinline__ void fused_levels(const FusedConsts<Real, RP>& C, int
                     const cx* x0p = sm + (p0 * PS + c);
                     const cx* x1p = sm + (p1 * PS + c);
                     const cx* du = dl + u * DS;
-                    // output a uses D_{a,q} (forward H) or conj(D_{q,a}) (adjoint G)
-                    const cx* d00 = du + (ADJ ? 0 : 0) * RP;
-                    const cx* d01 = du + (ADJ ? 2 : 1) * RP;
-                    const cx* d10 = du + (ADJ ? 1 : 2) * RP;
-                    const cx* d11 = du + 3 * RP;
+                    // output a uses D_{a,q} (forward H) or conj(D_{q,a}) (adjoint G):
+                    // d_{aq} below, with (d00, d10) the pair at s2 and (d01, d11)
+                    // the pair at r-1-s2 (tab_off: forward H pairs D_{0c}, D_{1c};
+                    // adjoint G, a G-kind table, pairs D_{c0}, D_{c1})
+                    const cx* pa = du;
+                    const cx* pb = du + 2 * RP;
                     cx we0[HR], wo0[HQ > 0 ? HQ : 1], we1[HR], wo1[HQ > 0 ? HQ : 1];
 #pragma unroll
                     for (int t = 0; t < HR; ++t) we0[t] = we1[t] = cz<cx>();
@@ -304,10 +335,13 @@ __device__ __forceinline__ void fused_levels(const FusedConsts<Real, RP>& C, int
 #pragma unroll
                     for (int s2 = 0; s2 < RP; ++s2) {
                         const cx xa = x0p[s2 * rt], xb = x1p[(RP - 1 - s2) * rt];
-                        const cx y00 = ADJ ? cmulc(d00[s2], xa) : cmul(d00[s2], xa);
-                        const cx y01 = ADJ ? cmulc(d01[RP - 1 - s2], xb) : cmul(d01[RP - 1 - s2], xb);
-                        const cx y10 = ADJ ? cmulc(d10[s2], xa) : cmul(d10[s2], xa);
-                        const cx y11 = ADJ ? cmulc(d11[RP - 1 - s2], xb) : cmul(d11[RP - 1 - s2], xb);
+                        cx d00, d10, d01, d11;
+                        ld_pair(pa + 2 * s2, d00, d10);
+                        ld_pair(pb + 2 * (RP - 1 - s2), d01, d11);
+                        const cx y00 = ADJ ? cmulc(d00, xa) : cmul(d00, xa);
+                        const cx y01 = ADJ ? cmulc(d01, xb) : cmul(d01, xb);
+                        const cx y10 = ADJ ? cmulc(d10, xa) : cmul(d10, xa);
+                        const cx y11 = ADJ ? cmulc(d11, xb) : cmul(d11, xb);
                         const cx pv0 = p2add(y00, y01), mv0 = p2sub(y00, y01);
                         const cx pv1 = p2add(y10, y11), mv1 = p2sub(y10, y11);
 #pragma unroll
@@ -363,6 +397,11 @@ __device__ __forceinline__ void fused_levels(const FusedConsts<Real, RP>& C, int
 #pragma unroll
                     for (int t = 0; t < RP; ++t) {
                         cx a0 = cz<cx>(), a1 = cz<cx>();
+                        // forward G: dA_q = D_{0,q}[t], dB_q = D_{1,q}[r-1-t];
+                        // adjoint H (an H-kind table): dA_q = D_{q,0}[t], dB_q = D_{q,1}[r-1-t]
+                        cx dA[2], dB[2];
+                        ld_pair(du + 2 * t, dA[0], dA[1]);
+                        ld_pair(du + 2 * RP + 2 * (RP - 1 - t), dB[0], dB[1]);
 #pragma unroll
                         for (int q = 0; q < 2; ++q) {
                             cx e = cz<cx>(), f = cz<cx>();
@@ -373,10 +412,8 @@ __device__ __forceinline__ void fused_levels(const FusedConsts<Real, RP>& C, int
                             // (T_0^T x_q)[t] and (T_1^T x_q)[RP-1-t]
                             const cx z0 = p2add(e, f), z1 = p2sub(e, f);
                             // forward G: output a uses D_{a,q}; adjoint H: output c uses conj(D_{q,c})
-                            const cx* dA = du + (ADJ ? (q * 2 + 0) : (0 * 2 + q)) * RP;
-                            const cx* dB = du + (ADJ ? (q * 2 + 1) : (1 * 2 + q)) * RP;
-                            cmacx<ADJ>(a0, dA[t], z0);
-                            cmacx<ADJ>(a1, dB[RP - 1 - t], z1);
+                            cmacx<ADJ>(a0, dA[q], z0);
+                            cmacx<ADJ>(a1, dB[q], z1);
                         }
                         o0[t * rt] = a0;
                         o1[(RP - 1 - t) * rt] = a1;
@@ -414,7 +451,7 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
     const int64_t jb = grp & ((1LL << nbj) - 1);
     const int64_t N = P.N;
 
-    constexpr int DS = 4 * RP + 1;   // per-unit stride of the staged tables, padded against bank conflicts
+    constexpr int DS = 4 * RP;   // per-unit stride of the staged tables (pair layout of tab_off)
     cx* dsm = sm + (size_t)G * PS;
     // a Lambda tile read through asynchronous copies: the table copies go out
     // with it, one wait and one barrier for both
@@ -422,7 +459,7 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
     // (the tables are read-only during a launch, so the persistent form, whose
     // tile loads bypass L1, issues them early too)
     const bool early = P.pro == PRO_LAMBDA || P.pro == PRO_V;
-    if (early) fused_stage_tables<Real, RP>(P, i0, jb, k, dsm);
+    if (early) fused_stage_tables<Real, RP, KIND>(P, i0, jb, k, dsm);
 
     // ---------------------------------------------------------------- load
     if (P.pro == PRO_V) {
@@ -514,7 +551,7 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
     // ------------------------------------------------- stage phase tables
     // (issued above together with the Lambda tile when the input is a tile)
     if (!early) {
-        fused_stage_tables<Real, RP>(P, i0, jb, k, dsm);
+        fused_stage_tables<Real, RP, KIND>(P, i0, jb, k, dsm);
         cp_async_wait();
         __syncthreads();
     }
@@ -835,7 +872,7 @@ static int fused_upload_consts(const ibf_plan* p)
 }
 
 // dynamic shared memory of one fused CTA: the Lambda tile plus the staged
-// phase tables of its k levels (padded per-unit stride 4r+1); a launch with
+// phase tables of its k levels (per-unit stride 4r); a launch with
 // the V^0 prologue also stages its g values and V^0 rows
 inline size_t fused_smem_bytes(int k, int rt, int RP, size_t esz, int pro = PRO_LAMBDA)
 {

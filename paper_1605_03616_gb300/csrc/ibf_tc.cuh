@@ -189,8 +189,9 @@ __device__ __forceinline__ void tc_teardown(TcCtx& t)
 }
 
 // One G-form butterfly level of the fused tile through the tensor cores: sm
-// holds the Lambda tile ([pos][t][col], stride PS = r rt + 1), du_base the
-// staged tables of this level ([u][a][c][RP], stride 4r+1).  Rounds of 128
+// holds the Lambda tile ([pos][t][col], stride PS = r rt + 1), dl the staged
+// tables of this level ([u], stride 4r, pair layout of tab_off for the level
+// kind: G for the forward form, H for the adjoint).  Rounds of 128
 // (unit, column) tasks; per round and input q: rows to tensor memory, five
 // MMAs per component, products back, diagonals applied.  All threads take
 // part in every round (the tensor-memory transfers are warp-collective).
@@ -200,7 +201,8 @@ __device__ __forceinline__ void tc_level_g(TcCtx& tc, int bit, int nunit, int rt
 {
     const int rt = RT ? RT : rt_run;
     const int PS = RP * rt + 1;
-    constexpr int DS = 4 * RP + 1;
+    constexpr int DS = 4 * RP;
+    constexpr int KIND = ADJ ? 0 : 1;
     const uint32_t lane = (uint32_t)(threadIdx.x & ~31) << 16;
     const int ntask = nunit * rt;
     for (int r0 = 0; r0 < ntask; r0 += kTcThreads) {
@@ -286,7 +288,8 @@ __device__ __forceinline__ void tc_level_g(TcCtx& tc, int bit, int nunit, int rt
                 tc_ld16(tc.tmem + lane + kTcDre + 16 * a, zr);
                 tc_ld16(tc.tmem + lane + kTcDim + 16 * a, zi);
                 tc_wait_ld();
-                const float2* dA = du + (ADJ ? (q * 2 + a) : (a * 2 + q)) * RP;
+                const int ac = ADJ ? (q * 2 + a) : (a * 2 + q);
+                const float2* dA = du + tab_off<RP, KIND>(ac, 0);
                 if (on) {
 #pragma unroll
                     for (int t = 0; t < RP; ++t) {
@@ -294,11 +297,11 @@ __device__ __forceinline__ void tc_level_g(TcCtx& tc, int bit, int nunit, int rt
                         if (a == 0) {
                             // input 0 is consumed: output 0 accumulates in its place
                             float2 y = q ? o0[t * rt] : make_float2(0.f, 0.f);
-                            cmacx<ADJ>(y, dA[t], z);
+                            cmacx<ADJ>(y, dA[2 * t], z);
                             o0[t * rt] = y;
                         } else {
                             if (q == 0) y1[t] = make_float2(0.f, 0.f);
-                            cmacx<ADJ>(y1[t], dA[t], z);
+                            cmacx<ADJ>(y1[t], dA[2 * t], z);
                         }
                     }
                 }
