@@ -452,6 +452,19 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
     const int64_t N = P.N;
 
     constexpr int DS = 4 * RP;   // per-unit stride of the staged tables (pair layout of tab_off)
+    // The persistent form (COH) runs every item of one level kind through one
+    // non-inlined body, so it compiles in only the prologues and epilogues a
+    // chunk of its kind can have (fewer live registers, fewer spills): the
+    // switch level h lies in [1, L-1] and no chunk spans it, so forward H
+    // chunks start with V^0 or a tile and end with the switch or a tile,
+    // forward G chunks end with U^L or a tile, adjoint G chunks start with
+    // U^L* or a tile and end with the switch or a tile, and adjoint H chunks
+    // end with V^0* or a tile.  The per-launch kernels keep every branch.
+    constexpr bool HAS_PRO_V = !COH || (!ADJ && KIND == 0);
+    constexpr bool HAS_PRO_UADJ = !COH || (ADJ && KIND == 1);
+    constexpr bool HAS_EPI_SWITCH = !COH || (!ADJ && KIND == 0) || (ADJ && KIND == 1);
+    constexpr bool HAS_EPI_U = !COH || (!ADJ && KIND == 1);
+    constexpr bool HAS_EPI_VADJ = !COH || (ADJ && KIND == 0);
     cx* dsm = sm + (size_t)G * PS;
     // a Lambda tile read through asynchronous copies: the table copies go out
     // with it, one wait and one barrier for both
@@ -462,7 +475,7 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
     if (early) fused_stage_tables<Real, RP, KIND>(P, i0, jb, k, dsm);
 
     // ---------------------------------------------------------------- load
-    if (P.pro == PRO_V) {
+    if (HAS_PRO_V && P.pro == PRO_V) {
         // forward, l0 = 0: Lambda^0_{0,j} = V^0-expansion of g(xi_j), j = jb 2^k + pos.
         // The block's g values ([c][pos]) and its V^0 rows (contiguous) are
         // staged after the table region, with the table copies in flight.
@@ -484,7 +497,7 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
 #pragma unroll
             for (int t = 0; t < RP; ++t) sm[pos * PS + t * rt + c] = cmul(vs[pos * RP + t], gv);
         }
-    } else if (P.pro == PRO_UADJ) {
+    } else if (HAS_PRO_UADJ && P.pro == PRO_UADJ) {
         // adjoint, top level L: Lambda^L_i[t] = sum_{n in leaf i} conj(U[n][t]) y[perm n]
         const cx* y = (const cx*)P.vin;
         const cx* U = (const cx*)P.Us;
@@ -594,7 +607,7 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
                 out[(pair * RP + t) * P.nc + col0 + c] = sm[pos * PS + t * rt + c];
             }
         }
-    } else if (P.epi == EPI_SWITCH) {
+    } else if (HAS_EPI_SWITCH && P.epi == EPI_SWITCH) {
         // forward: Lambda~ = M~' Lambda at level h; adjoint: Lambda = M~'^* Lambda~.
         // The CTA's G blocks of r x r are staged in the table region first.
         cx* out = (cx*)P.out;
@@ -679,7 +692,7 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
                 out[(pair * RP + t) * P.nc + col0 + c] = acc;
             }
         }
-    } else if (P.epi == EPI_U) {
+    } else if (HAS_EPI_U && P.epi == EPI_U) {
         // forward, level L: u(x_n) = sum_t U[n][t] Lambda^L_{leaf(n)}[t]
         cx* u = (cx*)P.vout;
         // the CTA's leaves are contiguous, so are their points [nb0, nb1);
@@ -709,7 +722,7 @@ __device__ __forceinline__ void fused_body(const FusedConsts<Real, RP>& C, const
                 u[P.perm[n] + N * (col0 + c)] = acc;
             }
         }
-    } else {
+    } else if (HAS_EPI_VADJ) {
         // adjoint, level 0: g(xi_j) = sum_t conj(V[j][t]) Lambda^0_{0,j}[t]
         cx* g = (cx*)P.vout;
         const cx* V = (const cx*)P.Vs;
