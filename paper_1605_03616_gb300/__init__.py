@@ -132,6 +132,34 @@ def _torch():
     return torch
 
 
+def _host_buffers(src, dst, N: int, double: bool):
+    """Checks the host buffers of ibf_apply_host, which the library cannot
+    size itself: CPU tensors or numpy arrays, C-contiguous, of the plan's
+    complex dtype, both of shape (nrhs, N) (or (N,) for one column).
+    Returns (src address, dst address, nrhs)."""
+    want = "complex128" if double else "complex64"
+    shapes = []
+    for name, a in (("src", src), ("dst", dst)):
+        if hasattr(a, "data_ptr"):
+            if a.is_cuda:
+                raise TypeError("%s: ibf_apply_host takes host buffers; use apply() for CUDA tensors" % name)
+            if str(a.dtype) != "torch." + want or not a.is_contiguous():
+                raise TypeError("%s: expected a contiguous torch.%s tensor" % (name, want))
+        elif isinstance(a, np.ndarray):
+            if a.dtype != np.dtype(want) or not a.flags["C_CONTIGUOUS"]:
+                raise TypeError("%s: expected a C-contiguous numpy.%s array" % (name, want))
+        else:
+            raise TypeError("%s: expected a CPU tensor or a numpy array" % name)
+        shapes.append(tuple(a.shape))
+    if shapes[0] != shapes[1]:
+        raise ValueError("src and dst shapes differ: %s vs %s" % (shapes[0], shapes[1]))
+    shp = shapes[0]
+    if not ((len(shp) == 2 and shp[1] == N and shp[0] >= 1) or shp == (N,)):
+        raise ValueError("expected shape (nrhs, %d) or (%d,), got %s" % (N, N, shp))
+    addr = [a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data for a in (src, dst)]
+    return addr[0], addr[1], (shp[0] if len(shp) == 2 else 1)
+
+
 class Plan:
     """An IBF plan (include/ibf.h: ibf_plan_create_ex / ibf_plan_destroy)."""
 
@@ -279,13 +307,9 @@ class Plan:
         unordered with `stream` until a later call without it or
         `host_flush`, so the last copy-out overlaps the next call's applies."""
         torch = _torch()
-
-        def ptr(a):
-            return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
-
-        nrhs = int(src.shape[0]) if len(src.shape) == 2 else 1
+        ps, pd, nrhs = _host_buffers(src, dst, self.N, self.dtype == C128)
         s = (stream or torch.cuda.current_stream()).cuda_stream
-        _check(self._lib.ibf_apply_host(self._p, ctypes.c_void_p(ptr(src)), ctypes.c_void_p(ptr(dst)), nrhs,
+        _check(self._lib.ibf_apply_host(self._p, ctypes.c_void_p(ps), ctypes.c_void_p(pd), nrhs,
                                         (HOST_ADJOINT if adjoint else 0) | (HOST_PIPELINE if pipeline else 0) |
                                         (HOST_DEFER if defer else 0), ctypes.c_void_p(s)))
 
